@@ -1,0 +1,162 @@
+/*
+ * ch.h - C ABI of libch.so, a GB300 (sm_103a) implementation of the integer
+ * convex-hull preconditioner of Cadenas & Megson, "An Empirical Evaluation of
+ * Preconditioning Data for Accelerating Convex Hull Computations".
+ *
+ * The hot path has three steps, each a CUDA kernel family:
+ *   1. ch_reduce - Algorithm 1 (Reduction of Points, Section 2.1): n integer
+ *      points in [1,p]^2 become one (min y, max y) pair per x column, held in
+ *      an array L of p entries that start at (p+1, -1).
+ *   2. ch_chain  - the scan of Lemma 1 (Section 2.1) and the bit array M of
+ *      the "Extraction using an array of bits" passage (Section 4): the valid
+ *      columns (entries that left (p+1, -1)) become the x-ordered lower chain
+ *      (x, ly) and upper chain (x, hy).
+ *   3. ch_hull   - a monotone-chain hull on the two chains, so nothing is
+ *      sorted.  Output: the strict vertices (collinear points removed, as in
+ *      the Appendix) counter-clockwise from the lexicographic minimum.
+ *
+ * Conventions shared by every entry point
+ *   - Points are int32 pairs (x, y), interleaved: pts[2k] = x, pts[2k+1] = y.
+ *     Every point must satisfy 1 <= x, y <= p (the square of side p).
+ *   - L is int32[p][2], 0-based: column x is L[2(x-1)] = ly, L[2(x-1)+1] = hy;
+ *     an empty column holds (p+1, -1).
+ *   - Array arguments are DEVICE pointers owned by the caller, unless the name
+ *     says host.  int32 pairs must be 8-byte aligned; 16-byte alignment of the
+ *     point array gives the fastest loads.
+ *   - Nothing allocates device memory inside a call: each call that needs
+ *     scratch takes a caller-owned device workspace whose size is returned by
+ *     the matching *_workspace_size query.  A workspace may be reused by any
+ *     later call on the same stream; two calls in flight at once need two.
+ *   - Calls are asynchronous and stream-ordered on `stream` (NULL = legacy
+ *     default stream).  The return value reports argument and launch errors
+ *     only.  Errors that depend on the data (a point outside [1,p]^2, a
+ *     capacity overflow, a bounded wait that ran out) are recorded in a sticky
+ *     per-device status word; ch_sync_status() waits for the stream and
+ *     returns (and clears) it.  After such an error the outputs of that call
+ *     are unspecified but every kernel has returned: no call ever hangs.
+ *   - p must satisfy 1 <= p <= 2^30 (so int64 cross products of coordinate
+ *     differences cannot overflow); n >= 0.
+ */
+#ifndef CH_H
+#define CH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so this header needs no CUDA. */
+typedef struct CUstream_st *ch_stream_t;
+
+/* Status codes. */
+#define CH_OK 0
+#define CH_ERR_ARG (-1)       /* bad argument: null pointer, n < 0, p out of range, misalignment */
+#define CH_ERR_RANGE (-2)     /* some point outside [1,p]^2 (recorded by a kernel) */
+#define CH_ERR_CAPACITY (-3)  /* an output or workspace region was too small (recorded by a kernel) */
+#define CH_ERR_TIMEOUT (-4)   /* a bounded inter-block wait ran out (recorded by a kernel) */
+#define CH_ERR_CUDA (-5)      /* a CUDA runtime call or kernel launch failed */
+#define CH_ERR_WORKSPACE (-6) /* ws_bytes smaller than the *_workspace_size query */
+
+#define CH_MAX_P (1 << 30)
+
+/* Text for a status code (static storage, never NULL). */
+const char *ch_strerror(int code);
+
+/* ABI version, (major << 16) | minor. */
+int ch_version(void);
+
+/* Wait for `stream`, then read and clear the calling device's status word.
+ * Returns CH_OK or the first recorded error (RANGE, CAPACITY, TIMEOUT), or
+ * CH_ERR_CUDA if the stream itself failed. */
+int ch_sync_status(ch_stream_t stream);
+
+/* Clear the calling device's status word (stream-ordered). */
+int ch_clear_status(ch_stream_t stream);
+
+/* Profiling aid (not part of the method).  events: npairs pairs of
+ * cudaEvent_t handles created by the caller with timing enabled.  While set,
+ * every ch_reduce / ch_convex_hull call records the next pair (round robin)
+ * on its stream immediately before and after its reduction kernel, so the
+ * caller can time that kernel inside a longer stream of work.  npairs = 0
+ * (or events = NULL) turns it off.  Process-wide; the handles must outlive
+ * the calls that use them. */
+int ch_trace_set(void *const *events, int npairs);
+
+/* ---------------------------------------------------------------------- */
+/* Step 1: Algorithm 1, Reduction of Points (Section 2.1).                 */
+/* ---------------------------------------------------------------------- */
+
+/* Workspace bytes ch_reduce needs for n points and side p on the current
+ * device (it holds one private L per resident thread block). */
+int ch_reduce_workspace_size(int64_t n, int32_t p, size_t *bytes);
+
+/* L[x-1] = (min y, max y) over the points with that x, (p+1, -1) for columns
+ * with no point.  pts: int32[n][2] (read only).  L: int32[p][2], written in
+ * full.  Points outside [1,p]^2 are skipped and recorded as CH_ERR_RANGE. */
+int ch_reduce(const int32_t *pts, int64_t n, int32_t p, int32_t *L,
+              void *workspace, size_t ws_bytes, ch_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Step 2: chains of the valid columns (Lemma 1; bit array M, Section 4).  */
+/* ---------------------------------------------------------------------- */
+
+int ch_chain_workspace_size(int32_t p, size_t *bytes);
+
+/* From L (int32[p][2], as written by ch_reduce): a column is valid when its
+ * entry differs from (p+1, -1).  Writes, in increasing x, lower[k] = (x, ly)
+ * and upper[k] = (x, hy) for the k-th valid column (capacity p pairs each),
+ * counts[0] = counts[1] = number of valid columns (device int32[2]), and, if
+ * mask is not NULL, the bit array M: uint32[(p+31)/32], column i (1-based) at
+ * bit (i-1) & 31 of word (i-1) >> 5. */
+int ch_chain(const int32_t *L, int32_t p, int32_t *lower, int32_t *upper,
+             int32_t *counts, uint32_t *mask,
+             void *workspace, size_t ws_bytes, ch_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Step 3: hull of the chains (monotone chain; strictness per Appendix).   */
+/* ---------------------------------------------------------------------- */
+
+int ch_hull_workspace_size(int32_t p, size_t *bytes);
+
+/* lower: int32[counts[0]][2], upper: int32[counts[1]][2], both strictly
+ * increasing in x, with lower[k].y <= upper[j].y where they share a column
+ * (as written by ch_chain).  counts is a DEVICE int32[2] (the host need not
+ * know it).  Writes the strict hull vertices counter-clockwise from the
+ * lexicographic minimum to hull (capacity 2p pairs) and their number to
+ * *hull_count (device int32).  Empty chains give hull_count = 0. */
+int ch_hull(const int32_t *lower, const int32_t *upper, const int32_t *counts,
+            int32_t p, int32_t *hull, int32_t *hull_count,
+            void *workspace, size_t ws_bytes, ch_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* The three steps in one call (the reduction's per-block partial arrays   */
+/* are merged inside the chain step instead of through a separate pass).   */
+/* ---------------------------------------------------------------------- */
+
+int ch_convex_hull_workspace_size(int64_t n, int32_t p, size_t *bytes);
+
+/* Same outputs as ch_reduce + ch_chain + ch_hull; L, lower, upper, counts
+ * may each be NULL, in which case the workspace holds them. */
+int ch_convex_hull(const int32_t *pts, int64_t n, int32_t p, int32_t *L,
+                   int32_t *lower, int32_t *upper, int32_t *counts,
+                   int32_t *hull, int32_t *hull_count,
+                   void *workspace, size_t ws_bytes, ch_stream_t stream);
+
+int ch_convex_hull_host_workspace_size(int64_t n, int32_t p, size_t *bytes);
+
+/* End to end from HOST memory: copies host_pts (int32[n][2]; pinned memory
+ * gives full copy speed) to the device workspace, runs ch_convex_hull, copies
+ * the hull to host_hull (capacity 2p pairs) and its size to
+ * *host_hull_count, and waits for the stream.  Returns the data status too
+ * (it calls ch_sync_status). */
+int ch_convex_hull_host(const int32_t *host_pts, int64_t n, int32_t p,
+                        int32_t *host_hull, int32_t *host_hull_count,
+                        void *workspace, size_t ws_bytes, ch_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CH_H */

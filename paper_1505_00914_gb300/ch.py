@@ -1,0 +1,248 @@
+"""Thin ctypes binding of libch.so (C ABI in include/ch.h).
+
+Argument marshalling only: every step of the hull path runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the current CUDA stream.
+The functions keep the C names; outputs and workspaces the caller does not
+pass are allocated here with torch (the C calls never allocate).
+
+Importing this module does not touch the GPU.  The first call loads
+libch.so and raises ``RuntimeError`` if it cannot (no silent fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import _build
+
+CH_OK = 0
+CH_ERR_ARG = -1
+CH_ERR_RANGE = -2
+CH_ERR_CAPACITY = -3
+CH_ERR_TIMEOUT = -4
+CH_ERR_CUDA = -5
+CH_ERR_WORKSPACE = -6
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ChError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+def _declare(lib):
+    P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    szp = ctypes.POINTER(ctypes.c_size_t)
+    sigs = {
+        "ch_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "ch_version": (ctypes.c_int, []),
+        "ch_sync_status": (ctypes.c_int, [P]),
+        "ch_clear_status": (ctypes.c_int, [P]),
+        "ch_trace_set": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
+        "ch_reduce_workspace_size": (ctypes.c_int, [i64, i32, szp]),
+        "ch_reduce": (ctypes.c_int, [P, i64, i32, P, P, sz, P]),
+        "ch_chain_workspace_size": (ctypes.c_int, [i32, szp]),
+        "ch_chain": (ctypes.c_int, [P, i32, P, P, P, P, P, sz, P]),
+        "ch_hull_workspace_size": (ctypes.c_int, [i32, szp]),
+        "ch_hull": (ctypes.c_int, [P, P, P, i32, P, P, P, sz, P]),
+        "ch_convex_hull_workspace_size": (ctypes.c_int, [i64, i32, szp]),
+        "ch_convex_hull": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P, sz, P]),
+        "ch_convex_hull_host_workspace_size": (ctypes.c_int, [i64, i32, szp]),
+        "ch_convex_hull_host": (ctypes.c_int, [P, i64, i32, P, ctypes.POINTER(ctypes.c_int32), P, sz, P]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libch.so (built first if absent)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                path = _build.build()
+            try:
+                _lib = _declare(ctypes.CDLL(path))
+            except OSError as e:
+                raise RuntimeError(f"libch.so could not be loaded from {path}: {e}") from e
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().ch_strerror(int(code)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != CH_OK:
+        raise ChError(rc, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t):
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return t.device
+
+
+def _size(fn, *args) -> int:
+    out = ctypes.c_size_t(0)
+    _check(fn(*args, ctypes.byref(out)), fn.__name__)
+    return int(out.value)
+
+
+def _ws(nbytes: int, device, ws):
+    if ws is not None:
+        if ws.numel() * ws.element_size() < nbytes:
+            raise ChError(CH_ERR_WORKSPACE, "workspace")
+        return ws
+    return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+
+
+def _pts(pts):
+    if pts.dtype != torch.int32 or pts.dim() != 2 or pts.shape[1] != 2 or not pts.is_contiguous():
+        raise ValueError("points must be a contiguous int32 tensor of shape (n, 2)")
+    return pts
+
+
+def ch_sync_status(stream=None) -> int:
+    return int(lib().ch_sync_status(_stream(stream)))
+
+
+def ch_clear_status(stream=None):
+    _check(lib().ch_clear_status(_stream(stream)), "ch_clear_status")
+
+
+def ch_trace_set(events):
+    """Profiling aid: a list of (start, end) torch.cuda.Event pairs (timing
+    enabled, already recorded once so their handles exist); every reduction
+    kernel launched afterwards is bracketed by the next pair.  [] turns it off."""
+    flat = [e.cuda_event for pair in events for e in pair]
+    arr = (ctypes.c_void_p * max(1, len(flat)))(*flat)
+    _check(lib().ch_trace_set(arr, len(events)), "ch_trace_set")
+
+
+def ch_reduce_workspace_size(n: int, p: int) -> int:
+    return _size(lib().ch_reduce_workspace_size, int(n), int(p))
+
+
+def ch_reduce(pts, p: int, L=None, workspace=None, stream=None):
+    """Algorithm 1: returns L (p, 2) int32 on the points' device."""
+    pts = _pts(pts)
+    dev = _dev(pts)
+    n = pts.shape[0]
+    if L is None:
+        L = torch.empty((p, 2), dtype=torch.int32, device=dev)
+    ws = _ws(ch_reduce_workspace_size(n, p), dev, workspace)
+    _check(lib().ch_reduce(_ptr(pts), n, int(p), _ptr(L), _ptr(ws), ws.numel(), _stream(stream)),
+           "ch_reduce")
+    return L
+
+
+def ch_chain_workspace_size(p: int) -> int:
+    return _size(lib().ch_chain_workspace_size, int(p))
+
+
+def ch_chain(L, p: int | None = None, lower=None, upper=None, counts=None, mask=None,
+             workspace=None, stream=None, with_mask: bool = False):
+    """Lemma 1 chains of L: returns (lower, upper, counts[, mask]); lower and
+    upper have capacity p rows, the first counts[0] of which are valid."""
+    dev = _dev(L)
+    p = int(L.shape[0] if p is None else p)
+    if lower is None:
+        lower = torch.empty((p, 2), dtype=torch.int32, device=dev)
+    if upper is None:
+        upper = torch.empty((p, 2), dtype=torch.int32, device=dev)
+    if counts is None:
+        counts = torch.empty(2, dtype=torch.int32, device=dev)
+    if with_mask and mask is None:
+        mask = torch.empty(((p + 31) // 32,), dtype=torch.int32, device=dev)
+    ws = _ws(ch_chain_workspace_size(p), dev, workspace)
+    _check(lib().ch_chain(_ptr(L), p, _ptr(lower), _ptr(upper), _ptr(counts), _ptr(mask),
+                          _ptr(ws), ws.numel(), _stream(stream)), "ch_chain")
+    if mask is not None:
+        return lower, upper, counts, mask
+    return lower, upper, counts
+
+
+def ch_hull_workspace_size(p: int) -> int:
+    return _size(lib().ch_hull_workspace_size, int(p))
+
+
+def ch_hull(lower, upper, counts, p: int, hull=None, hull_count=None, workspace=None,
+            stream=None):
+    """Strict hull of the chains: returns (hull (2p, 2) capacity, hull_count (1,))."""
+    dev = _dev(lower)
+    if hull is None:
+        hull = torch.empty((2 * p, 2), dtype=torch.int32, device=dev)
+    if hull_count is None:
+        hull_count = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = _ws(ch_hull_workspace_size(p), dev, workspace)
+    _check(lib().ch_hull(_ptr(lower), _ptr(upper), _ptr(counts), int(p), _ptr(hull),
+                         _ptr(hull_count), _ptr(ws), ws.numel(), _stream(stream)), "ch_hull")
+    return hull, hull_count
+
+
+def ch_convex_hull_workspace_size(n: int, p: int) -> int:
+    return _size(lib().ch_convex_hull_workspace_size, int(n), int(p))
+
+
+def ch_convex_hull(pts, p: int, L=None, lower=None, upper=None, counts=None, hull=None,
+                   hull_count=None, workspace=None, stream=None):
+    """All three steps; returns (hull, hull_count).  L/lower/upper/counts are
+    written when given (else kept in the workspace)."""
+    pts = _pts(pts)
+    dev = _dev(pts)
+    n = pts.shape[0]
+    if hull is None:
+        hull = torch.empty((2 * p, 2), dtype=torch.int32, device=dev)
+    if hull_count is None:
+        hull_count = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = _ws(ch_convex_hull_workspace_size(n, p), dev, workspace)
+    _check(lib().ch_convex_hull(_ptr(pts), n, int(p), _ptr(L), _ptr(lower), _ptr(upper),
+                                _ptr(counts), _ptr(hull), _ptr(hull_count), _ptr(ws), ws.numel(),
+                                _stream(stream)), "ch_convex_hull")
+    return hull, hull_count
+
+
+def ch_convex_hull_host_workspace_size(n: int, p: int) -> int:
+    return _size(lib().ch_convex_hull_host_workspace_size, int(n), int(p))
+
+
+def ch_convex_hull_host(host_pts, p: int, workspace, stream=None, host_hull=None):
+    """End to end from host memory (a CPU int32 (n, 2) tensor, pinned for
+    speed): returns the hull as a CPU int32 (h, 2) tensor."""
+    if host_pts.is_cuda or host_pts.dtype != torch.int32 or not host_pts.is_contiguous():
+        raise ValueError("host_pts must be a contiguous CPU int32 tensor of shape (n, 2)")
+    n = host_pts.shape[0]
+    if host_hull is None:
+        host_hull = torch.empty((2 * p, 2), dtype=torch.int32)
+    cnt = ctypes.c_int32(0)
+    _check(lib().ch_convex_hull_host(_ptr(host_pts), n, int(p), _ptr(host_hull),
+                                     ctypes.byref(cnt), _ptr(workspace), workspace.numel(),
+                                     _stream(stream)), "ch_convex_hull_host")
+    return host_hull[: cnt.value]

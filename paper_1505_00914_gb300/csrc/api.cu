@@ -1,0 +1,379 @@
+// C ABI of libch.so (declared in include/ch.h): argument checks, workspace
+// layouts, the per-device status word and launch sequencing.  No entry point
+// allocates device memory; every launch goes to the caller's stream.
+#include <mutex>
+
+#include "ch_internal.cuh"
+
+// Sticky per-device error word written by the kernels (ST_* bits).
+__device__ unsigned g_ch_status = 0;
+
+namespace ch {
+
+namespace {
+constexpr int MAX_DEV = 64;
+std::mutex g_mu;
+unsigned *g_status_ptr[MAX_DEV] = {};
+int g_sms[MAX_DEV] = {};
+
+inline bool aligned8(const void *p) { return ((uintptr_t)p & 7) == 0; }
+
+// ch_trace_set ring of event pairs around the reduction kernel.
+std::mutex g_trace_mu;
+cudaEvent_t g_trace[2 * 1024];
+int g_trace_n = 0, g_trace_next = 0;
+
+template <class F>
+cudaError_t traced(cudaStream_t s, F &&launch)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_trace_mu);
+        if (g_trace_n > 0) {
+            const int i = g_trace_next;
+            g_trace_next = (g_trace_next + 1) % g_trace_n;
+            e0 = g_trace[2 * i];
+            e1 = g_trace[2 * i + 1];
+        }
+    }
+    if (e0 && cudaEventRecord(e0, s) != cudaSuccess)
+        return cudaErrorUnknown;
+    cudaError_t e = launch();
+    if (e == cudaSuccess && e1)
+        e = cudaEventRecord(e1, s);
+    return e;
+}
+inline int cuda_rc(cudaError_t e) { return e == cudaSuccess ? CH_OK : CH_ERR_CUDA; }
+}  // namespace
+
+unsigned *device_status_ptr()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV)
+        return nullptr;
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!g_status_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_ch_status) != cudaSuccess)
+            return nullptr;
+        g_status_ptr[dev] = reinterpret_cast<unsigned *>(p);
+    }
+    return g_status_ptr[dev];
+}
+
+int sm_count()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV)
+        return 0;
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!g_sms[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        g_sms[dev] = v;
+    }
+    return g_sms[dev];
+}
+
+namespace {
+
+// Workspace of the whole path: chain look-back state, partial arrays (or L
+// for p > 65536), optional chain outputs, hull scratch.
+struct PathWs {
+    ReducePlan plan;
+    size_t state, part, L, lower, upper, counts, hull, end;
+};
+
+int path_layout(int64_t n, int p, PathWs *w)
+{
+    int rc = reduce_plan(n, p, &w->plan);
+    if (rc != CH_OK)
+        return rc;
+    WsLayout l;
+    w->state = l.take(chain_state_bytes(p));
+    w->part = l.take(reduce_partials_bytes(w->plan, p));
+    w->L = l.take((size_t)p * 8);
+    w->lower = l.take((size_t)p * 8);
+    w->upper = l.take((size_t)p * 8);
+    w->counts = l.take(8);
+    w->hull = l.take(hull_ws_bytes(p));
+    w->end = l.off;
+    return CH_OK;
+}
+
+int check_np(int64_t n, int32_t p)
+{
+    if (n < 0 || p < 1 || p > CH_MAX_P)
+        return CH_ERR_ARG;
+    return CH_OK;
+}
+
+}  // namespace
+}  // namespace ch
+
+using namespace ch;
+
+extern "C" {
+
+const char *ch_strerror(int code)
+{
+    switch (code) {
+    case CH_OK: return "ok";
+    case CH_ERR_ARG: return "invalid argument";
+    case CH_ERR_RANGE: return "a point lies outside [1,p]^2";
+    case CH_ERR_CAPACITY: return "output or workspace capacity exceeded";
+    case CH_ERR_TIMEOUT: return "a bounded inter-block wait ran out";
+    case CH_ERR_CUDA: return "CUDA runtime error";
+    case CH_ERR_WORKSPACE: return "workspace smaller than the size query";
+    default: return "unknown status";
+    }
+}
+
+int ch_version(void) { return (1 << 16) | 0; }
+
+int ch_sync_status(ch_stream_t stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess)
+        return CH_ERR_CUDA;
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    unsigned v = 0;
+    if (cudaMemcpy(&v, st, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CH_ERR_CUDA;
+    if (v) {
+        const unsigned zero = 0;
+        if (cudaMemcpy(st, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
+            return CH_ERR_CUDA;
+    }
+    if (v & ST_RANGE)
+        return CH_ERR_RANGE;
+    if (v & ST_CAPACITY)
+        return CH_ERR_CAPACITY;
+    if (v & ST_TIMEOUT)
+        return CH_ERR_TIMEOUT;
+    return CH_OK;
+}
+
+int ch_clear_status(ch_stream_t stream)
+{
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    return cuda_rc(cudaMemsetAsync(st, 0, sizeof(unsigned), reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int ch_trace_set(void *const *events, int npairs)
+{
+    if (npairs < 0 || npairs > 1024 || (npairs > 0 && !events))
+        return CH_ERR_ARG;
+    std::lock_guard<std::mutex> g(g_trace_mu);
+    for (int i = 0; i < 2 * npairs; ++i)
+        g_trace[i] = reinterpret_cast<cudaEvent_t>(events[i]);
+    g_trace_n = npairs;
+    g_trace_next = 0;
+    return CH_OK;
+}
+
+int ch_reduce_workspace_size(int64_t n, int32_t p, size_t *bytes)
+{
+    if (!bytes || check_np(n, p) != CH_OK)
+        return CH_ERR_ARG;
+    ReducePlan pl;
+    int rc = reduce_plan(n, p, &pl);
+    if (rc != CH_OK)
+        return rc;
+    WsLayout l;
+    l.take(reduce_partials_bytes(pl, p));
+    *bytes = l.off;
+    return CH_OK;
+}
+
+int ch_reduce(const int32_t *pts, int64_t n, int32_t p, int32_t *L, void *workspace,
+              size_t ws_bytes, ch_stream_t stream)
+{
+    if (check_np(n, p) != CH_OK || !L || (n > 0 && !pts) || !aligned8(pts) || !aligned8(L))
+        return CH_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ReducePlan pl;
+    int rc = reduce_plan(n, p, &pl);
+    if (rc != CH_OK)
+        return rc;
+    const size_t need = reduce_partials_bytes(pl, p);
+    if (ws_bytes < need || (need > 0 && !workspace))
+        return CH_ERR_WORKSPACE;
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    uint32_t *part = reinterpret_cast<uint32_t *>(workspace);
+    cudaError_t e = traced(s, [&] { return reduce_launch(pl, pts, n, p, part, L, st, s); });
+    if (e == cudaSuccess && pl.mode == 0)
+        e = reduce_merge_launch(part, pl.copies, p, L, s);
+    return cuda_rc(e);
+}
+
+int ch_chain_workspace_size(int32_t p, size_t *bytes)
+{
+    if (!bytes || p < 1 || p > CH_MAX_P)
+        return CH_ERR_ARG;
+    WsLayout l;
+    l.take(chain_state_bytes(p));
+    *bytes = l.off;
+    return CH_OK;
+}
+
+int ch_chain(const int32_t *L, int32_t p, int32_t *lower, int32_t *upper, int32_t *counts,
+             uint32_t *mask, void *workspace, size_t ws_bytes, ch_stream_t stream)
+{
+    if (p < 1 || p > CH_MAX_P || !L || !lower || !upper || !counts || !aligned8(L) ||
+        !aligned8(lower) || !aligned8(upper))
+        return CH_ERR_ARG;
+    size_t need = 0;
+    ch_chain_workspace_size(p, &need);
+    if (ws_bytes < need || !workspace)
+        return CH_ERR_WORKSPACE;
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    return cuda_rc(chain_launch(L, nullptr, 0, p, nullptr, lower, upper, counts, mask, workspace,
+                                st, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int ch_hull_workspace_size(int32_t p, size_t *bytes)
+{
+    if (!bytes || p < 1 || p > CH_MAX_P)
+        return CH_ERR_ARG;
+    *bytes = hull_ws_bytes(p);
+    return CH_OK;
+}
+
+int ch_hull(const int32_t *lower, const int32_t *upper, const int32_t *counts, int32_t p,
+            int32_t *hull, int32_t *hull_count, void *workspace, size_t ws_bytes,
+            ch_stream_t stream)
+{
+    if (p < 1 || p > CH_MAX_P || !lower || !upper || !counts || !hull || !hull_count ||
+        !aligned8(lower) || !aligned8(upper) || !aligned8(hull))
+        return CH_ERR_ARG;
+    if (ws_bytes < hull_ws_bytes(p) || !workspace)
+        return CH_ERR_WORKSPACE;
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    return cuda_rc(hull_launch(lower, upper, counts, p, hull, hull_count, workspace, st,
+                               reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int ch_convex_hull_workspace_size(int64_t n, int32_t p, size_t *bytes)
+{
+    if (!bytes || check_np(n, p) != CH_OK)
+        return CH_ERR_ARG;
+    PathWs w;
+    int rc = path_layout(n, p, &w);
+    if (rc != CH_OK)
+        return rc;
+    *bytes = w.end;
+    return CH_OK;
+}
+
+int ch_convex_hull(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t *lower,
+                   int32_t *upper, int32_t *counts, int32_t *hull, int32_t *hull_count,
+                   void *workspace, size_t ws_bytes, ch_stream_t stream)
+{
+    if (check_np(n, p) != CH_OK || (n > 0 && !pts) || !hull || !hull_count || !aligned8(pts) ||
+        !aligned8(L) || !aligned8(lower) || !aligned8(upper) || !aligned8(hull))
+        return CH_ERR_ARG;
+    PathWs w;
+    int rc = path_layout(n, p, &w);
+    if (rc != CH_OK)
+        return rc;
+    if (ws_bytes < w.end || !workspace)
+        return CH_ERR_WORKSPACE;
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *b = reinterpret_cast<char *>(workspace);
+    if (!L && w.plan.mode == 1)
+        L = reinterpret_cast<int32_t *>(b + w.L);
+    if (!lower)
+        lower = reinterpret_cast<int32_t *>(b + w.lower);
+    if (!upper)
+        upper = reinterpret_cast<int32_t *>(b + w.upper);
+    if (!counts)
+        counts = reinterpret_cast<int32_t *>(b + w.counts);
+    uint32_t *part = reinterpret_cast<uint32_t *>(b + w.part);
+    cudaError_t e = traced(s, [&] { return reduce_launch(w.plan, pts, n, p, part, L, st, s); });
+    if (e != cudaSuccess)
+        return CH_ERR_CUDA;
+    if (w.plan.mode == 0)
+        e = chain_launch(nullptr, part, w.plan.copies, p, L, lower, upper, counts, nullptr,
+                         b + w.state, st, s);
+    else
+        e = chain_launch(L, nullptr, 0, p, nullptr, lower, upper, counts, nullptr, b + w.state, st,
+                         s);
+    if (e != cudaSuccess)
+        return CH_ERR_CUDA;
+    return cuda_rc(hull_launch(lower, upper, counts, p, hull, hull_count, b + w.hull, st, s));
+}
+
+int ch_convex_hull_host_workspace_size(int64_t n, int32_t p, size_t *bytes)
+{
+    if (!bytes || check_np(n, p) != CH_OK)
+        return CH_ERR_ARG;
+    PathWs w;
+    int rc = path_layout(n, p, &w);
+    if (rc != CH_OK)
+        return rc;
+    WsLayout l;
+    l.take((size_t)n * 8);
+    l.take((size_t)p * 16);
+    l.take(8);
+    l.take(w.end);
+    *bytes = l.off;
+    return CH_OK;
+}
+
+int ch_convex_hull_host(const int32_t *host_pts, int64_t n, int32_t p, int32_t *host_hull,
+                        int32_t *host_hull_count, void *workspace, size_t ws_bytes,
+                        ch_stream_t stream)
+{
+    if (check_np(n, p) != CH_OK || (n > 0 && !host_pts) || !host_hull || !host_hull_count)
+        return CH_ERR_ARG;
+    size_t need = 0;
+    int rc = ch_convex_hull_host_workspace_size(n, p, &need);
+    if (rc != CH_OK)
+        return rc;
+    if (ws_bytes < need || !workspace)
+        return CH_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    WsLayout l;
+    char *b = reinterpret_cast<char *>(workspace);
+    int32_t *d_pts = reinterpret_cast<int32_t *>(b + l.take((size_t)n * 8));
+    int32_t *d_hull = reinterpret_cast<int32_t *>(b + l.take((size_t)p * 16));
+    int32_t *d_cnt = reinterpret_cast<int32_t *>(b + l.take(8));
+    const size_t inner_off = l.take(0);
+    void *inner = b + inner_off;
+    const size_t inner_bytes = ws_bytes - inner_off;
+    if (n > 0 && cudaMemcpyAsync(d_pts, host_pts, (size_t)n * 8, cudaMemcpyHostToDevice, s) !=
+                     cudaSuccess)
+        return CH_ERR_CUDA;
+    rc = ch_convex_hull(d_pts, n, p, nullptr, nullptr, nullptr, nullptr, d_hull, d_cnt, inner,
+                        inner_bytes, stream);
+    if (rc != CH_OK)
+        return rc;
+    int32_t h = 0;
+    if (cudaMemcpyAsync(&h, d_cnt, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CH_ERR_CUDA;
+    if (h < 0 || h > 2 * p)
+        return CH_ERR_CAPACITY;
+    if (h > 0 && cudaMemcpyAsync(host_hull, d_hull, (size_t)h * 8, cudaMemcpyDeviceToHost, s) !=
+                     cudaSuccess)
+        return CH_ERR_CUDA;
+    *host_hull_count = h;
+    return ch_sync_status(stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,56 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/*.h declares (no compute call: these run without a GPU)."""
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1505_00914_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(ch_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    return _build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("ch_reduce", "ch_chain", "ch_hull", "ch_convex_hull", "ch_sync_status"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = _declared() - exported
+    assert not missing, missing
+
+
+def test_library_loads_and_binds_without_gpu(lib_path):
+    from paper_1505_00914_gb300 import ch
+    lib = ch.lib()
+    assert lib.ch_version() >> 16 == 1
+    for name in _declared():
+        assert hasattr(lib, name)
+    assert ch.strerror(ch.CH_ERR_RANGE)
+    assert ch.strerror(0) == "ok"
+
+
+def test_objects_target_sm_103a(lib_path):
+    """The build passes one -gencode, for sm_103a only."""
+    assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
