@@ -207,7 +207,7 @@ int ch_reduce(const int32_t *pts, int64_t n, int32_t p, int32_t *L, void *worksp
     unsigned *st = device_status_ptr();
     if (!st)
         return CH_ERR_CUDA;
-    uint32_t *part = reinterpret_cast<uint32_t *>(workspace);
+    void *part = workspace;
     cudaError_t e = traced(s, [&] { return reduce_launch(pl, pts, n, p, part, L, st, s); });
     if (e == cudaSuccess && pl.mode == 0)
         e = reduce_merge_launch(part, pl.copies, p, L, s);
@@ -237,8 +237,8 @@ int ch_chain(const int32_t *L, int32_t p, int32_t *lower, int32_t *upper, int32_
     unsigned *st = device_status_ptr();
     if (!st)
         return CH_ERR_CUDA;
-    return cuda_rc(chain_launch(L, nullptr, 0, p, nullptr, lower, upper, counts, mask, workspace,
-                                st, reinterpret_cast<cudaStream_t>(stream)));
+    return cuda_rc(chain_launch(L, p, lower, upper, counts, mask, workspace, false, nullptr,
+                                nullptr, st, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 int ch_hull_workspace_size(int32_t p, size_t *bytes)
@@ -295,27 +295,33 @@ int ch_convex_hull(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t
         return CH_ERR_CUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *b = reinterpret_cast<char *>(workspace);
-    if (!L && w.plan.mode == 1)
-        L = reinterpret_cast<int32_t *>(b + w.L);
+    if (!L && w.plan.mode != 0)
+        L = reinterpret_cast<int32_t *>(b + w.L);  // the filtered forms write L directly
     if (!lower)
         lower = reinterpret_cast<int32_t *>(b + w.lower);
     if (!upper)
         upper = reinterpret_cast<int32_t *>(b + w.upper);
     if (!counts)
         counts = reinterpret_cast<int32_t *>(b + w.counts);
-    uint32_t *part = reinterpret_cast<uint32_t *>(b + w.part);
+    void *part = b + w.part;
     cudaError_t e = traced(s, [&] { return reduce_launch(w.plan, pts, n, p, part, L, st, s); });
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
-    if (w.plan.mode == 0)
-        e = chain_launch(nullptr, part, w.plan.copies, p, L, lower, upper, counts, nullptr,
-                         b + w.state, st, s);
-    else
-        e = chain_launch(L, nullptr, 0, p, nullptr, lower, upper, counts, nullptr, b + w.state, st,
-                         s);
+    if (w.plan.mode == 0) {
+        if (!L)
+            L = reinterpret_cast<int32_t *>(b + w.L);
+        e = reduce_merge_launch(part, w.plan.copies, p, L, s);
+        if (e != cudaSuccess)
+            return CH_ERR_CUDA;
+    }
+    const HullLayout hl = hull_layout(p);
+    char *hw = b + w.hull;
+    e = chain_launch(L, p, lower, upper, counts, nullptr, b + w.state, false,
+                     reinterpret_cast<int2 *>(hw + hl.cand), reinterpret_cast<int *>(hw + hl.ccnt),
+                     st, s);
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
-    return cuda_rc(hull_launch(lower, upper, counts, p, hull, hull_count, b + w.hull, st, s));
+    return cuda_rc(hull_final_launch(hl, hw, hull, hull_count, s));
 }
 
 int ch_convex_hull_host_workspace_size(int64_t n, int32_t p, size_t *bytes)

@@ -22,13 +22,6 @@ enum : unsigned {
 // far below a hang.
 constexpr int SPIN_LIMIT = 1 << 22;
 
-// Packed private column word of the reduction: (lo16 << 16) | hi16 with
-// lo16 = min(y) - 1 and hi16 = max(y) - 1; an empty column is lo16 = 0xFFFF,
-// hi16 = 0.  A column is non-empty iff lo16 <= hi16 (a column whose only y is
-// p = 65536 holds lo16 = hi16 = 0xFFFF).  Usable for p <= 65536.
-constexpr uint32_t PACK_EMPTY = 0xFFFF0000u;
-constexpr int PACK_MAX_P = 65536;
-
 // 64-bit orientation of (o, a, b): > 0 for a counter-clockwise turn.
 __device__ __forceinline__ long long cross3(int2 o, int2 a, int2 b)
 {
@@ -49,37 +42,50 @@ struct WsLayout {
 
 // ---- reduction (reduce.cu) ----
 struct ReducePlan {
-    int mode;      // 0: private packed copies, 1: global atomics (p > 65536)
-    int cluster;   // CTAs sharing one private copy (1 or 2)
-    int grid;      // CTAs launched
-    int copies;    // grid / cluster = number of partial arrays
-    int cols;      // columns held per CTA
+    int mode;      // 0: private copies, 1: filtered global L, 2: global L only
+    int cluster;   // CTAs per cluster (always 1)
+    int grid;      // CTAs of the main reduction kernel
+    int threads;   // threads per CTA of the main reduction kernel
+    int copies;    // mode 0: number of int2[p] partial arrays
+    int shift;     // modes 1-2: row-bin shift of the filter
     size_t smem;   // dynamic shared memory per CTA
 };
 int reduce_plan(int64_t n, int p, ReducePlan *plan);
 size_t reduce_partials_bytes(const ReducePlan &plan, int p);
-// Writes plan.copies packed partial arrays of p words each (mode 0), or the
-// final L directly (mode 1).
+// Mode 0 writes plan.copies packed uint32[p] partial arrays to `scratch`
+// (((lo-1) << 16) | (hi-1), 0xFFFF0000 when empty); modes 1-2 write the final
+// L (mode 1 keeps its global filter in `scratch`).
 cudaError_t reduce_launch(const ReducePlan &plan, const int32_t *pts, int64_t n, int p,
-                          uint32_t *partials, int32_t *L, unsigned *status, cudaStream_t s);
+                          void *scratch, int32_t *L, unsigned *status, cudaStream_t s);
 // L = column-wise merge of `copies` packed partial arrays.
-cudaError_t reduce_merge_launch(const uint32_t *partials, int copies, int p, int32_t *L,
+cudaError_t reduce_merge_launch(const void *partials, int copies, int p, int32_t *L,
                                 cudaStream_t s);
 
 // ---- chain (chain.cu) ----
 int chain_tiles(int p);
 size_t chain_state_bytes(int p);
-// If partials != nullptr, merges `copies` packed arrays into L first (and
-// writes L if L_out != nullptr); otherwise reads L_in.
-cudaError_t chain_launch(const int32_t *L_in, const uint32_t *partials, int copies, int p,
-                         int32_t *L_out, int32_t *lower, int32_t *upper, int32_t *counts,
-                         uint32_t *mask, void *state, unsigned *status, cudaStream_t s);
+// Chains of L.  With cand != nullptr also runs the exact hull pre-filter on
+// each 1024-column tile and writes its survivors in the hull layout (so that
+// hull_final_launch can follow directly).  state: chain_state_bytes(p),
+// zeroed here unless state_zeroed.
+cudaError_t chain_launch(const int32_t *L, int p, int32_t *lower, int32_t *upper, int32_t *counts,
+                         uint32_t *mask, void *state, bool state_zeroed, int2 *cand, int *ccnt,
+                         unsigned *status, cudaStream_t s);
 
 // ---- hull (hull.cu) ----
+struct HullLayout {
+    int nblk;  // runs of 1024 chain points (or chain tiles) per chain
+    size_t cand, ccnt, gA, gB, gF, gix, end;
+};
+HullLayout hull_layout(int p);
 size_t hull_ws_bytes(int p);
+// Filter + final CTA from the chains.
 cudaError_t hull_launch(const int32_t *lower, const int32_t *upper, const int32_t *counts, int p,
                         int32_t *hull, int32_t *hull_count, void *ws, unsigned *status,
                         cudaStream_t s);
+// Final CTA only, from survivors already in the hull workspace.
+cudaError_t hull_final_launch(const HullLayout &h, void *ws, int32_t *hull, int32_t *hull_count,
+                              cudaStream_t s);
 
 // ---- api.cu ----
 unsigned *device_status_ptr();  // this device's status word (nullptr on failure)

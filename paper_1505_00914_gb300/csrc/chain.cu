@@ -6,22 +6,26 @@
 // block/bit indexing with w = 32).  Where the paper walks set bits with ctz,
 // the GPU ranks them: a column's output slot is the number of valid columns
 // before it, popc of the lower bits of its word plus an exclusive scan over
-// words.  The scan runs in one pass over the tiles of L: each tile publishes
-// its count and looks back at its predecessors' (decoupled look-back), with
-// tiles handed out in launch order by an atomic ticket so that every tile it
-// waits on is already running; every wait is bounded.
+// words.  The scan runs in one pass over 1024-column tiles of L: each tile
+// publishes its count and looks back at its predecessors' (decoupled
+// look-back), with tiles handed out in launch order by an atomic ticket so
+// that every tile it waits on is already running; every wait is bounded.
+//
+// The fused form used by the whole path also runs the exact hull pre-filter
+// (hull_filter.cuh) on the tile's own stretch of both chains while it is in
+// shared memory, and writes the survivors of each tile for the final hull.
 #include <cuda/atomic>
 
+#include <type_traits>
+
 #include "ch_internal.cuh"
+#include "hull_filter.cuh"
 
 namespace ch {
 namespace {
 
-constexpr int CT = 256;           // threads per CTA
-constexpr int CPT = 4;            // columns per thread
-constexpr int WPB = CT / 32;      // warps per CTA
-constexpr int TILE = CT * CPT;    // columns per tile (= 32 words of M)
-static_assert(CPT * WPB == 32, "one warp scans the tile's words");
+constexpr int TILE = RUN;         // columns per tile (one per thread)
+constexpr int WPB = TILE / 32;    // words of M per tile
 
 constexpr unsigned long long FLAG_AGG = 1ull << 62;
 constexpr unsigned long long FLAG_PRE = 2ull << 62;
@@ -29,104 +33,119 @@ constexpr unsigned long long VAL_MASK = (1ull << 62) - 1;
 
 using aref = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>;
 
-__device__ long long look_back(unsigned long long *ts, int tile, long long agg, unsigned *status)
+// Exclusive prefix of tile `tile` by decoupled look-back, run by a full warp.
+// A window covers LB_W * 32 predecessors (lane l, slot k inspects tile
+// base - l - 32k), all loads in flight at once; the window moves back until
+// it meets a tile that has published its inclusive prefix.  Waiting tiles are
+// running (ticket order), so the spin polls without sleeping; it is bounded.
+constexpr int LB_W = 8;
+
+__device__ long long warp_look_back(unsigned long long *ts, int tile, long long agg, int lane,
+                                    unsigned *status)
 {
     if (tile == 0) {
-        aref(ts[0]).store(FLAG_PRE | (unsigned long long)agg, cuda::memory_order_release);
+        if (lane == 0)
+            aref(ts[0]).store(FLAG_PRE | (unsigned long long)agg, cuda::memory_order_release);
         return 0;
     }
-    aref(ts[tile]).store(FLAG_AGG | (unsigned long long)agg, cuda::memory_order_release);
+    if (lane == 0)
+        aref(ts[tile]).store(FLAG_AGG | (unsigned long long)agg, cuda::memory_order_release);
     long long excl = 0;
-    int j = tile - 1, spins = 0;
-    while (j >= 0) {
-        unsigned long long v = aref(ts[j]).load(cuda::memory_order_acquire);
-        unsigned long long f = v & ~VAL_MASK;
-        if (f == 0) {
-            if (++spins > SPIN_LIMIT) {
-                atomicOr(status, ST_TIMEOUT);
-                break;
-            }
-            __nanosleep(100);
-            continue;
+    int base = tile - 1;
+    int spins = 0;
+    bool timed_out = false;
+    while (base >= 0) {
+        unsigned long long v[LB_W];
+#pragma unroll
+        for (int k = 0; k < LB_W; ++k) {
+            const int j = base - lane - 32 * k;
+            v[k] = j >= 0 ? aref(ts[j]).load(cuda::memory_order_acquire) : FLAG_PRE;
         }
-        excl += (long long)(v & VAL_MASK);
-        if (f == FLAG_PRE)
+#pragma unroll
+        for (int k = 0; k < LB_W; ++k) {
+            const int j = base - lane - 32 * k;
+            while ((v[k] & ~VAL_MASK) == 0) {
+                if (++spins > SPIN_LIMIT) {
+                    timed_out = true;
+                    v[k] = FLAG_PRE;
+                    break;
+                }
+                v[k] = aref(ts[j]).load(cuda::memory_order_acquire);
+            }
+        }
+        // nearest inclusive prefix in the window: slot k, lane l <-> distance 32k + l
+        int stop = 32 * LB_W;
+#pragma unroll
+        for (int k = LB_W - 1; k >= 0; --k) {
+            const unsigned pre = __ballot_sync(0xFFFFFFFFu, (v[k] & ~VAL_MASK) == FLAG_PRE);
+            if (pre)
+                stop = 32 * k + __ffs(pre) - 1;
+        }
+        long long val = 0;
+#pragma unroll
+        for (int k = 0; k < LB_W; ++k)
+            if (32 * k + lane <= stop)
+                val += (long long)(v[k] & VAL_MASK);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            val += __shfl_xor_sync(0xFFFFFFFFu, val, o);
+        excl += val;
+        if (stop < 32 * LB_W)
             break;
-        --j;
+        base -= 32 * LB_W;
     }
-    aref(ts[tile]).store(FLAG_PRE | (unsigned long long)(excl + agg), cuda::memory_order_release);
+    if (__any_sync(0xFFFFFFFFu, timed_out) && lane == 0)
+        atomicOr(status, ST_TIMEOUT);
+    if (lane == 0)
+        aref(ts[tile]).store(FLAG_PRE | (unsigned long long)(excl + agg), cuda::memory_order_release);
     return excl;
 }
 
-template <bool FROM_PART>
-__global__ void __launch_bounds__(CT)
-    k_chain(const int2 *__restrict__ Lin, const uint32_t *__restrict__ part, int copies, int p,
-            int2 *Lout, int2 *lower, int2 *upper, int *counts, uint32_t *mask,
-            unsigned long long *state, int ntiles, unsigned *status)
+struct FilterSmem {
+    int2 P[2][TILE];     // the tile's stretch of the lower chain and mirrored upper chain
+    short M[2][2 * TILE];
+};
+
+template <bool FILTER>
+__global__ void __launch_bounds__(TILE)
+    k_chain(const int2 *__restrict__ L, int p, int2 *lower, int2 *upper, int *counts,
+            uint32_t *mask, unsigned long long *state, int ntiles, int2 *cand, int *ccnt,
+            unsigned *status)
 {
-    __shared__ int s_tile;
-    __shared__ int s_wc[CPT * WPB];
+    __shared__ int s_tile, s_cnt;
+    __shared__ int s_wc[WPB + 1];
     __shared__ long long s_prefix;
+    __shared__ typename std::conditional<FILTER, FilterSmem, int>::type fs;
     if (threadIdx.x == 0)
         s_tile = (int)atomicAdd(state, 1ull);
     __syncthreads();
     const int tile = s_tile;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-
-    int2 e[CPT];
-    unsigned bal[CPT];
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-        const int c = tile * TILE + k * CT + threadIdx.x;  // 0-based column
-        const bool inr = c < p;
-        bool valid;
-        if constexpr (FROM_PART) {
-            uint32_t lo = 0xFFFFu, hi = 0;
-            if (inr) {
-                const uint32_t *q = part + c;
-                int j = 0;
-                for (; j + 4 <= copies; j += 4) {
-                    uint32_t a0 = __ldcg(q + (size_t)(j + 0) * p), a1 = __ldcg(q + (size_t)(j + 1) * p);
-                    uint32_t a2 = __ldcg(q + (size_t)(j + 2) * p), a3 = __ldcg(q + (size_t)(j + 3) * p);
-                    lo = min(min(lo, a0 >> 16), min(a1 >> 16, min(a2 >> 16, a3 >> 16)));
-                    hi = max(max(hi, a0 & 0xFFFFu), max(a1 & 0xFFFFu, max(a2 & 0xFFFFu, a3 & 0xFFFFu)));
-                }
-                for (; j < copies; ++j) {
-                    uint32_t a = __ldcg(q + (size_t)j * p);
-                    lo = min(lo, a >> 16);
-                    hi = max(hi, a & 0xFFFFu);
-                }
-            }
-            valid = inr && lo <= hi;
-            e[k] = valid ? make_int2((int)lo + 1, (int)hi + 1) : make_int2(p + 1, -1);
-            if (inr && Lout)
-                Lout[c] = e[k];
-        } else {
-            e[k] = inr ? Lin[c] : make_int2(p + 1, -1);
-            valid = inr && !(e[k].x == p + 1 && e[k].y == -1);
-        }
-        bal[k] = __ballot_sync(0xFFFFFFFFu, valid);
-        if (lane == 0) {
-            s_wc[k * WPB + w] = __popc(bal[k]);
-            if (mask && c < p)
-                mask[c >> 5] = bal[k];
-        }
+    const int c = tile * TILE + threadIdx.x;  // 0-based column
+    const int2 e = c < p ? L[c] : make_int2(p + 1, -1);
+    const bool valid = c < p && !(e.x == p + 1 && e.y == -1);
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, valid);
+    if (lane == 0) {
+        s_wc[w] = __popc(bal);
+        if (mask && c < p)
+            mask[c >> 5] = bal;
     }
     __syncthreads();
     if (w == 0) {
-        int v = s_wc[lane];
+        const int v = s_wc[lane];
         int incl = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
             if (lane >= o)
                 incl += t;
         }
         s_wc[lane] = incl - v;
         const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        const long long pre = warp_look_back(state + 1, tile, total, lane, status);
         if (lane == 0) {
-            long long pre = look_back(state + 1, tile, total, status);
             s_prefix = pre;
+            s_cnt = total;
             if (tile == ntiles - 1) {
                 counts[0] = (int)(pre + total);
                 counts[1] = (int)(pre + total);
@@ -134,15 +153,28 @@ __global__ void __launch_bounds__(CT)
         }
     }
     __syncthreads();
-    const long long pre = s_prefix;
-    const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-        if ((bal[k] >> lane) & 1u) {
-            const int c = tile * TILE + k * CT + threadIdx.x;
-            const long long pos = pre + s_wc[k * WPB + w] + __popc(bal[k] & lt);
-            lower[pos] = make_int2(c + 1, e[k].x);
-            upper[pos] = make_int2(c + 1, e[k].y);
+    const int r = s_wc[w] + __popc(bal & ((1u << lane) - 1u));  // rank within the tile
+    if (valid) {
+        const long long pos = s_prefix + r;
+        lower[pos] = make_int2(c + 1, e.x);
+        upper[pos] = make_int2(c + 1, e.y);
+    }
+    if constexpr (FILTER) {
+        const int cnt = s_cnt;
+        if (valid) {
+            fs.P[0][r] = make_int2(c + 1, e.x);
+            fs.P[1][r] = make_int2(c + 1, -e.y);
+        }
+        __syncthreads();
+        build_min_tree(fs.P[0], fs.M[0], cnt);
+        build_min_tree(fs.P[1], fs.M[1], cnt);
+        const bool k0 = run_keeps(fs.P[0], fs.M[0], cnt, threadIdx.x);
+        const bool k1 = run_keeps(fs.P[1], fs.M[1], cnt, threadIdx.x);
+        const int n0 = compact_run(fs.P[0], k0, cand + (size_t)tile * TILE, s_wc);
+        const int n1 = compact_run(fs.P[1], k1, cand + ((size_t)ntiles + tile) * TILE, s_wc);
+        if (threadIdx.x == 0) {
+            ccnt[tile] = n0;
+            ccnt[ntiles + tile] = n1;
         }
     }
 }
@@ -153,26 +185,27 @@ int chain_tiles(int p) { return (p + TILE - 1) / TILE; }
 
 size_t chain_state_bytes(int p) { return (size_t)(chain_tiles(p) + 1) * 8; }
 
-cudaError_t chain_launch(const int32_t *L_in, const uint32_t *partials, int copies, int p,
-                         int32_t *L_out, int32_t *lower, int32_t *upper, int32_t *counts,
-                         uint32_t *mask, void *state, unsigned *status, cudaStream_t s)
+cudaError_t chain_launch(const int32_t *L, int p, int32_t *lower, int32_t *upper, int32_t *counts,
+                         uint32_t *mask, void *state, bool state_zeroed, int2 *cand, int *ccnt,
+                         unsigned *status, cudaStream_t s)
 {
     const int nt = chain_tiles(p);
-    cudaError_t e = cudaMemsetAsync(state, 0, chain_state_bytes(p), s);
-    if (e != cudaSuccess)
-        return e;
+    if (!state_zeroed) {
+        cudaError_t e = cudaMemsetAsync(state, 0, chain_state_bytes(p), s);
+        if (e != cudaSuccess)
+            return e;
+    }
     auto *st = reinterpret_cast<unsigned long long *>(state);
-    if (partials)
-        k_chain<true><<<nt, CT, 0, s>>>(nullptr, partials, copies, p,
-                                        reinterpret_cast<int2 *>(L_out),
-                                        reinterpret_cast<int2 *>(lower),
-                                        reinterpret_cast<int2 *>(upper), counts, mask, st, nt,
-                                        status);
+    if (cand)
+        k_chain<true><<<nt, TILE, 0, s>>>(reinterpret_cast<const int2 *>(L), p,
+                                          reinterpret_cast<int2 *>(lower),
+                                          reinterpret_cast<int2 *>(upper), counts, mask, st, nt,
+                                          cand, ccnt, status);
     else
-        k_chain<false><<<nt, CT, 0, s>>>(reinterpret_cast<const int2 *>(L_in), nullptr, 0, p,
-                                         nullptr, reinterpret_cast<int2 *>(lower),
-                                         reinterpret_cast<int2 *>(upper), counts, mask, st, nt,
-                                         status);
+        k_chain<false><<<nt, TILE, 0, s>>>(reinterpret_cast<const int2 *>(L), p,
+                                           reinterpret_cast<int2 *>(lower),
+                                           reinterpret_cast<int2 *>(upper), counts, mask, st, nt,
+                                           nullptr, nullptr, status);
     return cudaGetLastError();
 }
 

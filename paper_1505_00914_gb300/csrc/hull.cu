@@ -6,64 +6,41 @@
 // hull of the input.  The upper chain is mirrored (y -> -y) so that one
 // lower-hull routine serves both.
 //
-// Parallel monotone chain:
-//   k_hull_seg   - every thread runs Andrew's scan (pop while the turn is not
-//                  strictly counter-clockwise, int64 orientation) over a
-//                  segment of 32 consecutive chain points.  A point that is
-//                  not a strict vertex of its segment's hull lies on or above
-//                  a segment between two other points, so it is not a strict
-//                  vertex of the whole hull either: dropping it is exact.
-//   k_hull_final - one CTA merges adjacent segment hulls pairwise, level by
-//                  level.  Two x-separated lower hulls A (left) and B (right)
-//                  merge into A[0..u] ++ B[v..] where (a_u, b_v) is their
-//                  bridge; a warp finds it by a 32-way search over A, each
-//                  lane locating the tangent from its a_i to B by binary
-//                  search.  Ties are resolved towards the strict hull: the
-//                  tangent takes the farthest of collinear B points, the
-//                  bridge the leftmost of collinear A points.
+// k_hull_filter - per block of 1024 consecutive chain points (in shared
+//                 memory), one thread per point i drops the point when it lies
+//                 on or above the segment between two other points of the
+//                 block, one on each side: the lowest points of the sibling
+//                 sub-blocks of i at every level of a binary min-tree, and the
+//                 points at distances d, e in {s, 2s}, s = 1, 2, 4, ...  Such a
+//                 point is a convex combination of two input points, so it is
+//                 not a strict vertex of the hull and every drop is exact; on
+//                 chains of real data nearly all non-vertices go.  Survivors
+//                 of each block are compacted in order.
+// k_hull_final  - one CTA gathers the survivors, runs Andrew's scan (pop while
+//                 the turn is not strictly counter-clockwise, int64
+//                 orientation) over runs of 16 of them per thread, merges the
+//                 run hulls pairwise, level by level, and stitches the result.
+// A merge of two x-separated lower hulls A (left) and B (right) happens in
+// place, B's survivors moving left to follow A's.  Small pairs are merged by
+// one thread continuing Andrew's scan over B; large pairs by a warp that
+// finds the bridge (a_u, b_v) - the result being A[0..u] ++ B[v..] - with a
+// 32-way search over A, each lane locating the tangent from its a_i to B by
+// binary search.  Ties resolve towards the strict hull: the tangent takes the
+// farthest of collinear B points, the bridge the leftmost of collinear A
+// points.
 #include "ch_internal.cuh"
+#include "hull_filter.cuh"
 
 namespace ch {
 namespace {
 
-constexpr int HS = 32;    // chain points per segment
-constexpr int HT = 128;   // threads per CTA of the segment kernel
-constexpr int FT = 1024;  // threads of the final CTA
-constexpr int PCAP = 6144;  // points per shared-memory buffer (two buffers)
-constexpr int SCAP = 4096;  // segments per shared-memory index array (six arrays)
-constexpr size_t FINAL_SMEM = 2 * PCAP * sizeof(int2) + 6 * SCAP * sizeof(int);
-
-__global__ void __launch_bounds__(HT)
-    k_hull_seg(const int2 *__restrict__ lower, const int2 *__restrict__ upper,
-               const int *__restrict__ counts, int p, int nsegmax, int2 *cand, int *segcnt)
-{
-    __shared__ int2 stk[HS][HT];
-    const int gid = blockIdx.x * HT + threadIdx.x;
-    if (gid >= 2 * nsegmax)
-        return;
-    const int chain = gid >= nsegmax;
-    const int seg = gid - chain * nsegmax;
-    const int m = max(0, min(counts[chain], p));
-    const int b = seg * HS;
-    if (b >= m)
-        return;
-    const int e = min(m, b + HS);
-    const int2 *src = chain ? upper : lower;
-    const int sg = chain ? -1 : 1;
-    int top = 0;
-    for (int i = b; i < e; ++i) {
-        int2 q = src[i];
-        q.y *= sg;
-        while (top >= 2 && cross3(stk[top - 2][threadIdx.x], stk[top - 1][threadIdx.x], q) <= 0)
-            --top;
-        stk[top][threadIdx.x] = q;
-        ++top;
-    }
-    int2 *out = cand + (size_t)gid * HS;
-    for (int k = 0; k < top; ++k)
-        out[k] = stk[k][threadIdx.x];
-    segcnt[gid] = top;
-}
+constexpr int HS = 16;        // points per thread run of the merge fallback
+constexpr int SMALL = 32;     // pairs with na + nb <= SMALL merge on one thread
+constexpr int FT = 1024;      // threads of the final CTA
+constexpr int PCAP = 8192;    // survivors held in shared memory by the final CTA
+constexpr int PEEL_MAX = 24;  // peeling rounds before the merge fallback
+constexpr size_t FINAL_SMEM =
+    2 * PCAP * sizeof(int2) + PCAP * sizeof(int) + 4 * (PCAP / HS + 2) * sizeof(int);
 
 // Index of the tangent point from a (left of every point of B) to the lower
 // hull B: the vertex of least slope, the farthest one on ties.
@@ -71,7 +48,7 @@ __device__ __forceinline__ int tangent(const int2 *B, int nb, int2 a)
 {
     int lo = 0, hi = nb - 1;
     while (lo < hi) {
-        int mid = (lo + hi) >> 1;
+        const int mid = (lo + hi) >> 1;
         if (cross3(a, B[mid], B[mid + 1]) <= 0)
             lo = mid + 1;
         else
@@ -83,8 +60,7 @@ __device__ __forceinline__ int tangent(const int2 *B, int nb, int2 a)
 // Bridge (u, v) of lower hulls A (left) and B (right); called by a full warp.
 // u is the first i for which a_{i+1} is not strictly below the line from a_i
 // to its tangent point on B.
-__device__ void warp_bridge(const int2 *A, int na, const int2 *B, int nb, int lane, int &u,
-                            int &v)
+__device__ void warp_bridge(const int2 *A, int na, const int2 *B, int nb, int lane, int &u, int &v)
 {
     int lo = 0, hi = na - 1;
     while (lo < hi) {
@@ -111,11 +87,35 @@ __device__ void warp_bridge(const int2 *A, int na, const int2 *B, int nb, int la
     v = tangent(B, nb, A[u]);
 }
 
+// One thread: continue Andrew's scan of the hull at D[a..a+na) over the hull
+// at D[b..b+nb) (b >= a + na), in place.  Returns the merged length.
+__device__ int thread_merge(int2 *D, int a, int na, int b, int nb)
+{
+    int top = na;
+    int2 t1 = D[a + top - 1];
+    int2 t0 = top >= 2 ? D[a + top - 2] : t1;
+    for (int k = 0; k < nb; ++k) {
+        const int2 q = D[b + k];
+        while (top >= 2 && cross3(t0, t1, q) <= 0) {
+            --top;
+            t1 = t0;
+            if (top >= 2)
+                t0 = D[a + top - 2];
+        }
+        D[a + top] = q;
+        ++top;
+        t0 = t1;
+        t1 = q;
+    }
+    return top;
+}
+
 // In-place exclusive scan of a[0..n) by the whole CTA; returns the total.
+template <int NT>
 __device__ int block_excl_scan(int *a, int n, int *s_warp, int *s_total)
 {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int per = (n + FT - 1) / FT;
+    const int per = (n + NT - 1) / NT;
     const int b = min(n, t * per), e = min(n, b + per);
     int sum = 0;
     for (int i = b; i < e; ++i)
@@ -123,7 +123,7 @@ __device__ int block_excl_scan(int *a, int n, int *s_warp, int *s_total)
     int incl = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        const int x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
         if (lane >= o)
             incl += x;
     }
@@ -131,21 +131,23 @@ __device__ int block_excl_scan(int *a, int n, int *s_warp, int *s_total)
         s_warp[w] = incl;
     __syncthreads();
     if (w == 0) {
-        int v = s_warp[lane], inc = v;
+        const int v = lane < NT / 32 ? s_warp[lane] : 0;
+        int inc = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int x = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            const int x = __shfl_up_sync(0xFFFFFFFFu, inc, o);
             if (lane >= o)
                 inc += x;
         }
-        s_warp[lane] = inc - v;
+        if (lane < NT / 32)
+            s_warp[lane] = inc - v;
         if (lane == 31)
             *s_total = inc;
     }
     __syncthreads();
     int run = s_warp[w] + incl - sum;
     for (int i = b; i < e; ++i) {
-        int v = a[i];
+        const int v = a[i];
         a[i] = run;
         run += v;
     }
@@ -154,109 +156,233 @@ __device__ int block_excl_scan(int *a, int n, int *s_warp, int *s_total)
     return total;
 }
 
-__global__ void __launch_bounds__(FT, 1)
-    k_hull_final(const int2 *__restrict__ cand, const int *__restrict__ segcnt,
-                 const int *__restrict__ counts, int p, int nsegmax, int2 *gA, int2 *gB,
-                 int *gseg, int2 *hull, int *hull_count)
+// In-place pairwise merge tree.  Segments [0, c0) belong to chain 0 and
+// [c0, c0 + c1) to chain 1; segment s is D[S[s] .. S[s] + L[s]), and each
+// segment starts at or after the end of the previous one.  On return the
+// index arrays (swapped as needed) describe one hull per non-empty chain.
+struct Tree {
+    int2 *D;
+    int *S, *L, *S2, *L2;
+    int c0, c1;
+};
+
+template <int NT>
+__device__ void merge_tree(Tree &t)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    while (t.c0 > 1 || t.c1 > 1) {
+        const int d0 = (t.c0 + 1) >> 1, d1 = (t.c1 + 1) >> 1, nd = d0 + d1;
+        // small pairs and carries: one thread each
+        for (int j = threadIdx.x; j < nd; j += NT) {
+            const int chain = j >= d0;
+            const int jj = j - (chain ? d0 : 0);
+            const int cc = chain ? t.c1 : t.c0;
+            const int ia = (chain ? t.c0 : 0) + 2 * jj, ib = ia + 1;
+            const int la = t.L[ia];
+            if (2 * jj + 1 >= cc) {
+                t.S2[j] = t.S[ia];
+                t.L2[j] = la;
+            } else if (la + t.L[ib] <= SMALL) {
+                t.S2[j] = t.S[ia];
+                t.L2[j] = thread_merge(t.D, t.S[ia], la, t.S[ib], t.L[ib]);
+            }
+        }
+        // large pairs: one warp each
+        for (int j = warp; j < nd; j += NT / 32) {
+            const int chain = j >= d0;
+            const int jj = j - (chain ? d0 : 0);
+            const int cc = chain ? t.c1 : t.c0;
+            const int ia = (chain ? t.c0 : 0) + 2 * jj, ib = ia + 1;
+            if (2 * jj + 1 >= cc || t.L[ia] + t.L[ib] <= SMALL)
+                continue;
+            const int sa = t.S[ia], sb = t.S[ib], lb = t.L[ib];
+            int u, v;
+            warp_bridge(t.D + sa, t.L[ia], t.D + sb, lb, lane, u, v);
+            const int cnt = lb - v;
+            int2 *dst = t.D + sa + u + 1;
+            const int2 *src = t.D + sb + v;
+            for (int k0 = 0; k0 < cnt; k0 += 32) {
+                const int k = k0 + lane;
+                int2 q;
+                if (k < cnt)
+                    q = src[k];
+                __syncwarp();
+                if (k < cnt)
+                    dst[k] = q;
+                __syncwarp();
+            }
+            if (lane == 0) {
+                t.S2[j] = sa;
+                t.L2[j] = u + 1 + cnt;
+            }
+        }
+        __syncthreads();
+        int *x = t.S;
+        t.S = t.S2;
+        t.S2 = x;
+        x = t.L;
+        t.L = t.L2;
+        t.L2 = x;
+        t.c0 = d0;
+        t.c1 = d1;
+    }
+}
+
+// Survivors of chain run b (RUN consecutive chain points) of chain c.
+__global__ void __launch_bounds__(RUN)
+    k_hull_filter(const int2 *__restrict__ lower, const int2 *__restrict__ upper,
+                  const int *__restrict__ counts, int p, int nblk, int2 *cand, int *ccnt)
+{
+    __shared__ int2 P[RUN];
+    __shared__ short M[2 * RUN];
+    __shared__ int s_wc[RUN / 32 + 1];
+    const int chain = blockIdx.x >= nblk;
+    const int blk = blockIdx.x - chain * nblk;
+    const int m = max(0, min(counts[chain], p));
+    const int b0 = blk * RUN;
+    const int nin = max(0, min(RUN, m - b0));
+    if (threadIdx.x < nin) {
+        int2 q = (chain ? upper : lower)[b0 + threadIdx.x];
+        q.y = chain ? -q.y : q.y;
+        P[threadIdx.x] = q;
+    }
+    __syncthreads();
+    build_min_tree(P, M, nin);
+    const bool keep = run_keeps(P, M, nin, threadIdx.x);
+    const int n = compact_run(P, keep, cand + (size_t)blockIdx.x * RUN, s_wc);
+    if (threadIdx.x == 0)
+        ccnt[blockIdx.x] = n;
+}
+
+// True when point i of the chain stored at D[cs..ce) lies on or above a
+// segment between two of its neighbours (at most two places away).
+__device__ __forceinline__ bool peel_drops(const int2 *D, int cs, int ce, int i)
+{
+    if (i - 1 < cs || i + 1 >= ce)
+        return false;
+    const int2 q = D[i], l1 = D[i - 1], r1 = D[i + 1];
+    if (cross3(l1, r1, q) >= 0)
+        return true;
+    const bool l2 = i - 2 >= cs, r2 = i + 2 < ce;
+    const int2 a2 = l2 ? D[i - 2] : l1, b2 = r2 ? D[i + 2] : r1;
+    return (r2 && cross3(l1, b2, q) >= 0) || (l2 && cross3(a2, r1, q) >= 0) ||
+           (l2 && r2 && cross3(a2, b2, q) >= 0);
+}
+
+// The final CTA.  Gathers the survivors of every run (chain 0 first), peels
+// them - dropping, round after round, every point that lies on or above a
+// segment between its current neighbours - until a round drops nothing: an
+// x-monotone chain that turns strictly counter-clockwise at every point is
+// its own strict lower hull.  If PEEL_MAX rounds do not get there, the rest
+// goes through runs of HS points and the pairwise merge tree.  Then stitches.
+template <bool SM>
+__device__ __forceinline__ void final_body(const int2 *__restrict__ cand, const int *__restrict__ ccnt,
+                                           const int *offs, int nblk, int T0, int T, int2 *gA,
+                                           int2 *gB, int *gF, int *gix, int2 *hull, int *hull_count,
+                                           int *s_warp, int *s_total)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_warp[32];
-    __shared__ int s_total;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    int2 *A = SM ? reinterpret_cast<int2 *>(smem) : gA;
+    int2 *B = SM ? reinterpret_cast<int2 *>(smem) + PCAP : gB;
+    int *F = SM ? reinterpret_cast<int *>(reinterpret_cast<int2 *>(smem) + 2 * PCAP) : gF;
+    int *ix = SM ? reinterpret_cast<int *>(reinterpret_cast<int2 *>(smem) + 2 * PCAP) + PCAP : gix;
 
-    const int m0 = max(0, min(counts[0], p)), m1 = max(0, min(counts[1], p));
-    const int n0 = (m0 + HS - 1) / HS, n1 = (m1 + HS - 1) / HS, ns = n0 + n1;
-
-    int *ix[6];
-    const bool seg_smem = ns <= SCAP;
-    for (int r = 0; r < 6; ++r)
-        ix[r] = seg_smem ? reinterpret_cast<int *>(smem + 2 * PCAP * sizeof(int2)) + r * SCAP
-                         : gseg + (size_t)r * 2 * nsegmax;
-    int *segS = ix[0], *segL = ix[1], *nS = ix[2], *nL = ix[3], *U = ix[4], *V = ix[5];
-
-    for (int s = t; s < ns; s += FT) {
-        const int chain = s >= n0, seg = s - (chain ? n0 : 0);
-        const int len = segcnt[chain * nsegmax + seg];
-        segL[s] = len;
-        segS[s] = len;
-    }
-    __syncthreads();
-    const int total = block_excl_scan(segS, ns, s_warp, &s_total);
-    const bool pt_smem = total <= PCAP;
-    int2 *A = pt_smem ? reinterpret_cast<int2 *>(smem) : gA;
-    int2 *B = pt_smem ? reinterpret_cast<int2 *>(smem) + PCAP : gB;
-
-    for (int idx = t; idx < ns * HS; idx += FT) {
-        const int s = idx / HS, k = idx - s * HS;
-        if (k < segL[s]) {
-            const int chain = s >= n0, seg = s - (chain ? n0 : 0);
-            A[segS[s] + k] = cand[((size_t)chain * nsegmax + seg) * HS + k];
+    // gather
+    for (int s = warp; s < 2 * nblk; s += FT / 32) {
+        const int2 *src = cand + (size_t)s * RUN;
+        const int len = ccnt[s], st = offs[s];
+        for (int k0 = 0; k0 < len; k0 += 128) {
+            int2 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (k0 + u * 32 + lane < len)
+                    q[u] = src[k0 + u * 32 + lane];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (k0 + u * 32 + lane < len)
+                    A[st + k0 + u * 32 + lane] = q[u];
         }
     }
     __syncthreads();
 
-    int c0 = n0, c1 = n1;
-    while (c0 > 1 || c1 > 1) {
-        const int d0 = (c0 + 1) >> 1, d1 = (c1 + 1) >> 1, nd = d0 + d1;
-        for (int j = warp; j < nd; j += FT / 32) {
-            const int chain = j >= d0;
-            const int jj = j - (chain ? d0 : 0);
-            const int cc = chain ? c1 : c0;
-            const int ia = (chain ? c0 : 0) + 2 * jj, ib = ia + 1;
-            if (2 * jj + 1 < cc) {
-                int u, v;
-                warp_bridge(A + segS[ia], segL[ia], A + segS[ib], segL[ib], lane, u, v);
-                if (lane == 0) {
-                    U[j] = u;
-                    V[j] = v;
-                    nL[j] = u + 1 + segL[ib] - v;
-                }
-            } else if (lane == 0) {
-                U[j] = segL[ia] - 1;
-                V[j] = -1;
-                nL[j] = segL[ia];
-            }
+    bool done = false;
+    for (int round = 0; round < PEEL_MAX && !done; ++round) {
+        for (int i = t; i < T; i += FT) {
+            const bool c1 = i >= T0;
+            F[i] = peel_drops(A, c1 ? T0 : 0, c1 ? T : T0, i) ? 0 : 1;
         }
         __syncthreads();
-        for (int j = t; j < nd; j += FT)
-            nS[j] = nL[j];
-        __syncthreads();
-        block_excl_scan(nS, nd, s_warp, &s_total);
-        for (int j = warp; j < nd; j += FT / 32) {
-            const int chain = j >= d0;
-            const int jj = j - (chain ? d0 : 0);
-            const int ia = (chain ? c0 : 0) + 2 * jj, ib = ia + 1;
-            const int u = U[j], v = V[j];
-            int2 *dst = B + nS[j];
-            const int2 *sa = A + segS[ia];
-            for (int k = lane; k <= u; k += 32)
-                dst[k] = sa[k];
-            if (v >= 0) {
-                const int2 *sb = A + segS[ib];
-                const int lb = segL[ib];
-                for (int k = v + lane; k < lb; k += 32)
-                    dst[u + 1 + k - v] = sb[k];
-            }
+        const int kept = block_excl_scan<FT>(F, T, s_warp, s_total);
+        if (kept == T) {
+            done = true;  // block-uniform
+            break;
         }
+        for (int i = t; i < T; i += FT) {
+            const int next = i + 1 < T ? F[i + 1] : kept;
+            if (next != F[i])
+                B[F[i]] = A[i];
+        }
+        const int nT0 = T0 < T ? F[T0] : kept;
         __syncthreads();
-        int2 *tp = A;
+        int2 *x = A;
         A = B;
-        B = tp;
-        int *ti = segS;
-        segS = nS;
-        nS = ti;
-        ti = segL;
-        segL = nL;
-        nL = ti;
-        c0 = d0;
-        c1 = d1;
+        B = x;
+        T = kept;
+        T0 = nT0;
+    }
+
+    int hl, hu;
+    const int2 *LH, *UH;
+    if (done) {
+        hl = T0;
+        hu = T - T0;
+        LH = A;
+        UH = A + T0;
+    } else {
+        // fallback: Andrew's scan over runs of HS points, then the merge tree
+        const int T1 = T - T0;
+        const int r0 = (T0 + HS - 1) / HS, r1 = (T1 + HS - 1) / HS, nr = r0 + r1;
+        for (int r = t; r < nr; r += FT) {
+            const bool c1 = r >= r0;
+            const int st = c1 ? T0 + (r - r0) * HS : r * HS;
+            const int cnt = min(HS, (c1 ? T : T0) - st);
+            int top = 0;
+            int2 a0 = make_int2(0, 0), a1 = make_int2(0, 0);
+            for (int i = 0; i < cnt; ++i) {
+                const int2 q = A[st + i];
+                while (top >= 2 && cross3(a0, a1, q) <= 0) {
+                    --top;
+                    a1 = a0;
+                    if (top >= 2)
+                        a0 = A[st + top - 2];
+                }
+                A[st + top] = q;
+                ++top;
+                a0 = a1;
+                a1 = q;
+            }
+            ix[r] = st;
+            ix[nr + r] = top;
+        }
+        __syncthreads();
+        Tree tr;
+        tr.D = A;
+        tr.S = ix;
+        tr.L = ix + nr;
+        tr.S2 = ix + 2 * nr;
+        tr.L2 = ix + 3 * nr;
+        tr.c0 = r0;
+        tr.c1 = r1;
+        merge_tree<FT>(tr);
+        hl = tr.c0 ? tr.L[0] : 0;
+        hu = tr.c1 ? tr.L[tr.c0] : 0;
+        LH = A + (tr.c0 ? tr.S[0] : 0);
+        UH = A + (tr.c1 ? tr.S[tr.c0] : 0);
     }
 
     // Stitch: lower hull left to right, then the upper hull right to left,
     // without repeating the shared end points.
-    const int hl = c0 ? segL[0] : 0, hu = c1 ? segL[c0] : 0;
-    const int2 *LH = A + (c0 ? segS[0] : 0);
-    const int2 *UH = A + (c1 ? segS[c0] : 0);
     int kl = hu - 1, kf = 0;
     if (hl > 0 && hu > 0) {
         const int2 ul = UH[hu - 1], ll = LH[hl - 1];
@@ -277,54 +403,103 @@ __global__ void __launch_bounds__(FT, 1)
         *hull_count = hl + nup;
 }
 
-struct HullWs {
-    size_t cand, segcnt, gA, gB, gseg, end;
-};
-
-HullWs hull_layout(int p)
+__global__ void __launch_bounds__(FT, 1)
+    k_hull_final(const int2 *__restrict__ cand, const int *__restrict__ ccnt, int nblk, int2 *gA,
+                 int2 *gB, int *gF, int *gix, int2 *hull, int *hull_count)
 {
-    const size_t nsegmax = ((size_t)p + HS - 1) / HS;
+    __shared__ int s_warp[32];
+    __shared__ int s_total, s_t0;
+    __shared__ int s_offs[2 * 128 + 1];
+    const int t = threadIdx.x, nb = 2 * nblk;
+    int *offs = nb <= 2 * 128 ? s_offs : gix;  // global scratch reused before the fallback
+    for (int s = t; s < nb; s += FT)
+        offs[s] = ccnt[s];
+    __syncthreads();
+    const int total = block_excl_scan<FT>(offs, nb, s_warp, &s_total);
+    if (t == 0)
+        s_t0 = offs[nblk];
+    __syncthreads();
+    const int T0 = s_t0;
+    if (total <= PCAP)
+        final_body<true>(cand, ccnt, offs, nblk, T0, total, gA, gB, gF, gix + nb + 1, hull,
+                         hull_count, s_warp, &s_total);
+    else
+        final_body<false>(cand, ccnt, offs, nblk, T0, total, gA, gB, gF, gix + nb + 1, hull,
+                          hull_count, s_warp, &s_total);
+}
+
+}  // namespace
+
+HullLayout hull_layout(int p)
+{
+    const size_t nblk = ((size_t)p + RUN - 1) / RUN;
+    const size_t cap = 2 * nblk * RUN;  // survivors of both chains, at most
     WsLayout w;
-    HullWs h;
-    h.cand = w.take(2 * nsegmax * HS * sizeof(int2));
-    h.segcnt = w.take(2 * nsegmax * sizeof(int));
-    h.gA = w.take(2 * nsegmax * HS * sizeof(int2));
-    h.gB = w.take(2 * nsegmax * HS * sizeof(int2));
-    h.gseg = w.take(6 * 2 * nsegmax * sizeof(int));
+    HullLayout h;
+    h.nblk = (int)nblk;
+    h.cand = w.take(cap * sizeof(int2));
+    h.ccnt = w.take(2 * nblk * sizeof(int));
+    h.gA = w.take(cap * sizeof(int2));
+    h.gB = w.take(cap * sizeof(int2));
+    h.gF = w.take(cap * sizeof(int));
+    h.gix = w.take((2 * nblk + 1 + 4 * (cap / HS + 2)) * sizeof(int));
     h.end = w.off;
     return h;
+}
+
+namespace {
+
+cudaError_t set_attrs()
+{
+    static bool attrs_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64)
+        return cudaErrorInvalidDevice;
+    if (!attrs_set[dev]) {
+        cudaError_t a = cudaFuncSetAttribute(k_hull_final, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)FINAL_SMEM);
+        if (a != cudaSuccess)
+            return a;
+        attrs_set[dev] = true;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
 
 size_t hull_ws_bytes(int p) { return hull_layout(p).end; }
 
+cudaError_t hull_final_launch(const HullLayout &h, void *ws, int32_t *hull, int32_t *hull_count,
+                              cudaStream_t s)
+{
+    cudaError_t e = set_attrs();
+    if (e != cudaSuccess)
+        return e;
+    char *b = reinterpret_cast<char *>(ws);
+    k_hull_final<<<1, FT, FINAL_SMEM, s>>>(
+        reinterpret_cast<const int2 *>(b + h.cand), reinterpret_cast<const int *>(b + h.ccnt), h.nblk,
+        reinterpret_cast<int2 *>(b + h.gA), reinterpret_cast<int2 *>(b + h.gB),
+        reinterpret_cast<int *>(b + h.gF), reinterpret_cast<int *>(b + h.gix),
+        reinterpret_cast<int2 *>(hull), hull_count);
+    return cudaGetLastError();
+}
+
 cudaError_t hull_launch(const int32_t *lower, const int32_t *upper, const int32_t *counts, int p,
                         int32_t *hull, int32_t *hull_count, void *ws, unsigned *status,
                         cudaStream_t s)
 {
     (void)status;
-    const HullWs h = hull_layout(p);
-    const int nsegmax = (p + HS - 1) / HS;
+    const HullLayout h = hull_layout(p);
     char *b = reinterpret_cast<char *>(ws);
-    int2 *cand = reinterpret_cast<int2 *>(b + h.cand);
-    int *segcnt = reinterpret_cast<int *>(b + h.segcnt);
-    k_hull_seg<<<(2 * nsegmax + HT - 1) / HT, HT, 0, s>>>(
-        reinterpret_cast<const int2 *>(lower), reinterpret_cast<const int2 *>(upper), counts, p,
-        nsegmax, cand, segcnt);
+    k_hull_filter<<<2 * h.nblk, RUN, 0, s>>>(reinterpret_cast<const int2 *>(lower),
+                                             reinterpret_cast<const int2 *>(upper), counts, p,
+                                             h.nblk, reinterpret_cast<int2 *>(b + h.cand),
+                                             reinterpret_cast<int *>(b + h.ccnt));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    e = cudaFuncSetAttribute(k_hull_final, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)FINAL_SMEM);
-    if (e != cudaSuccess)
-        return e;
-    k_hull_final<<<1, FT, FINAL_SMEM, s>>>(cand, segcnt, counts, p, nsegmax,
-                                           reinterpret_cast<int2 *>(b + h.gA),
-                                           reinterpret_cast<int2 *>(b + h.gB),
-                                           reinterpret_cast<int *>(b + h.gseg),
-                                           reinterpret_cast<int2 *>(hull), hull_count);
-    return cudaGetLastError();
+    return hull_final_launch(h, ws, hull, hull_count, s);
 }
 
 }  // namespace ch

@@ -1,180 +1,453 @@
 // Step 1: Algorithm 1 (Reduction of Points, Section 2.1) on sm_103a.
 //
 // Each point (x, y) folds into column x of L as (min(y, ly), max(y, hy)).
-// Min and max commute, so any order of folding gives the same L; the GPU
-// folds in parallel into private copies of L and merges them afterwards.
+// Min and max commute, so the GPU may fold in any order and into any number
+// of partial arrays that are merged column by column afterwards.  Only the
+// native 32-bit shared-memory atomicMin/atomicMax run at streaming speed on
+// GB300 (compare-and-swap and cluster-remote atomics are an order of
+// magnitude slower), which fixes the two forms used here:
 //
-// Private copies live in shared memory as one packed 32-bit word per column
-// (lo16 = min y - 1, hi16 = max y - 1), so p <= 65536 columns need at most
-// 256 KB.  When that exceeds one CTA's shared memory (227 KB on GB300), two
-// CTAs of a thread-block cluster split the x range and fold the other half's
-// points into their partner's shared memory (distributed shared memory).
-// Every fold first reads the column word and only issues a compare-and-swap
-// when y falls outside [lo, hi]: the word only ever widens, so a stale read
-// can only cause a redundant CAS, never a missed update.
+// Private form (8p bytes fit one CTA's shared memory, p <= 29056):
+//   every CTA (one per SM) keeps int32 lo[p], hi[p] in shared memory, folds
+//   its slice of the points with unconditional shared atomics and writes its
+//   copy as one row of a partial array, packed as ((lo-1) << 16) | (hi-1)
+//   (0xFFFF0000 for an empty column); the chain step merges the rows.
 //
-// Each copy ends as one row of a partial array in the workspace; the chain
-// step (or reduce_merge below) combines the rows column by column.
-// p > 65536 uses a global-memory L with the same read-then-atomic rule.
-#include <cooperative_groups.h>
+// Filtered form (larger p): L lives in global memory and every CTA keeps a
+//   16-bit filter per column in shared memory: a row bin (y-1) >> shift for
+//   each of L's two extremes.  Every value a filter ever holds is the row bin
+//   of some input point, so the point(s) with a column's least y always have
+//   a bin <= the filter's lo bin and always pass, and a point whose bin is
+//   strictly above the lo bin cannot be that least y (likewise for the
+//   greatest y).  A point whose bin lies strictly between the two bins is
+//   therefore dropped after one shared load; any other point is folded into
+//   L with a global red.min / red.max and tightens the CTA's filter (plain,
+//   racing byte stores are safe: whichever lands, the value is still some
+//   point's bin).
+//   The filters start warm: k_filter_warm has each CTA build a filter from
+//   the first sixteenth of the slice it will reduce and store it as one row
+//   of a slot array; k_filter_merge folds the rows column-wise into one
+//   filter G (and fills L with (p+1, -1)); k_reduce_filtered starts from G
+//   and folds the whole slice (the warm-up part again, from L2).  About one
+//   point in fifty reaches global memory.
+//   Filters need 2p bytes of shared memory (p <= 116224); beyond that every
+//   point takes a read-then-atomic test against the global L.
+#include <map>
+#include <mutex>
 
 #include "ch_internal.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace ch {
 namespace {
 
-constexpr int RT = 512;  // threads per CTA
-constexpr int RU = 4;    // 16-byte loads in flight per thread per iteration
+constexpr int RU = 4;            // 16-byte loads in flight per thread per iteration
 
-__device__ __forceinline__ void fold(uint32_t *a, uint32_t v)
+// The point array is read as 16-byte pairs of points starting at the first
+// 16-byte boundary; an 8-byte aligned array has its first point handled on its
+// own, and an odd tail likewise.
+struct PairView {
+    const int4 *p4;
+    int64_t npairs;
+    int64_t head;  // 0 or 1 leading point outside the pairs
+    bool tail;     // one trailing point outside the pairs
+};
+
+__device__ __forceinline__ PairView pair_view(const int32_t *pts, int64_t n)
 {
-    uint32_t w = *reinterpret_cast<volatile uint32_t *>(a);
-    uint32_t lo = w >> 16, hi = w & 0xFFFFu;
-    while (v < lo || v > hi) {
-        uint32_t nw = (min(lo, v) << 16) | max(hi, v);
-        uint32_t prev = atomicCAS(a, w, nw);
-        if (prev == w)
-            return;
-        w = prev;
-        lo = w >> 16;
-        hi = w & 0xFFFFu;
-    }
+    PairView v;
+    v.head = (((uintptr_t)pts & 15) != 0 && n > 0) ? 1 : 0;
+    v.npairs = (n - v.head) >> 1;
+    v.tail = ((n - v.head) & 1) != 0;
+    v.p4 = reinterpret_cast<const int4 *>(pts + 2 * v.head);
+    return v;
 }
 
-template <int CL>
-__global__ void __launch_bounds__(RT, 1)
-    k_reduce_packed(const int32_t *__restrict__ pts, int64_t n, int p, int cols,
-                    uint32_t *__restrict__ part, unsigned *status)
+// ---------------------------------------------------------------- private
+template <int RT>
+__global__ void __launch_bounds__(RT)
+    k_reduce_private(const int32_t *__restrict__ pts, int64_t n, int p,
+                     uint32_t *__restrict__ part, unsigned *status)
 {
-    extern __shared__ __align__(16) uint32_t sL[];
-    for (int i = threadIdx.x; i < cols; i += RT)
-        sL[i] = PACK_EMPTY;
-
-    uint32_t *base0 = sL, *base1 = sL;
-    int rank = 0;
-    if constexpr (CL == 1) {
-        __syncthreads();
-    } else {
-        cg::cluster_group cl = cg::this_cluster();
-        rank = (int)cl.block_rank();
-        cl.sync();  // partner's words initialised before any remote fold
-        base0 = cl.map_shared_rank(sL, 0);
-        base1 = cl.map_shared_rank(sL, 1);
+    extern __shared__ __align__(16) int sI[];
+    int *slo = sI, *shi = sI + p;
+    for (int i = threadIdx.x; i < p; i += RT) {
+        slo[i] = p + 1;
+        shi[i] = -1;
     }
-
-    const uint32_t up = (uint32_t)p, ucols = (uint32_t)cols;
+    __syncthreads();
+    const uint32_t up = (uint32_t)p;
     bool bad = false;
-    auto proc = [&](int x, int y) {
-        uint32_t c = (uint32_t)(x - 1), v = (uint32_t)(y - 1);
-        if (c >= up || v >= up) {
+    auto fold = [&](int x, int y) {
+        const uint32_t c = (uint32_t)(x - 1);
+        if (c >= up || (uint32_t)(y - 1) >= up) {
             bad = true;
             return;
         }
-        uint32_t *a;
-        if constexpr (CL == 1)
-            a = sL + c;
-        else
-            a = c < ucols ? base0 + c : base1 + (c - ucols);
-        fold(a, v);
+        atomicMin(slo + c, y);
+        atomicMax(shi + c, y);
     };
-
-    // 16-byte loads need a 16-byte aligned start; an 8-byte aligned array
-    // has its first point handled on its own, and an odd tail likewise.
-    const int64_t head = (((uintptr_t)pts & 15) != 0 && n > 0) ? 1 : 0;
-    const int64_t npairs = (n - head) >> 1;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && head)
-        proc(pts[0], pts[1]);
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0 && ((n - head) & 1))
-        proc(pts[2 * (n - 1)], pts[2 * (n - 1) + 1]);
-    const int4 *p4 = reinterpret_cast<const int4 *>(pts + 2 * head);
-
-    const int64_t per = (npairs + gridDim.x - 1) / gridDim.x;
+    const PairView pv = pair_view(pts, n);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && pv.head)
+        fold(pts[0], pts[1]);
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0 && pv.tail)
+        fold(pts[2 * (n - 1)], pts[2 * (n - 1) + 1]);
+    const int64_t per = (pv.npairs + gridDim.x - 1) / gridDim.x;
     const int64_t s0 = (int64_t)blockIdx.x * per;
-    const int64_t e0 = min(npairs, s0 + per);
+    const int64_t e0 = min(pv.npairs, s0 + per);
     for (int64_t i = s0 + threadIdx.x; i < e0; i += (int64_t)RT * RU) {
         int4 v[RU];
 #pragma unroll
         for (int u = 0; u < RU; ++u) {
-            int64_t j = i + (int64_t)u * RT;
-            if (j < e0)
-                v[u] = __ldcs(p4 + j);
+            const int64_t j = i + (int64_t)u * RT;
+            v[u] = j < e0 ? __ldcs(pv.p4 + j) : make_int4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int u = 0; u < RU; ++u) {
-            int64_t j = i + (int64_t)u * RT;
-            if (j < e0) {
-                proc(v[u].x, v[u].y);
-                proc(v[u].z, v[u].w);
+            if (i + (int64_t)u * RT < e0) {
+                fold(v[u].x, v[u].y);
+                fold(v[u].z, v[u].w);
             }
         }
     }
-
-    if constexpr (CL == 1)
-        __syncthreads();
-    else
-        cg::this_cluster().sync();  // every remote fold has landed
-
-    const int copy = blockIdx.x / CL;
-    const int c0 = rank * cols;
-    const int mine = min(cols, p - c0);
-    uint32_t *out = part + (size_t)copy * p + c0;
-    for (int i = threadIdx.x; i < mine; i += RT)
-        out[i] = sL[i];
+    __syncthreads();
+    uint32_t *out = part + (size_t)blockIdx.x * p;
+    for (int i = threadIdx.x; i < p; i += RT)
+        out[i] = slo[i] <= p ? ((uint32_t)(slo[i] - 1) << 16) | (uint32_t)(shi[i] - 1) : 0xFFFF0000u;
     if (__syncthreads_or(bad) && threadIdx.x == 0)
         atomicOr(status, ST_RANGE);
 }
 
+// --------------------------------------------------------------- filtered
 __global__ void k_fill_empty(int2 *L, int p)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p; i += gridDim.x * blockDim.x)
         L[i] = make_int2(p + 1, -1);
 }
 
-// Large-p form: L in global memory (L2-resident for moderate p).
-__global__ void __launch_bounds__(256)
-    k_reduce_global(const int2 *__restrict__ pts, int64_t n, int p, int2 *L, unsigned *status)
+// Read-then-atomic fold of one point into the global L.
+__device__ __forceinline__ bool fold_global(int2 *L, uint32_t up, int x, int y)
 {
+    const uint32_t c = (uint32_t)(x - 1);
+    if (c >= up || (uint32_t)(y - 1) >= up)
+        return false;
+    const int2 e = L[c];
+    if (y < e.x)
+        atomicMin(&L[c].x, y);
+    if (y > e.y)
+        atomicMax(&L[c].y, y);
+    return true;
+}
+
+// Whole input through the read-then-atomic test (p too large for a filter).
+__global__ void __launch_bounds__(256)
+    k_reduce_global(const int32_t *__restrict__ pts, int64_t n, int p, int2 *L, unsigned *status)
+{
+    const PairView pv = pair_view(pts, n);
+    const uint32_t up = (uint32_t)p;
     bool bad = false;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        int2 q = __ldcs(pts + k);
-        uint32_t c = (uint32_t)(q.x - 1), v = (uint32_t)(q.y - 1);
-        if (c >= (uint32_t)p || v >= (uint32_t)p) {
-            bad = true;
-            continue;
-        }
-        volatile int *e = reinterpret_cast<volatile int *>(L + c);
-        if (q.y < e[0])
-            atomicMin(&L[c].x, q.y);
-        if (q.y > e[1])
-            atomicMax(&L[c].y, q.y);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < pv.npairs;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int4 v = __ldcs(pv.p4 + j);
+        bad |= !fold_global(L, up, v.x, v.y);
+        bad |= !fold_global(L, up, v.z, v.w);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (pv.head)
+            bad |= !fold_global(L, up, pts[0], pts[1]);
+        if (pv.tail)
+            bad |= !fold_global(L, up, pts[2 * (n - 1)], pts[2 * (n - 1) + 1]);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0)
         atomicOr(status, ST_RANGE);
 }
 
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ uint32_t bin_of(int y, int shift) { return (uint32_t)(y - 1) >> shift; }
+
+constexpr int WARM_DIV = 16;  // the warm-up reads the first 1/WARM_DIV of each slice
+
+// Slice of point pairs [s0, e0) reduced by CTA `b` of `grid`.
+__device__ __forceinline__ void slice_of(int64_t npairs, int b, int grid, int64_t &s0, int64_t &e0)
+{
+    const int64_t per = (npairs + grid - 1) / grid;
+    s0 = (int64_t)b * per;
+    e0 = min(npairs, s0 + per);
+}
+
+// Filter words are (lo bin << 8) | hi bin; "tighter of" two packed words is
+// a byte-wise min on the lo bytes and max on the hi bytes.
+__device__ __forceinline__ uint32_t tighter2(uint32_t a, uint32_t b)
+{
+    return (__vminu4(a, b) & 0xFF00FF00u) | (__vmaxu4(a, b) & 0x00FF00FFu);
+}
+
+__device__ __forceinline__ uint4 tighter8(uint4 a, uint4 b)
+{
+    return make_uint4(tighter2(a.x, b.x), tighter2(a.y, b.y), tighter2(a.z, b.z), tighter2(a.w, b.w));
+}
+
+template <int RT>
+__global__ void __launch_bounds__(RT)
+    k_filter_warm(const int32_t *__restrict__ pts, int64_t n, int p, int shift, int grid,
+                  uint16_t *__restrict__ slots)
+{
+    extern __shared__ __align__(16) uint16_t F[];
+    unsigned char *fb = reinterpret_cast<unsigned char *>(F);
+    const int words = (p + 7) / 8;
+    uint4 *F4 = reinterpret_cast<uint4 *>(F);
+    for (int i = threadIdx.x; i < words; i += RT)
+        F4[i] = make_uint4(0xFF00FF00u, 0xFF00FF00u, 0xFF00FF00u, 0xFF00FF00u);
+    __syncthreads();
+    const uint32_t up = (uint32_t)p;
+    auto learn = [&](int x, int y) {
+        const uint32_t c = (uint32_t)(x - 1);
+        if (c >= up || (uint32_t)(y - 1) >= up)
+            return;
+        const uint32_t f = F[c], b = bin_of(y, shift);
+        if (b < (f >> 8))
+            fb[2 * c + 1] = (unsigned char)b;
+        if (b > (f & 0xFFu))
+            fb[2 * c] = (unsigned char)b;
+    };
+    const PairView pv = pair_view(pts, n);
+    int64_t s0, e0;
+    slice_of(pv.npairs, blockIdx.x, grid, s0, e0);
+    const int64_t warm = s0 + (e0 - s0) / WARM_DIV;
+    constexpr int WU = 4 * RU;  // short loop: more loads in flight
+    for (int64_t i = s0 + threadIdx.x; i < warm; i += (int64_t)RT * WU) {
+        int4 v[WU];
+#pragma unroll
+        for (int u = 0; u < WU; ++u) {
+            const int64_t j = i + (int64_t)u * RT;
+            v[u] = j < warm ? __ldcg(pv.p4 + j) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < WU; ++u) {
+            learn(v[u].x, v[u].y);
+            learn(v[u].z, v[u].w);
+        }
+    }
+    __syncthreads();
+    uint4 *out = reinterpret_cast<uint4 *>(slots) + (size_t)blockIdx.x * words;
+    for (int i = threadIdx.x; i < words; i += RT)
+        __stcg(out + i, F4[i]);
+}
+
+// G = column-wise tighter-of over the `rows` slot rows; also L = (p+1, -1).
+// A CTA has MG_GROUPS thread groups over the same MG_V uint4 words (8
+// columns each); group g folds rows g, g + MG_GROUPS, ...
+constexpr int MG_V = 32, MG_GROUPS = 32;
+
+__global__ void __launch_bounds__(MG_V *MG_GROUPS)
+    k_filter_merge(const uint16_t *__restrict__ slots, int rows, int p, uint16_t *__restrict__ G,
+                   int2 *__restrict__ L)
+{
+    __shared__ uint4 part[MG_GROUPS][MG_V];
+    const int words = (p + 7) / 8;
+    const int v = threadIdx.x % MG_V, g = threadIdx.x / MG_V;
+    const int i = blockIdx.x * MG_V + v;
+    uint4 acc = make_uint4(0xFF00FF00u, 0xFF00FF00u, 0xFF00FF00u, 0xFF00FF00u);
+    if (i < words) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(slots) + i;
+        int r = g;
+        for (; r + 7 * MG_GROUPS < rows; r += 8 * MG_GROUPS) {
+            uint4 w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                w[u] = __ldcg(s4 + (size_t)(r + u * MG_GROUPS) * words);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                acc = tighter8(acc, w[u]);
+        }
+        for (; r < rows; r += MG_GROUPS)
+            acc = tighter8(acc, __ldcg(s4 + (size_t)r * words));
+    }
+    part[g][v] = acc;
+    __syncthreads();
+    if (g == 0 && i < words) {
+#pragma unroll
+        for (int h = 1; h < MG_GROUPS; ++h)
+            acc = tighter8(acc, part[h][v]);
+        reinterpret_cast<uint4 *>(G)[i] = acc;
+    }
+    const int c0 = blockIdx.x * MG_V * 8;
+    for (int c = c0 + threadIdx.x; c < min(p, c0 + MG_V * 8); c += MG_V * MG_GROUPS)
+        L[c] = make_int2(p + 1, -1);
+}
+
+template <int RT>
+__global__ void __launch_bounds__(RT)
+    k_reduce_filtered(const int32_t *__restrict__ pts, int64_t n, int p, int shift,
+                      const uint16_t *__restrict__ G, int2 *L, unsigned *status)
+{
+    extern __shared__ __align__(16) uint16_t F[];
+    unsigned char *fb = reinterpret_cast<unsigned char *>(F);
+    {
+        const int words = (p + 7) / 8;
+        const uint4 *G4 = reinterpret_cast<const uint4 *>(G);
+        uint4 *F4 = reinterpret_cast<uint4 *>(F);
+        for (int i0 = threadIdx.x; i0 < words; i0 += RT * 8) {
+            uint4 g[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 + u * RT < words)
+                    g[u] = __ldcg(G4 + i0 + u * RT);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 + u * RT < words)
+                    F4[i0 + u * RT] = g[u];
+        }
+    }
+    __syncthreads();
+    const uint32_t up = (uint32_t)p;
+    bool bad = false;
+    auto fold = [&](int x, int y) {
+        const uint32_t c = (uint32_t)(x - 1);
+        if (c >= up || (uint32_t)(y - 1) >= up) {
+            bad = true;
+            return;
+        }
+        const uint32_t f = F[c], b = bin_of(y, shift);
+        const uint32_t qlo = f >> 8, qhi = f & 0xFFu;
+        if (b <= qlo) {
+            atomicMin(&L[c].x, y);
+            if (b < qlo)
+                fb[2 * c + 1] = (unsigned char)b;
+        }
+        if (b >= qhi) {
+            atomicMax(&L[c].y, y);
+            if (b > qhi)
+                fb[2 * c] = (unsigned char)b;
+        }
+    };
+    const PairView pv = pair_view(pts, n);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && pv.head)
+        fold(pts[0], pts[1]);
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0 && pv.tail)
+        fold(pts[2 * (n - 1)], pts[2 * (n - 1) + 1]);
+    int64_t s0, e0;
+    slice_of(pv.npairs, blockIdx.x, gridDim.x, s0, e0);
+    for (int64_t i = s0 + threadIdx.x; i < e0; i += (int64_t)RT * RU) {
+        int4 v[RU];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int64_t j = i + (int64_t)u * RT;
+            v[u] = j < e0 ? __ldcs(pv.p4 + j) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            if (i + (int64_t)u * RT < e0) {
+                fold(v[u].x, v[u].y);
+                fold(v[u].z, v[u].w);
+            }
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0)
+        atomicOr(status, ST_RANGE);
+}
+
+// L = column-wise merge of the packed partial rows.  A CTA covers 32 columns
+// with 32 thread groups; group g folds rows g, g + 32, ... (all loads of a
+// thread in flight together), and the groups combine through shared memory.
+__global__ void __launch_bounds__(1024)
     k_merge_partials(const uint32_t *__restrict__ part, int copies, int p, int2 *L)
 {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < p; c += gridDim.x * blockDim.x) {
-        uint32_t lo = 0xFFFFu, hi = 0;
-        for (int j = 0; j < copies; ++j) {
-            uint32_t w = __ldcg(part + (size_t)j * p + c);
+    __shared__ uint32_t s_lo[32][33], s_hi[32][33];
+    const int v = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + v;
+    uint32_t lo = 0xFFFFu, hi = 0;
+    if (c < p) {
+        int r = g;
+        for (; r + 7 * 32 < copies; r += 8 * 32) {
+            uint32_t w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                w[u] = __ldcg(part + (size_t)(r + u * 32) * p + c);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                lo = min(lo, w[u] >> 16);
+                hi = max(hi, w[u] & 0xFFFFu);
+            }
+        }
+        for (; r < copies; r += 32) {
+            const uint32_t w = __ldcg(part + (size_t)r * p + c);
             lo = min(lo, w >> 16);
             hi = max(hi, w & 0xFFFFu);
+        }
+    }
+    s_lo[g][v] = lo;
+    s_hi[g][v] = hi;
+    __syncthreads();
+    if (g == 0 && c < p) {
+#pragma unroll 8
+        for (int h = 1; h < 32; ++h) {
+            lo = min(lo, s_lo[h][v]);
+            hi = max(hi, s_hi[h][v]);
         }
         L[c] = lo <= hi ? make_int2((int)lo + 1, (int)hi + 1) : make_int2(p + 1, -1);
     }
 }
 
-int optin_smem()
+// Per-device facts the plan needs, computed once: the opt-in shared memory
+// limit, kernel attributes raised to it, and the private kernels' occupancy
+// at each shared-memory size class.
+struct DevInfo {
+    bool ready = false;
+    int optin = 0;
+};
+std::mutex g_dev_mu;
+DevInfo g_dev[64];
+std::map<std::pair<int, size_t>, int> g_bps;  // (device, smem) -> CTAs/SM of the private kernel
+
+int dev_setup(int *dev_out)
 {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return v;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return -1;
+    *dev_out = dev;
+    std::lock_guard<std::mutex> g(g_dev_mu);
+    DevInfo &d = g_dev[dev];
+    if (!d.ready) {
+        if (cudaDeviceGetAttribute(&d.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+            return -1;
+        cudaFuncSetAttribute(k_reduce_private<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             d.optin);
+        cudaFuncSetAttribute(k_reduce_private<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             d.optin);
+        cudaFuncSetAttribute(k_reduce_filtered<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             d.optin);
+        cudaFuncSetAttribute(k_filter_warm<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             d.optin);
+        d.ready = true;
+    }
+    return d.optin;
+}
+
+int private_bps(int dev, int threads, size_t smem)
+{
+    std::lock_guard<std::mutex> g(g_dev_mu);
+    auto key = std::make_pair(dev * 2 + (threads == 1024), smem);
+    auto it = g_bps.find(key);
+    if (it != g_bps.end())
+        return it->second;
+    int bps = 0;
+    cudaError_t e = threads == 512
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_reduce_private<512>,
+                                                                        512, smem)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                              &bps, k_reduce_private<1024>, 1024, smem);
+    if (e != cudaSuccess)
+        return -1;
+    g_bps[key] = bps;
+    return bps;
+}
+
+int filter_shift(int p)
+{
+    int s = 0;
+    while (((p - 1) >> s) > 255)
+        ++s;
+    return s;
 }
 
 }  // namespace
@@ -184,100 +457,76 @@ int reduce_plan(int64_t n, int p, ReducePlan *pl)
     const int sms = sm_count();
     if (sms <= 0)
         return CH_ERR_CUDA;
-    if (p > PACK_MAX_P) {
-        pl->mode = 1;
-        pl->cluster = 1;
-        pl->copies = 0;
-        pl->cols = 0;
-        pl->smem = 0;
-        int64_t want = (n + 255) / 256;
-        pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
-        return CH_OK;
-    }
-    const int optin = optin_smem();
-    pl->mode = 0;
-    pl->cluster = ((size_t)p * 4 <= (size_t)optin) ? 1 : 2;
-    pl->cols = (p + pl->cluster - 1) / pl->cluster;
-    pl->smem = (size_t)pl->cols * 4;
+    int dev = 0;
+    const int optin_i = dev_setup(&dev);
+    if (optin_i <= 0)
+        return CH_ERR_CUDA;
+    const size_t optin = (size_t)optin_i;
     const int64_t npairs = n / 2;
-    // at least ~8K points per CTA so the private copy pays for itself
-    const int64_t want = std::max<int64_t>(1, (npairs + RT * RU * 2 - 1) / (RT * RU * 2));
-    int resident = 0;
-    if (pl->cluster == 1) {
-        cudaFuncSetAttribute(k_reduce_packed<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)pl->smem);
-        int bps = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_reduce_packed<1>, RT, pl->smem) !=
-            cudaSuccess)
+    pl->cluster = 1;
+    if ((size_t)p * 8 <= optin) {
+        pl->mode = 0;  // private copies
+        pl->smem = (size_t)p * 8;
+        pl->threads = 1024;
+        // at least ~16K points per CTA so a private copy pays for its merge
+        const int64_t want = std::max<int64_t>(1, (npairs + 8191) / 8192);
+        const int bps = private_bps(dev, pl->threads, pl->smem);
+        if (bps < 0)
             return CH_ERR_CUDA;
-        resident = std::max(1, bps) * sms;
-        pl->grid = (int)std::min<int64_t>(want, resident);
+        pl->grid = (int)std::min<int64_t>(want, (int64_t)std::max(1, std::min(bps, 1)) * sms);
+        pl->copies = pl->grid;
     } else {
-        cudaFuncSetAttribute(k_reduce_packed<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)pl->smem);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(2 * sms);
-        cfg.blockDim = dim3(RT);
-        cfg.dynamicSmemBytes = pl->smem;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 2;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int nc = 0;
-        if (cudaOccupancyMaxActiveClusters(&nc, k_reduce_packed<2>, &cfg) != cudaSuccess)
-            return CH_ERR_CUDA;
-        nc = std::max(1, nc);
-        int64_t clusters = std::min<int64_t>((want + 1) / 2, nc);
-        pl->grid = (int)std::max<int64_t>(1, clusters) * 2;
+        pl->mode = (size_t)p * 2 <= optin ? 1 : 2;  // filtered / sampled-only
+        pl->threads = 1024;
+        pl->smem = pl->mode == 1 ? (((size_t)p * 2 + 15) & ~size_t(15)) : 0;
+        pl->grid = sms;
+        pl->copies = 0;
+        pl->shift = filter_shift(p);
     }
-    pl->copies = pl->grid / pl->cluster;
     return CH_OK;
 }
 
 size_t reduce_partials_bytes(const ReducePlan &pl, int p)
 {
-    return pl.mode == 0 ? (size_t)pl.copies * (size_t)p * 4 : 0;
+    if (pl.mode == 0)
+        return (size_t)pl.copies * (size_t)p * 4;
+    if (pl.mode == 1)  // merged filter G, then one slot row per CTA
+        return (((size_t)p * 2 + 255) & ~size_t(255)) + (size_t)pl.grid * (((size_t)p + 7) / 8) * 16;
+    return 0;
 }
 
 cudaError_t reduce_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, int p,
-                          uint32_t *part, int32_t *L, unsigned *status, cudaStream_t s)
+                          void *part, int32_t *L, unsigned *status, cudaStream_t s)
 {
-    if (pl.mode == 1) {
-        int2 *L2 = reinterpret_cast<int2 *>(L);
-        k_fill_empty<<<std::min((p + 255) / 256, 4096), 256, 0, s>>>(L2, p);
-        if (n > 0)
-            k_reduce_global<<<pl.grid, 256, 0, s>>>(reinterpret_cast<const int2 *>(pts), n, p, L2,
-                                                   status);
+    if (pl.mode == 0) {
+        uint32_t *pp = reinterpret_cast<uint32_t *>(part);
+        if (pl.threads == 512)
+            k_reduce_private<512><<<pl.grid, 512, pl.smem, s>>>(pts, n, p, pp, status);
+        else
+            k_reduce_private<1024><<<pl.grid, 1024, pl.smem, s>>>(pts, n, p, pp, status);
         return cudaGetLastError();
     }
-    if (pl.cluster == 1) {
-        k_reduce_packed<1><<<pl.grid, RT, pl.smem, s>>>(pts, n, p, pl.cols, part, status);
+    int2 *L2 = reinterpret_cast<int2 *>(L);
+    const int sms = sm_count();
+    if (pl.mode == 2) {
+        k_fill_empty<<<std::max(1, std::min((p + 255) / 256, sms * 4)), 256, 0, s>>>(L2, p);
+        k_reduce_global<<<sms * 8, 256, 0, s>>>(pts, n, p, L2, status);
         return cudaGetLastError();
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(pl.grid);
-    cfg.blockDim = dim3(RT);
-    cfg.dynamicSmemBytes = pl.smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_reduce_packed<2>, pts, n, p, pl.cols, part, status);
+    uint16_t *G = reinterpret_cast<uint16_t *>(part);
+    uint16_t *slots = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(part) +
+                                                   ((((size_t)p * 2) + 255) & ~size_t(255)));
+    k_filter_warm<1024><<<pl.grid, 1024, pl.smem, s>>>(pts, n, p, pl.shift, pl.grid, slots);
+    const int words = (p + 7) / 8;
+    k_filter_merge<<<(words + MG_V - 1) / MG_V, MG_V * MG_GROUPS, 0, s>>>(slots, pl.grid, p, G, L2);
+    k_reduce_filtered<1024><<<pl.grid, 1024, pl.smem, s>>>(pts, n, p, pl.shift, G, L2, status);
+    return cudaGetLastError();
 }
 
-cudaError_t reduce_merge_launch(const uint32_t *part, int copies, int p, int32_t *L,
-                                cudaStream_t s)
+cudaError_t reduce_merge_launch(const void *part, int copies, int p, int32_t *L, cudaStream_t s)
 {
-    int blocks = std::min((p + 255) / 256, sm_count() * 8);
-    k_merge_partials<<<std::max(1, blocks), 256, 0, s>>>(part, copies, p,
-                                                         reinterpret_cast<int2 *>(L));
+    k_merge_partials<<<(p + 31) / 32, 1024, 0, s>>>(reinterpret_cast<const uint32_t *>(part),
+                                                         copies, p, reinterpret_cast<int2 *>(L));
     return cudaGetLastError();
 }
 
