@@ -300,7 +300,8 @@ def run_ours(args):
                    "distributions": [d for d, _ in inputs], "instances_per_step": len(inputs),
                    "l2": "inputs 8n bytes per instance, larger than L2; no flush"},
         "hbm_frac_step": (pts_step * 8 / (ms / args.steps / 1e3) / 1e9) / peak,
-        "roofline": {"bound": "hbm", "kernel": "k_reduce_packed", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": ["k_reduce_private", "k_reduce_filtered", "k_reduce_global"][ch.ch_plan_info(n, p)[0]],
+                     "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "algorithmic_bytes_per_launch": kernel_bytes, "avg_launch_ms": red_avg,
                      "traffic": (trec or {}).get("dram_bytes_per_launch")},
@@ -309,7 +310,7 @@ def run_ours(args):
         "cpu_baseline": {"value": cpu_v, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
                          "sample": f"{cpu_passes} pass(es) over the step's {len(inputs)} instances "
                                    f"({cpu_dt:.1f} s, single thread)"},
-        "gpu_launches": args.steps * len(inputs) * 4,
+        "gpu_launches": args.steps * len(inputs) * ch.ch_plan_info(n, p)[1],
         "clocks": clocks,
         "hull_vertices": hsz,
     }

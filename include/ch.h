@@ -78,11 +78,19 @@ int ch_clear_status(ch_stream_t stream);
 /* Profiling aid (not part of the method).  events: npairs pairs of
  * cudaEvent_t handles created by the caller with timing enabled.  While set,
  * every ch_reduce / ch_convex_hull call records the next pair (round robin)
- * on its stream immediately before and after its reduction kernel, so the
- * caller can time that kernel inside a longer stream of work.  npairs = 0
+ * on its stream immediately before and after its main reduction kernel (the
+ * one that reads every point), so the caller can time that kernel inside a
+ * longer stream of work.  npairs = 0
  * (or events = NULL) turns it off.  Process-wide; the handles must outlive
  * the calls that use them. */
 int ch_trace_set(void *const *events, int npairs);
+
+/* How ch_convex_hull will run n points of side p on the current device:
+ * *form = 0 (private shared-memory copies of L, p <= 29056), 1 (filtered
+ * global L, p <= 116224) or 2 (global L with a read-then-atomic test), and
+ * *kernels = the number of kernels one ch_convex_hull call launches.  Either
+ * pointer may be NULL. */
+int ch_plan_info(int64_t n, int32_t p, int32_t *form, int32_t *kernels);
 
 /* ---------------------------------------------------------------------- */
 /* Step 1: Algorithm 1, Reduction of Points (Section 2.1).                 */

@@ -45,6 +45,7 @@ def _declare(lib):
         "ch_sync_status": (ctypes.c_int, [P]),
         "ch_clear_status": (ctypes.c_int, [P]),
         "ch_trace_set": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
+        "ch_plan_info": (ctypes.c_int, [i64, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "ch_reduce_workspace_size": (ctypes.c_int, [i64, i32, szp]),
         "ch_reduce": (ctypes.c_int, [P, i64, i32, P, P, sz, P]),
         "ch_chain_workspace_size": (ctypes.c_int, [i32, szp]),
@@ -144,6 +145,14 @@ def ch_trace_set(events):
     flat = [e.cuda_event for pair in events for e in pair]
     arr = (ctypes.c_void_p * max(1, len(flat)))(*flat)
     _check(lib().ch_trace_set(arr, len(events)), "ch_trace_set")
+
+
+def ch_plan_info(n: int, p: int):
+    """(form, kernels): how ch_convex_hull runs n points of side p on the
+    current device, and how many kernels one call launches."""
+    form, kern = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib().ch_plan_info(int(n), int(p), ctypes.byref(form), ctypes.byref(kern)), "ch_plan_info")
+    return int(form.value), int(kern.value)
 
 
 def ch_reduce_workspace_size(n: int, p: int) -> int:

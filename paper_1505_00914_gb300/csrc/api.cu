@@ -23,25 +23,17 @@ std::mutex g_trace_mu;
 cudaEvent_t g_trace[2 * 1024];
 int g_trace_n = 0, g_trace_next = 0;
 
-template <class F>
-cudaError_t traced(cudaStream_t s, F &&launch)
+// The next traced event pair, or (nullptr, nullptr) when tracing is off.
+void next_trace(cudaEvent_t *e0, cudaEvent_t *e1)
 {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    {
-        std::lock_guard<std::mutex> g(g_trace_mu);
-        if (g_trace_n > 0) {
-            const int i = g_trace_next;
-            g_trace_next = (g_trace_next + 1) % g_trace_n;
-            e0 = g_trace[2 * i];
-            e1 = g_trace[2 * i + 1];
-        }
+    std::lock_guard<std::mutex> g(g_trace_mu);
+    *e0 = *e1 = nullptr;
+    if (g_trace_n > 0) {
+        const int i = g_trace_next;
+        g_trace_next = (g_trace_next + 1) % g_trace_n;
+        *e0 = g_trace[2 * i];
+        *e1 = g_trace[2 * i + 1];
     }
-    if (e0 && cudaEventRecord(e0, s) != cudaSuccess)
-        return cudaErrorUnknown;
-    cudaError_t e = launch();
-    if (e == cudaSuccess && e1)
-        e = cudaEventRecord(e1, s);
-    return e;
 }
 inline int cuda_rc(cudaError_t e) { return e == cudaSuccess ? CH_OK : CH_ERR_CUDA; }
 }  // namespace
@@ -177,6 +169,21 @@ int ch_trace_set(void *const *events, int npairs)
     return CH_OK;
 }
 
+int ch_plan_info(int64_t n, int32_t p, int32_t *form, int32_t *kernels)
+{
+    if (check_np(n, p) != CH_OK)
+        return CH_ERR_ARG;
+    ReducePlan pl;
+    int rc = reduce_plan(n, p, &pl);
+    if (rc != CH_OK)
+        return rc;
+    if (form)
+        *form = pl.mode;
+    if (kernels)  // reduction (+ merge of private copies), chain, final hull
+        *kernels = reduce_kernel_count(pl) + (pl.mode == 0 ? 1 : 0) + 2;
+    return CH_OK;
+}
+
 int ch_reduce_workspace_size(int64_t n, int32_t p, size_t *bytes)
 {
     if (!bytes || check_np(n, p) != CH_OK)
@@ -208,7 +215,9 @@ int ch_reduce(const int32_t *pts, int64_t n, int32_t p, int32_t *L, void *worksp
     if (!st)
         return CH_ERR_CUDA;
     void *part = workspace;
-    cudaError_t e = traced(s, [&] { return reduce_launch(pl, pts, n, p, part, L, st, s); });
+    cudaEvent_t ev0, ev1;
+    next_trace(&ev0, &ev1);
+    cudaError_t e = reduce_launch(pl, pts, n, p, part, L, st, s, nullptr, 0, ev0, ev1);
     if (e == cudaSuccess && pl.mode == 0)
         e = reduce_merge_launch(part, pl.copies, p, L, s);
     return cuda_rc(e);
@@ -304,19 +313,25 @@ int ch_convex_hull(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t
     if (!counts)
         counts = reinterpret_cast<int32_t *>(b + w.counts);
     void *part = b + w.part;
-    cudaError_t e = traced(s, [&] { return reduce_launch(w.plan, pts, n, p, part, L, st, s); });
+    cudaEvent_t ev0, ev1;
+    next_trace(&ev0, &ev1);
+    unsigned long long *zero = reinterpret_cast<unsigned long long *>(b + w.state);
+    const int nzero = (int)(chain_state_bytes(p) / 8);
+    // the look-back state is cleared by the last kernel before the chain step
+    cudaError_t e = reduce_launch(w.plan, pts, n, p, part, L, st, s,
+                                  w.plan.mode == 0 ? nullptr : zero, nzero, ev0, ev1);
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
     if (w.plan.mode == 0) {
         if (!L)
             L = reinterpret_cast<int32_t *>(b + w.L);
-        e = reduce_merge_launch(part, w.plan.copies, p, L, s);
+        e = reduce_merge_launch(part, w.plan.copies, p, L, s, zero, nzero);
         if (e != cudaSuccess)
             return CH_ERR_CUDA;
     }
     const HullLayout hl = hull_layout(p);
     char *hw = b + w.hull;
-    e = chain_launch(L, p, lower, upper, counts, nullptr, b + w.state, false,
+    e = chain_launch(L, p, lower, upper, counts, nullptr, b + w.state, true,
                      reinterpret_cast<int2 *>(hw + hl.cand), reinterpret_cast<int *>(hw + hl.ccnt),
                      st, s);
     if (e != cudaSuccess)

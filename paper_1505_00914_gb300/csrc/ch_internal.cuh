@@ -55,11 +55,17 @@ size_t reduce_partials_bytes(const ReducePlan &plan, int p);
 // Mode 0 writes plan.copies packed uint32[p] partial arrays to `scratch`
 // (((lo-1) << 16) | (hi-1), 0xFFFF0000 when empty); modes 1-2 write the final
 // L (mode 1 keeps its global filter in `scratch`).
+// zero/nzero: words (the chain look-back state) that the last kernel before
+// the main pass clears, or nullptr.  ev0/ev1: events recorded right before
+// and after the main reduction kernel (the dominant one), or nullptr.
 cudaError_t reduce_launch(const ReducePlan &plan, const int32_t *pts, int64_t n, int p,
-                          void *scratch, int32_t *L, unsigned *status, cudaStream_t s);
+                          void *scratch, int32_t *L, unsigned *status, cudaStream_t s,
+                          unsigned long long *zero = nullptr, int nzero = 0,
+                          cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+int reduce_kernel_count(const ReducePlan &plan);
 // L = column-wise merge of `copies` packed partial arrays.
 cudaError_t reduce_merge_launch(const void *partials, int copies, int p, int32_t *L,
-                                cudaStream_t s);
+                                cudaStream_t s, unsigned long long *zero = nullptr, int nzero = 0);
 
 // ---- chain (chain.cu) ----
 int chain_tiles(int p);

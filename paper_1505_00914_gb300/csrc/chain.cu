@@ -40,16 +40,19 @@ using aref = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>;
 // running (ticket order), so the spin polls without sleeping; it is bounded.
 constexpr int LB_W = 8;
 
+// Publishes the tile's own count (tile 0: its inclusive prefix); one thread.
+__device__ __forceinline__ void publish_aggregate(unsigned long long *ts, int tile, long long agg)
+{
+    aref(ts[tile]).store((tile == 0 ? FLAG_PRE : FLAG_AGG) | (unsigned long long)agg,
+                         cuda::memory_order_release);
+}
+
+// The tile's exclusive prefix; its aggregate was published earlier.
 __device__ long long warp_look_back(unsigned long long *ts, int tile, long long agg, int lane,
                                     unsigned *status)
 {
-    if (tile == 0) {
-        if (lane == 0)
-            aref(ts[0]).store(FLAG_PRE | (unsigned long long)agg, cuda::memory_order_release);
+    if (tile == 0)
         return 0;
-    }
-    if (lane == 0)
-        aref(ts[tile]).store(FLAG_AGG | (unsigned long long)agg, cuda::memory_order_release);
     long long excl = 0;
     int base = tile - 1;
     int spins = 0;
@@ -141,41 +144,47 @@ __global__ void __launch_bounds__(TILE)
                 incl += t;
         }
         s_wc[lane] = incl - v;
-        const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        const long long pre = warp_look_back(state + 1, tile, total, lane, status);
-        if (lane == 0) {
-            s_prefix = pre;
-            s_cnt = total;
-            if (tile == ntiles - 1) {
-                counts[0] = (int)(pre + total);
-                counts[1] = (int)(pre + total);
-            }
+        if (lane == 31) {
+            s_cnt = incl;
+            publish_aggregate(state + 1, tile, incl);  // early: successors need only this
         }
     }
     __syncthreads();
+    const int cnt = s_cnt;
     const int r = s_wc[w] + __popc(bal & ((1u << lane) - 1u));  // rank within the tile
-    if (valid) {
-        const long long pos = s_prefix + r;
-        lower[pos] = make_int2(c + 1, e.x);
-        upper[pos] = make_int2(c + 1, e.y);
-    }
     if constexpr (FILTER) {
-        const int cnt = s_cnt;
+        // the hull pre-filter needs no global position: run it before waiting
         if (valid) {
             fs.P[0][r] = make_int2(c + 1, e.x);
             fs.P[1][r] = make_int2(c + 1, -e.y);
         }
         __syncthreads();
-        build_min_tree(fs.P[0], fs.M[0], cnt);
-        build_min_tree(fs.P[1], fs.M[1], cnt);
+        build_min_trees(fs.P[0], fs.M[0], fs.P[1], fs.M[1], cnt);
         const bool k0 = run_keeps(fs.P[0], fs.M[0], cnt, threadIdx.x);
         const bool k1 = run_keeps(fs.P[1], fs.M[1], cnt, threadIdx.x);
-        const int n0 = compact_run(fs.P[0], k0, cand + (size_t)tile * TILE, s_wc);
-        const int n1 = compact_run(fs.P[1], k1, cand + ((size_t)ntiles + tile) * TILE, s_wc);
+        __shared__ int s_cw[WPB + 1];
+        const int n0 = compact_run(fs.P[0], k0, cand + (size_t)tile * TILE, s_cw);
+        const int n1 = compact_run(fs.P[1], k1, cand + ((size_t)ntiles + tile) * TILE, s_cw);
         if (threadIdx.x == 0) {
             ccnt[tile] = n0;
             ccnt[ntiles + tile] = n1;
         }
+    }
+    if (w == 0) {
+        const long long pre = warp_look_back(state + 1, tile, cnt, lane, status);
+        if (lane == 0) {
+            s_prefix = pre;
+            if (tile == ntiles - 1) {
+                counts[0] = (int)(pre + cnt);
+                counts[1] = (int)(pre + cnt);
+            }
+        }
+    }
+    __syncthreads();
+    if (valid) {
+        const long long pos = s_prefix + r;
+        lower[pos] = make_int2(c + 1, e.x);
+        upper[pos] = make_int2(c + 1, e.y);
     }
 }
 

@@ -5,8 +5,8 @@
 // decides whether point i can be a strict vertex of the lower hull.  It drops
 // the point when it lies on or above the segment between two other points of
 // the run, one on each side: the lowest points of the sibling sub-runs of i at
-// every level of a binary min-tree over the run, its immediate neighbours, and
-// the points at distances d, e in {s, 2s}, s = 1, 2, 4, ...  A dropped point
+// every level of a binary min-tree over the run, and its neighbours at most
+// two places away.  A dropped point
 // is a convex combination of two input points, so it is not a strict vertex:
 // every drop is exact, whichever tests are chosen; the tests only decide how
 // many non-vertices are left for the exact merge that follows.
@@ -23,54 +23,71 @@ constexpr int RUN_LOG = 10;
 // tree_off(k); 2 * RUN shorts hold every level.
 __device__ __forceinline__ int tree_off(int k) { return 2 * RUN - ((2 * RUN) >> (k - 1)); }
 
-// Builds the min-y index tree of P[0..n); every thread of the CTA calls it.
-__device__ __forceinline__ void build_min_tree(const int2 *P, short *M, int n)
+// Builds the min-y index trees of two runs, P0[0..n) and P1[0..n), level by
+// level; every thread of the CTA calls it.
+__device__ __forceinline__ void build_min_trees(const int2 *P0, short *M0, const int2 *P1, short *M1,
+                                                int n)
 {
     const int i = threadIdx.x;
     for (int k = 1; k <= RUN_LOG; ++k) {
         if (i < (RUN >> k)) {
-            int a, b;
+            int a0, b0, a1, b1;
             if (k == 1) {
-                a = 2 * i;
-                b = 2 * i + 1;
+                a0 = a1 = 2 * i;
+                b0 = b1 = 2 * i + 1;
             } else {
-                a = M[tree_off(k - 1) + 2 * i];
-                b = M[tree_off(k - 1) + 2 * i + 1];
+                a0 = M0[tree_off(k - 1) + 2 * i];
+                b0 = M0[tree_off(k - 1) + 2 * i + 1];
+                a1 = M1[tree_off(k - 1) + 2 * i];
+                b1 = M1[tree_off(k - 1) + 2 * i + 1];
             }
-            int best = (a >= 0 && a < n) ? a : -1;
-            if (b >= 0 && b < n && (best < 0 || P[b].y < P[best].y))
-                best = b;
-            M[tree_off(k) + i] = (short)best;
+            const bool va0 = a0 >= 0 && a0 < n, vb0 = b0 >= 0 && b0 < n;
+            const bool va1 = a1 >= 0 && a1 < n, vb1 = b1 >= 0 && b1 < n;
+            const int ya0 = va0 ? P0[a0].y : 0, yb0 = vb0 ? P0[b0].y : 0;
+            const int ya1 = va1 ? P1[a1].y : 0, yb1 = vb1 ? P1[b1].y : 0;
+            M0[tree_off(k) + i] = (short)(va0 ? ((vb0 && yb0 < ya0) ? b0 : a0) : (vb0 ? b0 : -1));
+            M1[tree_off(k) + i] = (short)(va1 ? ((vb1 && yb1 < ya1) ? b1 : a1) : (vb1 ? b1 : -1));
         }
         __syncthreads();
     }
 }
 
-// True when point i of P[0..n) may be a strict lower-hull vertex.
+// True when point i of P[0..n) may be a strict lower-hull vertex.  The anchor
+// loads of three levels at a time are issued before their orientation tests.
 __device__ __forceinline__ bool run_keeps(const int2 *P, const short *M, int n, int i)
 {
     if (i >= n)
         return false;
     const int2 q = P[i];
-    for (int k = 1; k < RUN_LOG; ++k) {
-        const int node = i >> k;
-        const int la = node >= 1 ? M[tree_off(k) + node - 1] : -1;
-        const int ra = (node + 1) < (RUN >> k) ? M[tree_off(k) + node + 1] : -1;
-        if (la >= 0 && ra >= 0 && cross3(P[la], P[ra], q) >= 0)
-            return false;
-        if (la >= 0 && i + 1 < n && cross3(P[la], P[i + 1], q) >= 0)
-            return false;
-        if (ra >= 0 && i >= 1 && cross3(P[i - 1], P[ra], q) >= 0)
-            return false;
+    const bool h1 = i >= 1 && i + 1 < n, l2 = i >= 2, r2 = i + 2 < n;
+    const int2 nl1 = i >= 1 ? P[i - 1] : q, nr1 = i + 1 < n ? P[i + 1] : q;
+    const int2 nl2 = l2 ? P[i - 2] : q, nr2 = r2 ? P[i + 2] : q;
+    bool drop = h1 && (cross3(nl1, nr1, q) >= 0 || (r2 && cross3(nl1, nr2, q) >= 0) ||
+                       (l2 && cross3(nl2, nr1, q) >= 0));
+    constexpr int CH = 3;  // levels per batch; levels 1..RUN_LOG-1 have siblings
+#pragma unroll
+    for (int k0 = 1; k0 < RUN_LOG; k0 += CH) {
+        int la[CH], ra[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int k = k0 + u, node = i >> k;
+            la[u] = node >= 1 ? M[tree_off(k) + node - 1] : -1;
+            ra[u] = (node + 1) < (RUN >> k) ? M[tree_off(k) + node + 1] : -1;
+        }
+        int2 A[CH], B[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            A[u] = la[u] >= 0 ? P[la[u]] : q;
+            B[u] = ra[u] >= 0 ? P[ra[u]] : q;
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            drop |= la[u] >= 0 && ra[u] >= 0 && cross3(A[u], B[u], q) >= 0;
+            drop |= la[u] >= 0 && i + 1 < n && cross3(A[u], nr1, q) >= 0;
+            drop |= ra[u] >= 0 && i >= 1 && cross3(nl1, B[u], q) >= 0;
+        }
     }
-    for (int s = 1; i - s >= 0 || i + s < n; s <<= 1) {
-        const bool l1 = i - s >= 0, r1 = i + s < n, l2 = i - 2 * s >= 0, r2 = i + 2 * s < n;
-        if ((l1 && r1 && cross3(P[i - s], P[i + s], q) >= 0) ||
-            (l1 && r2 && cross3(P[i - s], P[i + 2 * s], q) >= 0) ||
-            (l2 && r1 && cross3(P[i - 2 * s], P[i + s], q) >= 0))
-            return false;
-    }
-    return true;
+    return !drop;
 }
 
 // Writes the kept points of P[0..n), in order, to out; returns their number.

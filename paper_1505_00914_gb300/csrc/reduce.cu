@@ -118,8 +118,11 @@ __global__ void __launch_bounds__(RT)
 }
 
 // --------------------------------------------------------------- filtered
-__global__ void k_fill_empty(int2 *L, int p)
+__global__ void k_fill_empty(int2 *L, int p, unsigned long long *zero, int nzero)
 {
+    if (zero && blockIdx.x == 0)
+        for (int i = threadIdx.x; i < nzero; i += blockDim.x)
+            zero[i] = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p; i += gridDim.x * blockDim.x)
         L[i] = make_int2(p + 1, -1);
 }
@@ -239,8 +242,11 @@ constexpr int MG_V = 32, MG_GROUPS = 32;
 
 __global__ void __launch_bounds__(MG_V *MG_GROUPS)
     k_filter_merge(const uint16_t *__restrict__ slots, int rows, int p, uint16_t *__restrict__ G,
-                   int2 *__restrict__ L)
+                   int2 *__restrict__ L, unsigned long long *zero, int nzero)
 {
+    if (zero && blockIdx.x == 0)
+        for (int i = threadIdx.x; i < nzero; i += blockDim.x)
+            zero[i] = 0;
     __shared__ uint4 part[MG_GROUPS][MG_V];
     const int words = (p + 7) / 8;
     const int v = threadIdx.x % MG_V, g = threadIdx.x / MG_V;
@@ -349,8 +355,12 @@ __global__ void __launch_bounds__(RT)
 // with 32 thread groups; group g folds rows g, g + 32, ... (all loads of a
 // thread in flight together), and the groups combine through shared memory.
 __global__ void __launch_bounds__(1024)
-    k_merge_partials(const uint32_t *__restrict__ part, int copies, int p, int2 *L)
+    k_merge_partials(const uint32_t *__restrict__ part, int copies, int p, int2 *L,
+                     unsigned long long *zero, int nzero)
 {
+    if (zero && blockIdx.x == 0)
+        for (int i = threadIdx.x; i < nzero; i += blockDim.x)
+            zero[i] = 0;
     __shared__ uint32_t s_lo[32][33], s_hi[32][33];
     const int v = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int c = blockIdx.x * 32 + v;
@@ -486,6 +496,11 @@ int reduce_plan(int64_t n, int p, ReducePlan *pl)
     return CH_OK;
 }
 
+int reduce_kernel_count(const ReducePlan &pl)
+{
+    return pl.mode == 0 ? 1 : (pl.mode == 1 ? 3 : 2);
+}
+
 size_t reduce_partials_bytes(const ReducePlan &pl, int p)
 {
     if (pl.mode == 0)
@@ -496,21 +511,28 @@ size_t reduce_partials_bytes(const ReducePlan &pl, int p)
 }
 
 cudaError_t reduce_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, int p,
-                          void *part, int32_t *L, unsigned *status, cudaStream_t s)
+                          void *part, int32_t *L, unsigned *status, cudaStream_t s,
+                          unsigned long long *zero, int nzero, cudaEvent_t ev0, cudaEvent_t ev1)
 {
+    auto mark = [&](cudaEvent_t ev) { return ev ? cudaEventRecord(ev, s) : cudaSuccess; };
     if (pl.mode == 0) {
         uint32_t *pp = reinterpret_cast<uint32_t *>(part);
+        mark(ev0);
         if (pl.threads == 512)
             k_reduce_private<512><<<pl.grid, 512, pl.smem, s>>>(pts, n, p, pp, status);
         else
             k_reduce_private<1024><<<pl.grid, 1024, pl.smem, s>>>(pts, n, p, pp, status);
+        mark(ev1);
         return cudaGetLastError();
     }
     int2 *L2 = reinterpret_cast<int2 *>(L);
     const int sms = sm_count();
     if (pl.mode == 2) {
-        k_fill_empty<<<std::max(1, std::min((p + 255) / 256, sms * 4)), 256, 0, s>>>(L2, p);
+        k_fill_empty<<<std::max(1, std::min((p + 255) / 256, sms * 4)), 256, 0, s>>>(L2, p, zero,
+                                                                                    nzero);
+        mark(ev0);
         k_reduce_global<<<sms * 8, 256, 0, s>>>(pts, n, p, L2, status);
+        mark(ev1);
         return cudaGetLastError();
     }
     uint16_t *G = reinterpret_cast<uint16_t *>(part);
@@ -518,15 +540,20 @@ cudaError_t reduce_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, i
                                                    ((((size_t)p * 2) + 255) & ~size_t(255)));
     k_filter_warm<1024><<<pl.grid, 1024, pl.smem, s>>>(pts, n, p, pl.shift, pl.grid, slots);
     const int words = (p + 7) / 8;
-    k_filter_merge<<<(words + MG_V - 1) / MG_V, MG_V * MG_GROUPS, 0, s>>>(slots, pl.grid, p, G, L2);
+    k_filter_merge<<<(words + MG_V - 1) / MG_V, MG_V * MG_GROUPS, 0, s>>>(slots, pl.grid, p, G, L2,
+                                                                         zero, nzero);
+    mark(ev0);
     k_reduce_filtered<1024><<<pl.grid, 1024, pl.smem, s>>>(pts, n, p, pl.shift, G, L2, status);
+    mark(ev1);
     return cudaGetLastError();
 }
 
-cudaError_t reduce_merge_launch(const void *part, int copies, int p, int32_t *L, cudaStream_t s)
+cudaError_t reduce_merge_launch(const void *part, int copies, int p, int32_t *L, cudaStream_t s,
+                                unsigned long long *zero, int nzero)
 {
     k_merge_partials<<<(p + 31) / 32, 1024, 0, s>>>(reinterpret_cast<const uint32_t *>(part),
-                                                         copies, p, reinterpret_cast<int2 *>(L));
+                                                         copies, p, reinterpret_cast<int2 *>(L),
+                                                         zero, nzero);
     return cudaGetLastError();
 }
 
