@@ -163,6 +163,41 @@ int ch_convex_hull_host(const int32_t *host_pts, int64_t n, int32_t p,
                         int32_t *host_hull, int32_t *host_hull_count,
                         void *workspace, size_t ws_bytes, ch_stream_t stream);
 
+/* ---------------------------------------------------------------------- */
+/* Many independent sets in one persistent launch (the three steps per     */
+/* set, Section 2.1).                                                      */
+/* ---------------------------------------------------------------------- */
+
+/* Largest side p of a set in a batch. */
+#define CH_BATCH_MAX_P 16384
+
+/* Set s holds points [offsets[s], offsets[s+1]) of one interleaved int32
+ * point array and has side ps[s] (1 <= ps[s] <= CH_BATCH_MAX_P).  The plan
+ * cuts each set into chunks of about chunk_mult * ps[s] points (at least
+ * 65536, at most 2^22): the tuning knob.  host_offsets (int64[B+1]) and
+ * host_ps (int32[B]) are HOST arrays. */
+int ch_batched_workspace_size(int32_t B, const int64_t *host_offsets, const int32_t *host_ps,
+                              int32_t chunk_mult, size_t *bytes);
+
+/* Builds the work plan on the host and stores it in the device workspace
+ * (waits for `stream`).  The workspace then belongs to this plan: any number
+ * of ch_hull_batched calls with the same B may follow (and may be captured in
+ * a CUDA graph); prepare again after a change of sizes. */
+int ch_batched_prepare(int32_t B, const int64_t *host_offsets, const int32_t *host_ps,
+                       int32_t chunk_mult, void *workspace, size_t ws_bytes, ch_stream_t stream);
+
+/* Hulls of the B sets of the prepared plan in one launch.  pts: the device
+ * point array; offsets, ps: device copies of the sizes the plan was built
+ * from (kept in the signature; the plan carries them).  hull_out: int32 pairs,
+ * set s writing hull_out[hull_offsets[s] ...] (device int64[B+1]; capacity at
+ * least min(n_s, 2 * ps[s]) pairs per set); hull_counts: device int32[B].
+ * Each hull lists strict vertices counter-clockwise from the lexicographic
+ * minimum.  Returns CH_ERR_ARG if no plan for B sets was prepared in
+ * `workspace`. */
+int ch_hull_batched(const int32_t *pts, const int64_t *offsets, const int32_t *ps, int32_t B,
+                    int32_t *hull_out, const int64_t *hull_offsets, int32_t *hull_counts,
+                    void *workspace, size_t ws_bytes, ch_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,87 @@
+"""Autotuner for the batched launch: picks the chunk size per column
+(``chunk_mult``) of the work plan by timing the real launch on the batch at
+hand, and caches the winner per (device, batch shape) in a JSON file.
+
+The chunk size trades load balance (small chunks, more items for the
+persistent CTAs to share) against per-item overhead (every item initialises a
+private L of p columns and, when a set has several chunks, writes and merges a
+partial row of p words).  Everything timed here is the library's own launch;
+no kernel is written in Python.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+import numpy as np
+import torch
+
+from . import ch
+
+CANDIDATES = (8, 16, 32, 64, 128, 256, 1024)
+
+
+def _cache_path() -> str:
+    return os.environ.get("CH_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "chull_gb300", "autotune.json"))
+
+
+def batch_key(offsets, ps) -> str:
+    """Device name + a digest of the batch's shape (n and p per set)."""
+    off = np.asarray(offsets, np.int64)
+    pp = np.asarray(ps, np.int32)
+    h = hashlib.sha256(np.diff(off).tobytes() + pp.tobytes()).hexdigest()[:16]
+    return f"{torch.cuda.get_device_name()}|B={pp.shape[0]}|{h}"
+
+
+def _load():
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _store(db):
+    path = _cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(db, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass  # a read-only home only loses the cache
+
+
+def tune_batched(d_pts, offsets, ps, d_off, d_ps, hull, d_hoff, counts, candidates=CANDIDATES,
+                 reps: int = 3, use_cache: bool = True):
+    """Returns (best chunk_mult, {chunk_mult: ms}) for this batch; the host
+    arrays offsets/ps describe it, the device tensors are those the caller
+    will launch with."""
+    key = batch_key(offsets, ps)
+    db = _load() if use_cache else {}
+    if key in db:
+        return int(db[key]["chunk_mult"]), {int(k): v for k, v in db[key]["ms"].items()}
+    need = max(ch.ch_batched_workspace_size(offsets, ps, c) for c in candidates)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    times = {}
+    for c in candidates:
+        ch.ch_batched_prepare(offsets, ps, ws, c)
+        ch.ch_hull_batched(d_pts, d_off, d_ps, hull, d_hoff, counts, ws)  # warm-up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            ch.ch_hull_batched(d_pts, d_off, d_ps, hull, d_hoff, counts, ws)
+        b.record()
+        torch.cuda.synchronize()
+        times[c] = a.elapsed_time(b) / reps
+    rc = ch.ch_sync_status()
+    if rc != ch.CH_OK:
+        raise ch.ChError(rc, "tune_batched")
+    best = min(times, key=times.get)
+    db[key] = {"chunk_mult": best, "ms": times}
+    if use_cache:
+        _store(db)
+    return best, times

@@ -46,6 +46,9 @@ def _declare(lib):
         "ch_clear_status": (ctypes.c_int, [P]),
         "ch_trace_set": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
         "ch_plan_info": (ctypes.c_int, [i64, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "ch_batched_workspace_size": (ctypes.c_int, [i32, P, P, i32, szp]),
+        "ch_batched_prepare": (ctypes.c_int, [i32, P, P, i32, P, sz, P]),
+        "ch_hull_batched": (ctypes.c_int, [P, P, P, i32, P, P, P, P, sz, P]),
         "ch_reduce_workspace_size": (ctypes.c_int, [i64, i32, szp]),
         "ch_reduce": (ctypes.c_int, [P, i64, i32, P, P, sz, P]),
         "ch_chain_workspace_size": (ctypes.c_int, [i32, szp]),
@@ -255,3 +258,52 @@ def ch_convex_hull_host(host_pts, p: int, workspace, stream=None, host_hull=None
                                      ctypes.byref(cnt), _ptr(workspace), workspace.numel(),
                                      _stream(stream)), "ch_convex_hull_host")
     return host_hull[: cnt.value]
+
+
+# ------------------------------------------------------------------ batched
+
+
+def _host_sizes(offsets, ps):
+    import numpy as np
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    pp = np.ascontiguousarray(np.asarray(ps, dtype=np.int32))
+    return off, pp
+
+
+def ch_batched_workspace_size(offsets, ps, chunk_mult: int = 64) -> int:
+    off, pp = _host_sizes(offsets, ps)
+    out = ctypes.c_size_t(0)
+    _check(lib().ch_batched_workspace_size(pp.shape[0], off.ctypes.data_as(ctypes.c_void_p),
+                                           pp.ctypes.data_as(ctypes.c_void_p), int(chunk_mult),
+                                           ctypes.byref(out)), "ch_batched_workspace_size")
+    return int(out.value)
+
+
+def ch_batched_prepare(offsets, ps, workspace, chunk_mult: int = 64, stream=None):
+    """Plan the batch (host arrays offsets (B+1,), ps (B,)) into `workspace`."""
+    off, pp = _host_sizes(offsets, ps)
+    _check(lib().ch_batched_prepare(pp.shape[0], off.ctypes.data_as(ctypes.c_void_p),
+                                    pp.ctypes.data_as(ctypes.c_void_p), int(chunk_mult),
+                                    _ptr(workspace), workspace.numel(), _stream(stream)),
+           "ch_batched_prepare")
+
+
+def ch_hull_batched(pts, offsets, ps, hull_out, hull_offsets, hull_counts, workspace,
+                    stream=None):
+    """Hulls of all sets of the prepared batch (device tensors)."""
+    pts = _pts(pts)
+    B = int(ps.shape[0])
+    _check(lib().ch_hull_batched(_ptr(pts), _ptr(offsets), _ptr(ps), B, _ptr(hull_out),
+                                 _ptr(hull_offsets), _ptr(hull_counts), _ptr(workspace),
+                                 workspace.numel(), _stream(stream)), "ch_hull_batched")
+    return hull_out, hull_counts
+
+
+def hull_capacity_offsets(offsets, ps):
+    """int64 (B+1,) output offsets giving each set min(n, 2p) pairs."""
+    import numpy as np
+    off, pp = _host_sizes(offsets, ps)
+    cap = np.minimum(np.diff(off), 2 * pp.astype(np.int64))
+    out = np.zeros(pp.shape[0] + 1, dtype=np.int64)
+    np.cumsum(cap, out=out[1:])
+    return out

@@ -1,6 +1,7 @@
 // C ABI of libch.so (declared in include/ch.h): argument checks, workspace
 // layouts, the per-device status word and launch sequencing.  No entry point
 // allocates device memory; every launch goes to the caller's stream.
+#include <map>
 #include <mutex>
 
 #include "ch_internal.cuh"
@@ -337,6 +338,78 @@ int ch_convex_hull(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
     return cuda_rc(hull_final_launch(hl, hw, hull, hull_count, s));
+}
+
+namespace {
+std::mutex g_batch_mu;
+std::map<const void *, BatchPlanInfo> g_batch_plans;  // workspace -> prepared plan
+
+int check_batch(int32_t B, const int64_t *off, const int32_t *ps, int32_t chunk_mult)
+{
+    if (B < 0 || (B > 0 && (!off || !ps)) || chunk_mult < 1)
+        return CH_ERR_ARG;
+    if (B > 0 && off[0] < 0)
+        return CH_ERR_ARG;
+    for (int s = 0; s < B; ++s)
+        if (off[s + 1] < off[s] || ps[s] < 1 || ps[s] > BATCH_MAX_P)
+            return CH_ERR_ARG;
+    return CH_OK;
+}
+}  // namespace
+
+int ch_batched_workspace_size(int32_t B, const int64_t *host_offsets, const int32_t *host_ps,
+                              int32_t chunk_mult, size_t *bytes)
+{
+    if (!bytes)
+        return CH_ERR_ARG;
+    int rc = check_batch(B, host_offsets, host_ps, chunk_mult);
+    if (rc != CH_OK)
+        return rc;
+    return batch_sizes(B, host_offsets, host_ps, chunk_mult, bytes, nullptr);
+}
+
+int ch_batched_prepare(int32_t B, const int64_t *host_offsets, const int32_t *host_ps,
+                       int32_t chunk_mult, void *workspace, size_t ws_bytes, ch_stream_t stream)
+{
+    int rc = check_batch(B, host_offsets, host_ps, chunk_mult);
+    if (rc != CH_OK)
+        return rc;
+    if (!workspace)
+        return CH_ERR_WORKSPACE;
+    BatchPlanInfo info;
+    rc = batch_prepare(B, host_offsets, host_ps, chunk_mult, workspace, ws_bytes,
+                       reinterpret_cast<cudaStream_t>(stream), &info);
+    if (rc != CH_OK)
+        return rc;
+    std::lock_guard<std::mutex> g(g_batch_mu);
+    g_batch_plans[workspace] = info;
+    return CH_OK;
+}
+
+int ch_hull_batched(const int32_t *pts, const int64_t *offsets, const int32_t *ps, int32_t B,
+                    int32_t *hull_out, const int64_t *hull_offsets, int32_t *hull_counts,
+                    void *workspace, size_t ws_bytes, ch_stream_t stream)
+{
+    (void)offsets;
+    (void)ps;
+    if (B < 0 || (B > 0 && (!pts || !hull_out || !hull_offsets || !hull_counts)) ||
+        !aligned8(pts) || !aligned8(hull_out))
+        return CH_ERR_ARG;
+    if (B == 0)
+        return CH_OK;
+    BatchPlanInfo info;
+    {
+        std::lock_guard<std::mutex> g(g_batch_mu);
+        auto it = g_batch_plans.find(workspace);
+        if (it == g_batch_plans.end() || it->second.B != B)
+            return CH_ERR_ARG;  // no plan prepared in this workspace for B sets
+        info = it->second;
+    }
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    return batch_launch(pts, reinterpret_cast<int2 *>(hull_out), hull_offsets, hull_counts,
+                        workspace, ws_bytes, info, st, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int ch_convex_hull_host_workspace_size(int64_t n, int32_t p, size_t *bytes)

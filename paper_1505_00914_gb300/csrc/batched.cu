@@ -1,0 +1,361 @@
+// Many independent point sets in one persistent launch: Algorithm 1, the
+// chains and the hull (Section 2.1) for each set.
+//
+// A host-side planner cuts every set into chunks (work items) and sorts the
+// items longest first.  Persistent CTAs take items from an atomic queue.  For
+// an item the CTA folds its chunk into a private L in shared memory with
+// native shared atomicMin / atomicMax (int32 lo[p], hi[p]).  A set of one
+// chunk is finished by that CTA at once; a set of several chunks has each
+// chunk write its L as a packed partial row, and the CTA that completes the
+// last chunk (per-set atomic ticket) merges the rows and finishes the set.
+// Finishing scans L in 1024-column tiles: the valid columns of each tile go
+// through the exact hull pre-filter (hull_filter.cuh) and its survivors are
+// appended to per-chain lists; the lists are then peeled, merged and
+// stitched (hull_merge.cuh) straight into the set's slice of the ragged
+// output.  L never leaves shared memory for one-chunk sets.
+#include <algorithm>
+#include <vector>
+
+#include "ch_internal.cuh"
+#include "hull_filter.cuh"
+#include "hull_merge.cuh"
+
+namespace ch {
+namespace {
+
+constexpr int BT = 1024;       // threads per CTA (= RUN, one column per thread in a tile)
+constexpr int BPCAP = 8192;    // survivors (both chains) finished in shared memory
+
+struct BItem {
+    long long start, end;  // global point range [start, end)
+    int set, chunk;
+};
+struct BSet {
+    long long part_off;  // first packed partial row (uint32 units), sets with nchunks > 1
+    int nchunks, p;
+};
+
+// Dynamic shared memory: [L: 8 * BMAX_P][A: BPCAP int2][tile runs + trees].
+// After the tiles the L region holds B (BPCAP int2), F (BPCAP int), ix.
+constexpr size_t SM_L = 8 * (size_t)BATCH_MAX_P;
+constexpr size_t SM_A = BPCAP * sizeof(int2);
+constexpr size_t SM_RUNS = 2 * RUN * sizeof(int2) + 2 * 2 * RUN * sizeof(short);
+constexpr size_t BATCH_SMEM = SM_L + SM_A + SM_RUNS;
+static_assert(BPCAP * (sizeof(int2) + sizeof(int)) + 4 * (BPCAP / HS + 2) * sizeof(int) <= SM_L,
+              "peel scratch fits the L region");
+
+// Per-CTA global scratch (used when a set's survivors exceed BPCAP).
+constexpr size_t SCR_PTS = 2 * (size_t)BATCH_MAX_P;  // points, both chains
+constexpr size_t SCR_BYTES = 2 * SCR_PTS * sizeof(int2) + SCR_PTS * sizeof(int) +
+                             4 * (SCR_PTS / HS + 2) * sizeof(int) + 256;
+
+__device__ __forceinline__ void fold(int *slo, int *shi, uint32_t up, int x, int y, bool &bad)
+{
+    const uint32_t c = (uint32_t)(x - 1);
+    if (c >= up || (uint32_t)(y - 1) >= up) {
+        bad = true;
+        return;
+    }
+    atomicMin(slo + c, y);
+    atomicMax(shi + c, y);
+}
+
+// Folds points [0, n) of `base` (8-byte aligned) into slo/shi; whole CTA.
+__device__ void fold_range(const int32_t *__restrict__ base, int64_t n, int p, int *slo, int *shi,
+                           bool &bad)
+{
+    const uint32_t up = (uint32_t)p;
+    const int64_t head = (((uintptr_t)base & 15) != 0 && n > 0) ? 1 : 0;
+    const int64_t npairs = (n - head) >> 1;
+    if (threadIdx.x == 0) {
+        if (head)
+            fold(slo, shi, up, base[0], base[1], bad);
+        if ((n - head) & 1)
+            fold(slo, shi, up, base[2 * (n - 1)], base[2 * (n - 1) + 1], bad);
+    }
+    const int4 *p4 = reinterpret_cast<const int4 *>(base + 2 * head);
+    constexpr int U = 4;
+    for (int64_t i = threadIdx.x; i < npairs; i += (int64_t)BT * U) {
+        int4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t j = i + (int64_t)u * BT;
+            v[u] = j < npairs ? __ldcs(p4 + j) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (i + (int64_t)u * BT < npairs) {
+                fold(slo, shi, up, v[u].x, v[u].y, bad);
+                fold(slo, shi, up, v[u].z, v[u].w, bad);
+            }
+        }
+    }
+}
+
+// Hull of the set whose L is in slo/shi (p columns); whole CTA.
+__device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 *scr,
+                           int2 *hull, int *hull_count, int *s_warp, int *s_total, int *s_cnt)
+{
+    int2 *A = reinterpret_cast<int2 *>(smem + SM_L);
+    int2 *P0 = reinterpret_cast<int2 *>(smem + SM_L + SM_A);
+    int2 *P1 = P0 + RUN;
+    short *M0 = reinterpret_cast<short *>(P1 + RUN);
+    short *M1 = M0 + 2 * RUN;
+    // survivors are appended to the per-CTA global lists first (capacity p each)
+    int2 *glo = scr, *gup = scr + BATCH_MAX_P;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int T0 = 0, T1 = 0;
+    for (int t0 = 0; t0 < p; t0 += RUN) {
+        const int c = t0 + threadIdx.x;
+        const bool valid = c < p && slo[c] <= shi[c];
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, valid);
+        if (lane == 0)
+            s_warp[w] = __popc(bal);
+        __syncthreads();
+        if (w == 0) {
+            const int v = s_warp[lane];
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o)
+                    incl += x;
+            }
+            s_warp[lane] = incl - v;
+            if (lane == 31)
+                *s_cnt = incl;
+        }
+        __syncthreads();
+        const int cnt = *s_cnt;
+        if (valid) {
+            const int r = s_warp[w] + __popc(bal & ((1u << lane) - 1u));
+            P0[r] = make_int2(c + 1, slo[c]);
+            P1[r] = make_int2(c + 1, -shi[c]);
+        }
+        __syncthreads();
+        build_min_trees(P0, M0, P1, M1, cnt);
+        const bool k0 = run_keeps(P0, M0, cnt, threadIdx.x);
+        const bool k1 = run_keeps(P1, M1, cnt, threadIdx.x);
+        T0 += compact_run(P0, k0, glo + T0, s_warp);
+        T1 += compact_run(P1, k1, gup + T1, s_warp);
+        __syncthreads();
+    }
+    const int T = T0 + T1;
+    const bool in_smem = T <= BPCAP;
+    int2 *D = in_smem ? A : scr + 2 * BATCH_MAX_P;  // compact: lower then upper
+    for (int k = threadIdx.x; k < T0; k += BT)
+        D[k] = __ldcg(glo + k);
+    for (int k = threadIdx.x; k < T1; k += BT)
+        D[T0 + k] = __ldcg(gup + k);
+    __syncthreads();
+    int2 *B;
+    int *F, *ix;
+    if (in_smem) {  // L is no longer needed: its region holds the peel scratch
+        B = reinterpret_cast<int2 *>(smem);
+        F = reinterpret_cast<int *>(B + BPCAP);
+        ix = F + BPCAP;
+    } else {  // per-CTA global scratch: lists [0, 2P), D [2P, 4P), F, ix (P = BATCH_MAX_P)
+        B = scr;  // the survivor lists were copied to D already
+        F = reinterpret_cast<int *>(scr + 4 * BATCH_MAX_P);
+        ix = F + 2 * BATCH_MAX_P;
+    }
+    peel_merge_stitch(D, B, F, ix, T0, T, hull, hull_count, s_warp, s_total);
+}
+
+__global__ void __launch_bounds__(BT, 1)
+    k_batched(const int32_t *__restrict__ pts, const BItem *__restrict__ items, int nitems,
+              const BSet *__restrict__ sets, int *queue, int *set_done, uint32_t *part,
+              int2 *hull_out, const int64_t *__restrict__ hull_offsets, int *hull_counts,
+              unsigned char *scratch, unsigned *status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item, s_ticket, s_total, s_cnt;
+    __shared__ int s_warp[33];
+    int *slo = reinterpret_cast<int *>(smem);
+    int2 *scr = reinterpret_cast<int2 *>(scratch + (size_t)blockIdx.x * SCR_BYTES);
+    bool bad = false;
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems)
+            break;
+        const BItem item = items[it];
+        const BSet st = sets[item.set];
+        const int p = st.p;
+        int *shi = slo + p;
+        for (int i = threadIdx.x; i < p; i += BT) {
+            slo[i] = p + 1;
+            shi[i] = -1;
+        }
+        __syncthreads();
+        fold_range(pts + 2 * item.start, item.end - item.start, p, slo, shi, bad);
+        __syncthreads();
+        bool last = true;
+        if (st.nchunks > 1) {
+            uint32_t *row = part + st.part_off + (size_t)item.chunk * p;
+            for (int i = threadIdx.x; i < p; i += BT)
+                __stcg(row + i, slo[i] <= p ? ((uint32_t)(slo[i] - 1) << 16) | (uint32_t)(shi[i] - 1)
+                                            : 0xFFFF0000u);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0)
+                s_ticket = atomicAdd(set_done + item.set, 1);
+            __syncthreads();
+            last = s_ticket == st.nchunks - 1;
+            if (last) {
+                __threadfence();
+                const uint32_t *rows = part + st.part_off;
+                for (int i = threadIdx.x; i < p; i += BT) {
+                    uint32_t lo = 0xFFFFu, hi = 0;
+                    for (int r = 0; r < st.nchunks; ++r) {
+                        const uint32_t w = __ldcg(rows + (size_t)r * p + i);
+                        lo = min(lo, w >> 16);
+                        hi = max(hi, w & 0xFFFFu);
+                    }
+                    slo[i] = lo <= hi ? (int)lo + 1 : p + 1;
+                    shi[i] = lo <= hi ? (int)hi + 1 : -1;
+                }
+                __syncthreads();
+            }
+        }
+        if (last)
+            finish_set(p, slo, shi, smem, scr, hull_out + hull_offsets[item.set],
+                       hull_counts + item.set, s_warp, &s_total, &s_cnt);
+        __syncthreads();
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0)
+        atomicOr(status, ST_RANGE);
+}
+
+struct BatchWs {
+    size_t head, items, sets, part, scratch, end;
+};
+
+// Workspace of a prepared batch: [queue, set_done[B]][items][sets][partials][scratch].
+BatchWs batch_layout(int B, size_t nitems, size_t part_words, int grid)
+{
+    WsLayout w;
+    BatchWs b;
+    b.head = w.take((size_t)(B + 2) * sizeof(int));
+    b.items = w.take(nitems * sizeof(BItem));
+    b.sets = w.take((size_t)B * sizeof(BSet));
+    b.part = w.take(part_words * sizeof(uint32_t));
+    b.scratch = w.take((size_t)grid * SCR_BYTES);
+    b.end = w.off;
+    return b;
+}
+
+void build_plan(int B, const int64_t *off, const int32_t *ps, int chunk_mult,
+                std::vector<BItem> &items, std::vector<BSet> &sets, long long &part_words)
+{
+    items.clear();
+    sets.assign(B, BSet{0, 1, 1});
+    part_words = 0;
+    for (int s = 0; s < B; ++s) {
+        const long long n = off[s + 1] - off[s];
+        const int p = ps[s];
+        // chunk: chunk_mult points per column, at least 64K, at most 4M points
+        const long long chunk = std::min<long long>(std::max<long long>((long long)chunk_mult * p, 65536),
+                                                    1ll << 22);
+        const int nch = (int)std::max<long long>(1, (n + chunk - 1) / chunk);
+        sets[s].p = p;
+        sets[s].nchunks = nch;
+        sets[s].part_off = 0;
+        if (nch > 1) {
+            sets[s].part_off = part_words;
+            part_words += (long long)nch * p;
+        }
+        for (int c = 0; c < nch; ++c) {
+            const long long a = off[s] + (long long)c * chunk;
+            const long long e = std::min<long long>(off[s + 1], a + chunk);
+            items.push_back(BItem{a, e, s, c});
+        }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const BItem &a, const BItem &b) {
+        return (a.end - a.start) > (b.end - b.start);
+    });
+}
+
+}  // namespace
+
+size_t batch_smem() { return BATCH_SMEM; }
+
+int batch_sizes(int B, const int64_t *off, const int32_t *ps, int chunk_mult, size_t *ws_bytes,
+                BatchPlanInfo *info)
+{
+    std::vector<BItem> items;
+    std::vector<BSet> sets;
+    long long pw = 0;
+    build_plan(B, off, ps, chunk_mult, items, sets, pw);
+    const int grid = sm_count();
+    if (grid <= 0)
+        return CH_ERR_CUDA;
+    const BatchWs l = batch_layout(B, items.size(), (size_t)pw, grid);
+    *ws_bytes = l.end;
+    if (info) {
+        info->B = B;
+        info->nitems = (int)items.size();
+        info->grid = grid;
+        info->part_words = pw;
+    }
+    return CH_OK;
+}
+
+int batch_prepare(int B, const int64_t *off, const int32_t *ps, int chunk_mult, void *ws,
+                  size_t ws_bytes, cudaStream_t s, BatchPlanInfo *info)
+{
+    std::vector<BItem> items;
+    std::vector<BSet> sets;
+    long long pw = 0;
+    build_plan(B, off, ps, chunk_mult, items, sets, pw);
+    const int grid = sm_count();
+    if (grid <= 0)
+        return CH_ERR_CUDA;
+    const BatchWs l = batch_layout(B, items.size(), (size_t)pw, grid);
+    if (ws_bytes < l.end)
+        return CH_ERR_WORKSPACE;
+    char *b = reinterpret_cast<char *>(ws);
+    if (cudaMemcpyAsync(b + l.items, items.data(), items.size() * sizeof(BItem),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(b + l.sets, sets.data(), sets.size() * sizeof(BSet),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)  // the host vectors die on return
+        return CH_ERR_CUDA;
+    info->B = B;
+    info->nitems = (int)items.size();
+    info->grid = grid;
+    info->part_words = pw;
+    return CH_OK;
+}
+
+int batch_launch(const int32_t *pts, int2 *hull_out, const int64_t *hull_offsets, int *hull_counts,
+                 void *ws, size_t ws_bytes, const BatchPlanInfo &info, unsigned *status,
+                 cudaStream_t s)
+{
+    const BatchWs l = batch_layout(info.B, (size_t)info.nitems, (size_t)info.part_words, info.grid);
+    if (ws_bytes < l.end)
+        return CH_ERR_WORKSPACE;
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        if (cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)BATCH_SMEM) != cudaSuccess)
+            return CH_ERR_CUDA;
+        attr[dev] = true;
+    }
+    char *b = reinterpret_cast<char *>(ws);
+    int *head = reinterpret_cast<int *>(b + l.head);
+    if (cudaMemsetAsync(head, 0, (size_t)(info.B + 2) * sizeof(int), s) != cudaSuccess)
+        return CH_ERR_CUDA;
+    k_batched<<<info.grid, BT, BATCH_SMEM, s>>>(
+        pts, reinterpret_cast<const BItem *>(b + l.items), info.nitems,
+        reinterpret_cast<const BSet *>(b + l.sets), head, head + 1,
+        reinterpret_cast<uint32_t *>(b + l.part), hull_out, hull_offsets, hull_counts,
+        reinterpret_cast<unsigned char *>(b + l.scratch), status);
+    return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ERR_CUDA;
+}
+
+}  // namespace ch

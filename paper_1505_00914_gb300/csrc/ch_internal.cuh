@@ -93,6 +93,21 @@ cudaError_t hull_launch(const int32_t *lower, const int32_t *upper, const int32_
 cudaError_t hull_final_launch(const HullLayout &h, void *ws, int32_t *hull, int32_t *hull_count,
                               cudaStream_t s);
 
+// ---- batched (batched.cu) ----
+constexpr int BATCH_MAX_P = 16384;  // largest p of a set in a batch
+struct BatchPlanInfo {
+    int B, nitems, grid;
+    long long part_words;
+};
+size_t batch_smem();
+int batch_sizes(int B, const int64_t *off, const int32_t *ps, int chunk_mult, size_t *ws_bytes,
+                BatchPlanInfo *info);
+int batch_prepare(int B, const int64_t *off, const int32_t *ps, int chunk_mult, void *ws,
+                  size_t ws_bytes, cudaStream_t s, BatchPlanInfo *info);
+int batch_launch(const int32_t *pts, int2 *hull_out, const int64_t *hull_offsets, int *hull_counts,
+                 void *ws, size_t ws_bytes, const BatchPlanInfo &info, unsigned *status,
+                 cudaStream_t s);
+
 // ---- api.cu ----
 unsigned *device_status_ptr();  // this device's status word (nullptr on failure)
 int sm_count();

@@ -1,0 +1,115 @@
+"""Parity of the batched path (one persistent launch over many sets) with the
+CPU oracle, set by set; bit-exact hull vertex lists."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1505_00914_gb300 import ch, synth
+from gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+    yield
+    assert ch.ch_sync_status() == ch.CH_OK
+
+
+def run_batch(pts, offsets, ps, chunk_mult=64):
+    d_pts = torch.from_numpy(np.ascontiguousarray(pts, dtype=np.int32).reshape(-1, 2)).cuda()
+    d_off = torch.from_numpy(np.asarray(offsets, np.int64)).cuda()
+    d_ps = torch.from_numpy(np.asarray(ps, np.int32)).cuda()
+    hoff = ch.hull_capacity_offsets(offsets, ps)
+    d_hoff = torch.from_numpy(hoff).cuda()
+    hull = torch.zeros((max(1, int(hoff[-1])), 2), dtype=torch.int32, device="cuda")
+    cnt = torch.full((len(ps),), -7, dtype=torch.int32, device="cuda")
+    nws = ch.ch_batched_workspace_size(offsets, ps, chunk_mult)
+    ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+    ch.ch_batched_prepare(offsets, ps, ws, chunk_mult)
+    ch.ch_hull_batched(d_pts, d_off, d_ps, hull, d_hoff, cnt, ws)
+    torch.cuda.synchronize()
+    return hull.cpu().numpy(), hoff, cnt.cpu().numpy()
+
+
+def check_sets(pts, offsets, ps, hull, hoff, cnt, sets=None):
+    for s in (range(len(ps)) if sets is None else sets):
+        P = pts[offsets[s]:offsets[s + 1]]
+        H = oracle.hull_chain(oracle.reduce(P, int(ps[s])))
+        got = hull[hoff[s]:hoff[s] + cnt[s]]
+        assert cnt[s] == H.shape[0], (s, cnt[s], H.shape[0])
+        np.testing.assert_array_equal(got, H, err_msg=f"set {s}")
+
+
+def test_mixed_small_batch():
+    rng = np.random.default_rng(4)
+    B = 300
+    ps = rng.choice([1, 2, 5, 31, 256, 1000, 1024, 4096, 16384], size=B).astype(np.int32)
+    ns = np.rint(10 ** rng.uniform(0, 5.3, size=B)).astype(np.int64)
+    ns[rng.random(B) < 0.05] = 0
+    dists = ["uniform", "disc", "gaussian", "annulus"]
+    parts = [synth.points(dists[i % 4], int(ns[i]), int(ps[i]), seed=i) for i in range(B)]
+    offsets = np.zeros(B + 1, np.int64)
+    np.cumsum(ns, out=offsets[1:])
+    pts = np.concatenate(parts) if parts else np.zeros((0, 2), np.int32)
+    hull, hoff, cnt = run_batch(pts, offsets, ps)
+    check_sets(pts, offsets, ps, hull, hoff, cnt)
+
+
+def test_multi_chunk_sets_merge():
+    """chunk_mult = 1 cuts every set of more than 65536 points into chunks."""
+    rng = np.random.default_rng(5)
+    ps = np.asarray([256, 1024, 4096, 16384, 16384, 300, 7], np.int32)
+    ns = np.asarray([400_000, 300_001, 200_003, 150_000, 70_000, 1_000_000, 131_073], np.int64)
+    parts = [synth.points(["uniform", "disc", "gaussian", "annulus"][i % 4], int(ns[i]), int(ps[i]),
+                          seed=50 + i) for i in range(len(ps))]
+    offsets = np.zeros(len(ps) + 1, np.int64)
+    np.cumsum(ns, out=offsets[1:])
+    pts = np.concatenate(parts)
+    for cm in (1, 3, 64):
+        hull, hoff, cnt = run_batch(pts, offsets, ps, chunk_mult=cm)
+        check_sets(pts, offsets, ps, hull, hoff, cnt)
+
+
+def test_misaligned_set_starts_and_degenerate_sets():
+    # sets of odd lengths so that most start 8 (not 16) bytes into a pair
+    sets = [np.asarray([[3, 4]] * 5, np.int32), np.asarray([[2, 5], [2, 1], [2, 3]], np.int32),
+            np.asarray([[k, k] for k in range(1, 8)], np.int32), np.zeros((0, 2), np.int32),
+            np.asarray([[1, 1]], np.int32), synth.disc(999, 64, seed=3), synth.uniform(1001, 33, 4)]
+    ps = np.asarray([7, 7, 7, 9, 1, 64, 33], np.int32)
+    offsets = np.zeros(len(sets) + 1, np.int64)
+    np.cumsum([s.shape[0] for s in sets], out=offsets[1:])
+    pts = np.concatenate(sets)
+    hull, hoff, cnt = run_batch(pts, offsets, ps)
+    check_sets(pts, offsets, ps, hull, hoff, cnt)
+
+
+def test_batched_range_error_and_arguments():
+    pts = np.asarray([[1, 1], [9, 2], [3, 3]], np.int32)
+    run_batch(pts, np.asarray([0, 3]), np.asarray([8], np.int32))
+    assert ch.ch_sync_status() == ch.CH_ERR_RANGE
+    with pytest.raises(ch.ChError) as e:
+        ch.ch_batched_workspace_size(np.asarray([0, 3]), np.asarray([20000], np.int32))
+    assert e.value.code == ch.CH_ERR_ARG
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    z = torch.zeros(4, dtype=torch.int64, device="cuda")
+    with pytest.raises(ch.ChError) as e:  # no plan prepared in this workspace
+        ch.ch_hull_batched(torch.zeros((3, 2), dtype=torch.int32, device="cuda"), z,
+                           torch.ones(3, dtype=torch.int32, device="cuda"),
+                           torch.zeros((8, 2), dtype=torch.int32, device="cuda"), z,
+                           torch.zeros(3, dtype=torch.int32, device="cuda"), ws)
+    assert e.value.code == ch.CH_ERR_ARG
+
+
+def test_batched_config_full_size_sampled():
+    """10,000 sets, n log-uniform in [1e2, 1e6], p in {256, 1024, 4096, 16384},
+    uniform/disc/Gaussian: the launch the benchmark times; 200 sets checked."""
+    pts, offsets, ps, _ = synth.batched(10_000, seed=4)
+    hull, hoff, cnt = run_batch(pts, offsets, ps)
+    rng = np.random.default_rng(0)
+    sample = sorted(set(rng.choice(len(ps), size=200, replace=False).tolist())
+                    | {int(np.argmax(np.diff(offsets)))})
+    check_sets(pts, offsets, ps, hull, hoff, cnt, sets=sample)
+    assert np.all(cnt >= 1)
