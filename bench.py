@@ -40,6 +40,8 @@ WORKLOADS = {
     "plain_at_scale": (65536, 1 << 26, ("uniform", "disc", "gaussian")),
     "plain_small": (1024, 100_000, ("uniform",)),
     "projected_shells": (4096, 10_000_000, ("shells",)),
+    # profiling case of the filtered reduction: 268 MB of points, above L2
+    "profile_reduce": (65536, 1 << 25, ("uniform",)),
 }
 
 
@@ -52,18 +54,33 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _traffic_record(kernel_src):
-    """Per-launch DRAM bytes of the reduction kernel from the committed ncu
-    summary, valid only while the kernel source is unchanged."""
+def _kernel_sha(src_path, name):
+    """Digest of one kernel's source text: from the line that names it in a
+    definition to the end of its body (the first line that is a lone "}")."""
+    lines = open(src_path).read().split("\n")
+    start = next(i for i, l in enumerate(lines) if l.strip().startswith(name + "("))
+    while start > 0 and lines[start - 1].strip() and not lines[start - 1].startswith("//"):
+        start -= 1
+    end = next(i for i in range(start, len(lines)) if lines[i] == "}")
+    return hashlib.sha256("\n".join(lines[start:end + 1]).encode()).hexdigest()[:16]
+
+
+def _traffic(kernel, n, p):
+    """DRAM bytes per launch of the reduction kernel from the committed ncu
+    counters, scaled from the captured n to this n (the kernel streams each
+    point once); None when the kernel's source changed since the capture or
+    the capture was at another p."""
     try:
         with open(os.path.join(ROOT, "profiles", "reduce_traffic.json")) as f:
             rec = json.load(f)
-        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-        if rec.get("source_sha") == sha:
-            return rec
+        src = os.path.join(ROOT, "paper_1505_00914_gb300", "csrc", "reduce.cu")
+        if rec.get("kernel") != kernel or rec.get("p") != p:
+            return None
+        if rec.get("kernel_sha") != _kernel_sha(src, kernel):
+            return None
+        return (rec["dram_bytes_read"] + rec["dram_bytes_write"]) * n / rec["n"]
     except Exception:
-        pass
-    return None
+        return None
 
 
 class ClockSampler:
@@ -280,8 +297,7 @@ def run_ours(args):
 
     kernel_bytes = 8 * n + 8 * p  # points read + L produced, per launch
     achieved = kernel_bytes / (red_avg / 1e3) / 1e9
-    src = os.path.join(ROOT, "paper_1505_00914_gb300", "csrc", "reduce.cu")
-    trec = _traffic_record(src)
+    kname = ["k_reduce_private", "k_reduce_filtered", "k_reduce_global"][ch.ch_plan_info(n, p)[0]]
     cpu_v, cpu_dt, cpu_passes = cpu_oracle_rate(p, inputs, args.cpu_budget)
     line = {
         "metric": METRIC,
@@ -300,11 +316,11 @@ def run_ours(args):
                    "distributions": [d for d, _ in inputs], "instances_per_step": len(inputs),
                    "l2": "inputs 8n bytes per instance, larger than L2; no flush"},
         "hbm_frac_step": (pts_step * 8 / (ms / args.steps / 1e3) / 1e9) / peak,
-        "roofline": {"bound": "hbm", "kernel": ["k_reduce_private", "k_reduce_filtered", "k_reduce_global"][ch.ch_plan_info(n, p)[0]],
+        "roofline": {"bound": "hbm", "kernel": kname,
                      "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "algorithmic_bytes_per_launch": kernel_bytes, "avg_launch_ms": red_avg,
-                     "traffic": (trec or {}).get("dram_bytes_per_launch")},
+                     "traffic": _traffic(kname, n, p)},
         "e2e": {"value": e2e_val, "unit": "Gpoints/s", "h2d_bytes_per_step": pts_step * 8,
                 "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps},
         "cpu_baseline": {"value": cpu_v, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
