@@ -198,6 +198,93 @@ int ch_hull_batched(const int32_t *pts, const int64_t *offsets, const int32_t *p
                     int32_t *hull_out, const int64_t *hull_offsets, int32_t *hull_counts,
                     void *workspace, size_t ws_bytes, ch_stream_t stream);
 
+/* ---------------------------------------------------------------------- */
+/* Learned culling proposal: MLP 1024 -> 256 -> 256 -> K on a 32x32        */
+/* occupancy histogram (not in the paper; the hull stays exact whatever    */
+/* the network outputs, see ch_hull_learned).  All pointers are device     */
+/* pointers to row-major float32 arrays; GEMMs run on the tensor cores with */
+/* bf16 operands and fp32 accumulation.                                     */
+/* ---------------------------------------------------------------------- */
+
+#define CH_MLP_IN 1024
+#define CH_MLP_HID 256
+#define CH_MLP_K 16
+/* Parameter vector: W1[1024][256], b1[256], W2[256][256], b2[256],
+ * W3[256][16], b3[16] (W[i][j]: input i to output j), 332304 floats. */
+#define CH_MLP_PARAMS (1024 * 256 + 256 + 256 * 256 + 256 + 256 * 16 + 16)
+
+/* X[M][1024] -> H1 = relu(X W1 + b1), H2 = relu(H1 W2 + b2), Y = H2 W3 + b3
+ * (H1, H2: [M][256], kept for the backward pass; Y: [M][16]). */
+int ch_mlp_forward(const float *params, const float *X, int32_t M, float *H1, float *H2, float *Y,
+                   ch_stream_t stream);
+
+/* Loss of the direction offsets against targets T[M][16] in [-1, 1]:
+ * *loss = mean((tanh(Y) - T)^2) (device float), dY = dloss/dY. */
+int ch_mlp_loss(const float *Y, const float *T, int32_t M, float *dY, float *loss,
+                ch_stream_t stream);
+
+int ch_mlp_backward_workspace_size(int32_t M, size_t *bytes);
+
+/* Gradients of the loss with respect to every parameter (same layout as
+ * params) from the forward activations and dY. */
+int ch_mlp_backward(const float *params, const float *X, const float *H1, const float *H2,
+                    const float *dY, int32_t M, float *grads, void *workspace, size_t ws_bytes,
+                    ch_stream_t stream);
+
+/* One Adam step (step counts from 1) on params with moments m, v. */
+int ch_mlp_adam(float *params, const float *grads, float *m, float *v, int32_t step, float lr,
+                float beta1, float beta2, float eps, ch_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Learned culling (not in the paper; it serves the culling idea that a    */
+/* convex polygon with input points as vertices lies inside the hull, so   */
+/* that the points strictly inside it are no hull vertices).               */
+/*                                                                          */
+/* Sample: runs of CH_CULL_RUN consecutive points starting at j * (n /      */
+/* CH_CULL_RUNS), j < CH_CULL_RUNS (all points when n <= their product).   */
+/* Features: 32 x 32 occupancy histogram of the sample, cell (bx, by) =    */
+/* ((x-1)*32/p, (y-1)*32/p) at index by*32+bx, value count * (1024/m) in   */
+/* float32 (m = sample size).  Network: ch_mlp_forward's, for one vector,  */
+/* giving y[16]; directions theta_k = 2*pi*k/16 + (pi/16)*tanh(y_k) (the    */
+/* sector centres when params is NULL).  Extremes: per direction the sample */
+/* point maximising fl32(fl32(cos*x) + fl32(sin*y)), ties to the smaller    */
+/* index.  Polygon: strict hull of the extremes.  Start array Linit: for    */
+/* columns strictly between the polygon's extreme x values, (floor(b(x))+1, */
+/* ceil(u(x))-1) with b, u its lower and upper boundary; (p+1, -1) else.    */
+/* ---------------------------------------------------------------------- */
+
+#define CH_CULL_RUN 1024
+#define CH_CULL_RUNS 256
+
+int ch_cull_workspace_size(int32_t p, size_t *bytes);
+
+/* The culling proposal alone, with its intermediate results.  Linit: device
+ * int32[p][2] (required).  Optional (NULL to skip) device outputs: features
+ * float[1024], net_out float[16] (y), dirs float[32] (16 cosines then 16
+ * sines), poly int32[16][2] + poly_count (counter-clockwise from the
+ * lexicographic minimum), extremes int64[16] (point indices, -1 if none).
+ * params: device float[CH_MLP_PARAMS] or NULL.  Workspace: device memory of
+ * ch_cull_workspace_size bytes, no initial contents. */
+int ch_cull_propose(const int32_t *pts, int64_t n, int32_t p, const float *params, int32_t *Linit,
+                    float *features, float *net_out, float *dirs, int32_t *poly,
+                    int32_t *poly_count, int64_t *extremes, void *workspace, size_t ws_bytes,
+                    ch_stream_t stream);
+
+int ch_hull_learned_workspace_size(int64_t n, int32_t p, size_t *bytes);
+
+/* Kernels one ch_hull_learned call launches (with_net != 0: params given). */
+int ch_hull_learned_kernel_count(int64_t n, int32_t p, int32_t with_net, int32_t *kernels);
+
+/* The whole path with culling: the proposal above, Algorithm 1 started from
+ * Linit (L = column-wise (min, max) of Linit and the points), chains of the
+ * columns where L moved past Linit (lower: L.lo < Linit.lo, upper: L.hi >
+ * Linit.hi; counts[0], counts[1] may differ), and the strict hull, which is
+ * the same as ch_convex_hull's for every params (NULL included).  Arguments
+ * as in ch_convex_hull; L, Linit, lower, upper, counts may be NULL. */
+int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *params, int32_t *L,
+                    int32_t *Linit, int32_t *lower, int32_t *upper, int32_t *counts, int32_t *hull,
+                    int32_t *hull_count, void *workspace, size_t ws_bytes, ch_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,8 +37,8 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
-                           "-o", tmp, _SRC])
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC",
+                           "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -61,6 +61,9 @@ def _load():
                 "oracle_hull_brute": (i64, [P, i64, P]),
                 "oracle_polygon_init": (ctypes.c_int, [P, i32, i32, P]),
                 "oracle_chain_from": (None, [P, P, i32, P, P, P]),
+                "oracle_best_offsets": (None, [P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]),
+                "oracle_label_batch": (ctypes.c_int, [P, P, P, i64, ctypes.c_int, ctypes.c_int,
+                                                      ctypes.c_int, P, P]),
             }
             for name, (res, args) in sigs.items():
                 f = getattr(lib, name)
@@ -195,3 +198,29 @@ def chain_from(L, Linit) -> tuple[np.ndarray, np.ndarray]:
     cnt = np.zeros(2, dtype=np.int64)
     _load().oracle_chain_from(_ptr(L), _ptr(Linit), p, _ptr(lo), _ptr(up), _ptr(cnt))
     return lo[:cnt[0]].copy(), up[:cnt[1]].copy()
+
+
+def best_offsets(H, K: int = 16, sub: int = 9, rounds: int = 2) -> np.ndarray:
+    """Training label of the learned culling proposal (not in the paper): per
+    sector of directions, the offset (units of pi/K from the sector centre)
+    whose extreme hull vertex maximises the area of the polygon of the K
+    extreme vertices (coordinate ascent over `sub` candidates per sector)."""
+    H = _pts(H)
+    out = np.zeros(K, dtype=np.float32)
+    _load().oracle_best_offsets(_ptr(H), H.shape[0], K, sub, rounds, _ptr(out))
+    return out
+
+
+def label_batch(pts, offsets, ps, K: int = 16, sub: int = 9, rounds: int = 2):
+    """Labels (B, K) float32 and oracle hull sizes (B,) of a ragged batch."""
+    pts = _pts(pts)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    pp = np.ascontiguousarray(np.asarray(ps, dtype=np.int32))
+    B = pp.shape[0]
+    out = np.zeros((B, K), dtype=np.float32)
+    hs = np.zeros(B, dtype=np.int64)
+    rc = _load().oracle_label_batch(_ptr(pts), _ptr(off), _ptr(pp), B, K, sub, rounds, _ptr(out),
+                                    _ptr(hs))
+    if rc == ORC_ERR_RANGE:
+        raise OracleRangeError("point outside [1,p]^2")
+    return out, hs

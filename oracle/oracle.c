@@ -415,3 +415,136 @@ void oracle_chain_from(const int32_t *L, const int32_t *Linit, int32_t p,
     cnt[0] = nl;
     cnt[1] = nu;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Training labels of the learned culling proposal (not in the paper).      */
+/* For a hull H (strict vertices, counter-clockwise) and K sectors of        */
+/* directions [2*pi*k/K - pi/K, 2*pi*k/K + pi/K], choose one direction per   */
+/* sector (`sub` evenly spaced candidates) so that the polygon of the hull   */
+/* vertices extreme in those directions has the largest area; coordinate    */
+/* ascent, `rounds` sweeps from the sector centres.  out[k] = offset of the  */
+/* chosen direction from the sector centre in units of pi/K, in [-1, 1].     */
+/* ------------------------------------------------------------------------ */
+#include <math.h>
+
+static int64_t extreme_vertex(const int32_t *H, int64_t h, double c, double s)
+{
+    int64_t best = 0;
+    double bv = -1e300;
+    for (int64_t i = 0; i < h; ++i) {
+        double v = c * H[2 * i] + s * H[2 * i + 1];
+        if (v > bv) {
+            bv = v;
+            best = i;
+        }
+    }
+    return best;
+}
+
+/* Twice the area of the polygon of the distinct chosen vertices, visited in
+ * the hull's counter-clockwise order. */
+static double chosen_area2(const int32_t *H, int64_t h, const int64_t *idx, int K)
+{
+    int64_t sel[64];
+    int m = 0;
+    for (int k = 0; k < K && m < 64; ++k) {
+        int dup = 0;
+        for (int j = 0; j < m; ++j)
+            if (sel[j] == idx[k])
+                dup = 1;
+        if (!dup)
+            sel[m++] = idx[k];
+    }
+    /* sort by hull order */
+    for (int a = 1; a < m; ++a) {
+        int64_t v = sel[a];
+        int b = a - 1;
+        while (b >= 0 && sel[b] > v) {
+            sel[b + 1] = sel[b];
+            --b;
+        }
+        sel[b + 1] = v;
+    }
+    double s = 0;
+    for (int j = 0; j < m; ++j) {
+        const int32_t *u = &H[2 * sel[j]], *w = &H[2 * sel[(j + 1) % m]];
+        s += (double)u[0] * w[1] - (double)u[1] * w[0];
+    }
+    (void)h;
+    return s;
+}
+
+void oracle_best_offsets(const int32_t *H, int64_t h, int K, int sub, int rounds, float *out)
+{
+    int64_t idx[64];
+    double off[64];
+    if (K > 64)
+        K = 64;
+    for (int k = 0; k < K; ++k) {
+        off[k] = 0.0;
+        if (h == 0) {
+            idx[k] = 0;
+            continue;
+        }
+        double a = 2.0 * M_PI * k / K;
+        idx[k] = extreme_vertex(H, h, cos(a), sin(a));
+    }
+    if (h >= 3) {
+        for (int r = 0; r < rounds; ++r) {
+            for (int k = 0; k < K; ++k) {
+                double best_area = -1, best_off = off[k];
+                int64_t best_idx = idx[k];
+                for (int j = 0; j < sub; ++j) {
+                    double o = sub == 1 ? 0.0 : -1.0 + 2.0 * j / (sub - 1);
+                    double a = 2.0 * M_PI * k / K + o * M_PI / K;
+                    int64_t keep = idx[k];
+                    idx[k] = extreme_vertex(H, h, cos(a), sin(a));
+                    double ar = chosen_area2(H, h, idx, K);
+                    /* prefer the centre on ties */
+                    if (ar > best_area + 1e-9 || (ar > best_area - 1e-9 && fabs(o) < fabs(best_off))) {
+                        best_area = ar;
+                        best_off = o;
+                        best_idx = idx[k];
+                    }
+                    idx[k] = keep;
+                }
+                off[k] = best_off;
+                idx[k] = best_idx;
+            }
+        }
+    }
+    for (int k = 0; k < K; ++k)
+        out[k] = (float)off[k];
+}
+
+/* Labels of B sets: set s = pts[off[s], off[s+1]) of side ps[s]; its hull
+ * from Algorithm 1 + Andrew on the reduced set, then oracle_best_offsets. */
+int oracle_label_batch(const int32_t *pts, const int64_t *off, const int32_t *ps, int64_t B, int K,
+                       int sub, int rounds, float *out, int64_t *hull_sizes)
+{
+    int32_t *L = NULL, *Hb = NULL;
+    int64_t capL = 0;
+    for (int64_t s = 0; s < B; ++s) {
+        int32_t p = ps[s];
+        if ((int64_t)p > capL) {
+            free(L);
+            free(Hb);
+            capL = p;
+            L = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)p);
+            Hb = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(2 * p + 2));
+        }
+        int rc = oracle_reduce(pts + 2 * off[s], off[s + 1] - off[s], p, L);
+        if (rc != ORC_OK) {
+            free(L);
+            free(Hb);
+            return rc;
+        }
+        int64_t h = oracle_hull_chain(L, p, Hb);
+        if (hull_sizes)
+            hull_sizes[s] = h;
+        oracle_best_offsets(Hb, h, K, sub, rounds, out + (size_t)s * K);
+    }
+    free(L);
+    free(Hb);
+    return ORC_OK;
+}

@@ -59,6 +59,17 @@ def _declare(lib):
         "ch_convex_hull": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P, sz, P]),
         "ch_convex_hull_host_workspace_size": (ctypes.c_int, [i64, i32, szp]),
         "ch_convex_hull_host": (ctypes.c_int, [P, i64, i32, P, ctypes.POINTER(ctypes.c_int32), P, sz, P]),
+        "ch_mlp_forward": (ctypes.c_int, [P, P, i32, P, P, P, P]),
+        "ch_mlp_loss": (ctypes.c_int, [P, P, i32, P, P, P]),
+        "ch_mlp_backward_workspace_size": (ctypes.c_int, [i32, szp]),
+        "ch_mlp_backward": (ctypes.c_int, [P, P, P, P, P, i32, P, P, sz, P]),
+        "ch_mlp_adam": (ctypes.c_int, [P, P, P, P, i32, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_float, ctypes.c_float, P]),
+        "ch_cull_workspace_size": (ctypes.c_int, [i32, szp]),
+        "ch_cull_propose": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P, P, P, sz, P]),
+        "ch_hull_learned_workspace_size": (ctypes.c_int, [i64, i32, szp]),
+        "ch_hull_learned_kernel_count": (ctypes.c_int, [i64, i32, i32, ctypes.POINTER(i32)]),
+        "ch_hull_learned": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P, P, P, sz, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -307,3 +318,121 @@ def hull_capacity_offsets(offsets, ps):
     out = np.zeros(pp.shape[0] + 1, dtype=np.int64)
     np.cumsum(cap, out=out[1:])
     return out
+
+
+# ---------------------------------------------------------------- MLP
+CH_MLP_IN, CH_MLP_HID, CH_MLP_K = 1024, 256, 16
+CH_MLP_PARAMS = CH_MLP_IN * CH_MLP_HID + CH_MLP_HID + CH_MLP_HID * CH_MLP_HID + CH_MLP_HID \
+    + CH_MLP_HID * CH_MLP_K + CH_MLP_K
+
+
+def _f32(t, shape=None, name="tensor"):
+    if t.dtype != torch.float32 or not t.is_contiguous() or not t.is_cuda:
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+def ch_mlp_forward(params, X, H1=None, H2=None, Y=None, stream=None):
+    """Returns (H1, H2, Y) of the batch X (M, 1024)."""
+    _f32(params, (CH_MLP_PARAMS,), "params")
+    M = X.shape[0]
+    _f32(X, (M, CH_MLP_IN), "X")
+    dev = X.device
+    H1 = H1 if H1 is not None else torch.empty((M, CH_MLP_HID), dtype=torch.float32, device=dev)
+    H2 = H2 if H2 is not None else torch.empty((M, CH_MLP_HID), dtype=torch.float32, device=dev)
+    Y = Y if Y is not None else torch.empty((M, CH_MLP_K), dtype=torch.float32, device=dev)
+    _check(lib().ch_mlp_forward(_ptr(params), _ptr(X), M, _ptr(H1), _ptr(H2), _ptr(Y),
+                                _stream(stream)), "ch_mlp_forward")
+    return H1, H2, Y
+
+
+def ch_mlp_loss(Y, T, dY=None, loss=None, stream=None):
+    """Returns (loss (1,), dY) for targets T (M, 16)."""
+    M = Y.shape[0]
+    _f32(Y, (M, CH_MLP_K), "Y")
+    _f32(T, (M, CH_MLP_K), "T")
+    dY = dY if dY is not None else torch.empty_like(Y)
+    loss = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=Y.device)
+    _check(lib().ch_mlp_loss(_ptr(Y), _ptr(T), M, _ptr(dY), _ptr(loss), _stream(stream)),
+           "ch_mlp_loss")
+    return loss, dY
+
+
+def ch_mlp_backward(params, X, H1, H2, dY, grads=None, workspace=None, stream=None):
+    M = X.shape[0]
+    grads = grads if grads is not None else torch.empty_like(params)
+    ws = _ws(_size(lib().ch_mlp_backward_workspace_size, M), X.device, workspace)
+    _check(lib().ch_mlp_backward(_ptr(params), _ptr(X), _ptr(H1), _ptr(H2), _ptr(dY), M,
+                                 _ptr(grads), _ptr(ws), ws.numel(), _stream(stream)),
+           "ch_mlp_backward")
+    return grads
+
+
+def ch_mlp_adam(params, grads, m, v, step: int, lr: float, beta1: float = 0.9,
+                beta2: float = 0.999, eps: float = 1e-8, stream=None):
+    _check(lib().ch_mlp_adam(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(step), lr, beta1,
+                             beta2, eps, _stream(stream)), "ch_mlp_adam")
+
+
+# ---------------------------------------------------------------- learned culling
+def ch_cull_workspace_size(p: int) -> int:
+    return _size(lib().ch_cull_workspace_size, int(p))
+
+
+def ch_cull_propose(pts, p: int, params=None, workspace=None, stream=None):
+    """The culling proposal and its intermediate results, as a dict of device
+    tensors: Linit (p, 2), features (1024,), net_out (16,), dirs (2, 16),
+    poly (16, 2) with poly_count (1,), extremes (16,) int64."""
+    pts = _pts(pts)
+    dev = _dev(pts)
+    if params is not None:
+        _f32(params, (CH_MLP_PARAMS,), "params")
+    out = {
+        "Linit": torch.empty((p, 2), dtype=torch.int32, device=dev),
+        "features": torch.empty(CH_MLP_IN, dtype=torch.float32, device=dev),
+        "net_out": torch.zeros(CH_MLP_K, dtype=torch.float32, device=dev),
+        "dirs": torch.empty((2, CH_MLP_K), dtype=torch.float32, device=dev),
+        "poly": torch.zeros((CH_MLP_K, 2), dtype=torch.int32, device=dev),
+        "poly_count": torch.empty(1, dtype=torch.int32, device=dev),
+        "extremes": torch.empty(CH_MLP_K, dtype=torch.int64, device=dev),
+    }
+    ws = _ws(ch_cull_workspace_size(p), dev, workspace)
+    o = out
+    _check(lib().ch_cull_propose(_ptr(pts), pts.shape[0], int(p), _ptr(params), _ptr(o["Linit"]),
+                                 _ptr(o["features"]), _ptr(o["net_out"]), _ptr(o["dirs"]),
+                                 _ptr(o["poly"]), _ptr(o["poly_count"]), _ptr(o["extremes"]),
+                                 _ptr(ws), ws.numel(), _stream(stream)), "ch_cull_propose")
+    return out
+
+
+def ch_hull_learned_workspace_size(n: int, p: int) -> int:
+    return _size(lib().ch_hull_learned_workspace_size, int(n), int(p))
+
+
+def ch_hull_learned_kernel_count(n: int, p: int, with_net: bool) -> int:
+    k = ctypes.c_int32(0)
+    _check(lib().ch_hull_learned_kernel_count(int(n), int(p), int(bool(with_net)), ctypes.byref(k)),
+           "ch_hull_learned_kernel_count")
+    return int(k.value)
+
+
+def ch_hull_learned(pts, p: int, params=None, L=None, Linit=None, lower=None, upper=None,
+                    counts=None, hull=None, hull_count=None, workspace=None, stream=None):
+    """The whole path with the culling proposal; returns (hull, hull_count)."""
+    pts = _pts(pts)
+    dev = _dev(pts)
+    n = pts.shape[0]
+    if params is not None:
+        _f32(params, (CH_MLP_PARAMS,), "params")
+    if hull is None:
+        hull = torch.empty((2 * p, 2), dtype=torch.int32, device=dev)
+    if hull_count is None:
+        hull_count = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = _ws(ch_hull_learned_workspace_size(n, p), dev, workspace)
+    _check(lib().ch_hull_learned(_ptr(pts), n, int(p), _ptr(params), _ptr(L), _ptr(Linit),
+                                 _ptr(lower), _ptr(upper), _ptr(counts), _ptr(hull),
+                                 _ptr(hull_count), _ptr(ws), ws.numel(), _stream(stream)),
+           "ch_hull_learned")
+    return hull, hull_count

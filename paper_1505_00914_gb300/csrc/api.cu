@@ -1,6 +1,7 @@
 // C ABI of libch.so (declared in include/ch.h): argument checks, workspace
 // layouts, the per-device status word and launch sequencing.  No entry point
 // allocates device memory; every launch goes to the caller's stream.
+#include <cmath>
 #include <map>
 #include <mutex>
 
@@ -410,6 +411,221 @@ int ch_hull_batched(const int32_t *pts, const int64_t *offsets, const int32_t *p
         return CH_ERR_CUDA;
     return batch_launch(pts, reinterpret_cast<int2 *>(hull_out), hull_offsets, hull_counts,
                         workspace, ws_bytes, info, st, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------- MLP
+namespace {
+constexpr long long OFF_W1 = 0, OFF_B1 = OFF_W1 + (long long)CH_MLP_IN * CH_MLP_HID;
+constexpr long long OFF_W2 = OFF_B1 + CH_MLP_HID, OFF_B2 = OFF_W2 + (long long)CH_MLP_HID * CH_MLP_HID;
+constexpr long long OFF_W3 = OFF_B2 + CH_MLP_HID, OFF_B3 = OFF_W3 + (long long)CH_MLP_HID * CH_MLP_K;
+static_assert(OFF_B3 + CH_MLP_K == CH_MLP_PARAMS, "parameter layout");
+}  // namespace
+
+int ch_mlp_forward(const float *params, const float *X, int32_t M, float *H1, float *H2, float *Y,
+                   ch_stream_t stream)
+{
+    if (M < 0 || (M > 0 && (!params || !X || !H1 || !H2 || !Y)))
+        return CH_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const float *w = params;
+    const int I = CH_MLP_IN, H = CH_MLP_HID, K = CH_MLP_K;
+    cudaError_t e = gemm_launch(X, I, 1, w + OFF_W1, H, 1, H1, H, M, H, I, w + OFF_B1, 1, nullptr, 0,
+                                0.f, s);
+    if (e == cudaSuccess)
+        e = gemm_launch(H1, H, 1, w + OFF_W2, H, 1, H2, H, M, H, H, w + OFF_B2, 1, nullptr, 0, 0.f, s);
+    if (e == cudaSuccess)
+        e = gemm_launch(H2, H, 1, w + OFF_W3, K, 1, Y, K, M, K, H, w + OFF_B3, 0, nullptr, 0, 0.f, s);
+    return cuda_rc(e);
+}
+
+int ch_mlp_loss(const float *Y, const float *T, int32_t M, float *dY, float *loss,
+                ch_stream_t stream)
+{
+    if (M < 0 || (M > 0 && (!Y || !T || !dY || !loss)))
+        return CH_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), s);
+    if (e == cudaSuccess && M > 0)
+        e = tanh_mse_launch(Y, T, M * CH_MLP_K, dY, loss, s);
+    return cuda_rc(e);
+}
+
+int ch_mlp_backward_workspace_size(int32_t M, size_t *bytes)
+{
+    if (!bytes || M < 0)
+        return CH_ERR_ARG;
+    *bytes = 2 * (size_t)M * CH_MLP_HID * sizeof(float);
+    return CH_OK;
+}
+
+int ch_mlp_backward(const float *params, const float *X, const float *H1, const float *H2,
+                    const float *dY, int32_t M, float *grads, void *workspace, size_t ws_bytes,
+                    ch_stream_t stream)
+{
+    if (M < 1 || !params || !X || !H1 || !H2 || !dY || !grads)
+        return CH_ERR_ARG;
+    if (ws_bytes < 2 * (size_t)M * CH_MLP_HID * sizeof(float) || !workspace)
+        return CH_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int I = CH_MLP_IN, H = CH_MLP_HID, K = CH_MLP_K;
+    const float *w = params;
+    float *g = grads;
+    float *dH2 = reinterpret_cast<float *>(workspace), *dH1 = dH2 + (size_t)M * H;
+    cudaError_t e = gemm_launch(H2, 1, H, dY, K, 1, g + OFF_W3, K, H, K, M, nullptr, 0, nullptr, 0,
+                                0.f, s);  // dW3 = H2^T dY
+    if (e == cudaSuccess)
+        e = colsum_launch(dY, K, M, K, g + OFF_B3, s);
+    if (e == cudaSuccess)  // dH2 = (dY W3^T) . [H2 > 0]
+        e = gemm_launch(dY, K, 1, w + OFF_W3, 1, K, dH2, H, M, H, K, nullptr, 2, H2, H, 0.f, s);
+    if (e == cudaSuccess)
+        e = gemm_launch(H1, 1, H, dH2, H, 1, g + OFF_W2, H, H, H, M, nullptr, 0, nullptr, 0, 0.f, s);
+    if (e == cudaSuccess)
+        e = colsum_launch(dH2, H, M, H, g + OFF_B2, s);
+    if (e == cudaSuccess)  // dH1 = (dH2 W2^T) . [H1 > 0]
+        e = gemm_launch(dH2, H, 1, w + OFF_W2, 1, H, dH1, H, M, H, H, nullptr, 2, H1, H, 0.f, s);
+    if (e == cudaSuccess)
+        e = gemm_launch(X, 1, I, dH1, H, 1, g + OFF_W1, H, I, H, M, nullptr, 0, nullptr, 0, 0.f, s);
+    if (e == cudaSuccess)
+        e = colsum_launch(dH1, H, M, H, g + OFF_B1, s);
+    return cuda_rc(e);
+}
+
+int ch_mlp_adam(float *params, const float *grads, float *m, float *v, int32_t step, float lr,
+                float beta1, float beta2, float eps, ch_stream_t stream)
+{
+    if (!params || !grads || !m || !v || step < 1)
+        return CH_ERR_ARG;
+    const double c1 = 1.0 - std::pow((double)beta1, step), c2 = 1.0 - std::pow((double)beta2, step);
+    const float lr_t = (float)(lr * std::sqrt(c2) / c1);
+    return cuda_rc(adam_launch(params, grads, m, v, CH_MLP_PARAMS, lr_t, beta1, beta2, eps,
+                               reinterpret_cast<cudaStream_t>(stream)));
+}
+
+// ---------------------------------------------------------------- learned culling
+namespace {
+struct LearnedWs {
+    PathWs path;
+    size_t cull, Linit, end;
+};
+
+int learned_layout(int64_t n, int p, LearnedWs *w)
+{
+    int rc = path_layout(n, p, &w->path);
+    if (rc != CH_OK)
+        return rc;
+    WsLayout l;
+    l.off = w->path.end;
+    w->cull = l.take(cull_ws_bytes(p));
+    w->Linit = l.take((size_t)p * 8);
+    w->end = l.off;
+    return CH_OK;
+}
+}  // namespace
+
+int ch_cull_workspace_size(int32_t p, size_t *bytes)
+{
+    if (!bytes || p < 1 || p > CH_MAX_P)
+        return CH_ERR_ARG;
+    *bytes = cull_ws_bytes(p);
+    return CH_OK;
+}
+
+int ch_cull_propose(const int32_t *pts, int64_t n, int32_t p, const float *params, int32_t *Linit,
+                    float *features, float *net_out, float *dirs, int32_t *poly,
+                    int32_t *poly_count, int64_t *extremes, void *workspace, size_t ws_bytes,
+                    ch_stream_t stream)
+{
+    if (check_np(n, p) != CH_OK || (n > 0 && !pts) || !Linit || !aligned8(pts) ||
+        !aligned8(Linit) || !aligned8(poly))
+        return CH_ERR_ARG;
+    if (ws_bytes < cull_ws_bytes(p) || !workspace)
+        return CH_ERR_WORKSPACE;
+    return cuda_rc(cull_launch(pts, n, p, params, workspace, Linit, nullptr, nullptr, 0, nullptr, 0,
+                               features, net_out, dirs, poly, poly_count, extremes,
+                               reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int ch_hull_learned_workspace_size(int64_t n, int32_t p, size_t *bytes)
+{
+    if (!bytes || check_np(n, p) != CH_OK)
+        return CH_ERR_ARG;
+    LearnedWs w;
+    int rc = learned_layout(n, p, &w);
+    if (rc != CH_OK)
+        return rc;
+    *bytes = w.end;
+    return CH_OK;
+}
+
+int ch_hull_learned_kernel_count(int64_t n, int32_t p, int32_t with_net, int32_t *kernels)
+{
+    if (!kernels || check_np(n, p) != CH_OK)
+        return CH_ERR_ARG;
+    ReducePlan pl;
+    int rc = reduce_plan(n, p, &pl);
+    if (rc != CH_OK)
+        return rc;
+    // culling step, one reduction kernel (+ merge of private copies), chain, final hull
+    *kernels = cull_kernel_count(with_net != 0) + 1 + (pl.mode == 0 ? 1 : 0) + 2;
+    return CH_OK;
+}
+
+int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *params, int32_t *L,
+                    int32_t *Linit, int32_t *lower, int32_t *upper, int32_t *counts, int32_t *hull,
+                    int32_t *hull_count, void *workspace, size_t ws_bytes, ch_stream_t stream)
+{
+    if (check_np(n, p) != CH_OK || (n > 0 && !pts) || !hull || !hull_count || !aligned8(pts) ||
+        !aligned8(L) || !aligned8(Linit) || !aligned8(lower) || !aligned8(upper) || !aligned8(hull))
+        return CH_ERR_ARG;
+    LearnedWs w;
+    int rc = learned_layout(n, p, &w);
+    if (rc != CH_OK)
+        return rc;
+    if (ws_bytes < w.end || !workspace)
+        return CH_ERR_WORKSPACE;
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *b = reinterpret_cast<char *>(workspace);
+    const PathWs &pw = w.path;
+    if (!L)
+        L = reinterpret_cast<int32_t *>(b + pw.L);
+    if (!Linit)
+        Linit = reinterpret_cast<int32_t *>(b + w.Linit);
+    if (!lower)
+        lower = reinterpret_cast<int32_t *>(b + pw.lower);
+    if (!upper)
+        upper = reinterpret_cast<int32_t *>(b + pw.upper);
+    if (!counts)
+        counts = reinterpret_cast<int32_t *>(b + pw.counts);
+    void *part = b + pw.part;
+    unsigned long long *zero = reinterpret_cast<unsigned long long *>(b + pw.state);
+    const int nzero = (int)(chain_state_bytes(p) / 8);
+    const int mode = pw.plan.mode;
+    // the culling step writes Linit, the start of L (filtered forms), the
+    // filter (mode 1) and clears the chain's look-back state
+    cudaError_t e = cull_launch(pts, n, p, params, b + w.cull, Linit, mode != 0 ? L : nullptr,
+                                mode == 1 ? reinterpret_cast<uint16_t *>(part) : nullptr,
+                                pw.plan.shift, zero, nzero, nullptr, nullptr, nullptr, nullptr,
+                                nullptr, nullptr, s);
+    if (e != cudaSuccess)
+        return CH_ERR_CUDA;
+    cudaEvent_t ev0, ev1;
+    next_trace(&ev0, &ev1);
+    e = reduce_launch(pw.plan, pts, n, p, part, L, st, s, nullptr, 0, ev0, ev1, true);
+    if (e == cudaSuccess && mode == 0)
+        e = reduce_merge_launch(part, pw.plan.copies, p, L, s, nullptr, 0, Linit);
+    if (e != cudaSuccess)
+        return CH_ERR_CUDA;
+    const HullLayout hl = hull_layout(p);
+    char *hw = b + pw.hull;
+    e = chain_launch(L, p, lower, upper, counts, nullptr, zero, true,
+                     reinterpret_cast<int2 *>(hw + hl.cand), reinterpret_cast<int *>(hw + hl.ccnt),
+                     st, s, Linit);
+    if (e != cudaSuccess)
+        return CH_ERR_CUDA;
+    return cuda_rc(hull_final_launch(hl, hw, hull, hull_count, s));
 }
 
 int ch_convex_hull_host_workspace_size(int64_t n, int32_t p, size_t *bytes)

@@ -133,7 +133,7 @@ __device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 
             P1[r] = make_int2(c + 1, -shi[c]);
         }
         __syncthreads();
-        build_min_trees(P0, M0, P1, M1, cnt);
+        build_min_trees(P0, M0, cnt, P1, M1, cnt);
         const bool k0 = run_keeps(P0, M0, cnt, threadIdx.x);
         const bool k1 = run_keeps(P1, M1, cnt, threadIdx.x);
         T0 += compact_run(P0, k0, glo + T0, s_warp);

@@ -17,9 +17,9 @@ enum : unsigned {
     ST_TIMEOUT = 4u,
 };
 
-// Iteration cap of every inter-block spin (decoupled look-back).  Each
-// iteration sleeps ~0.1-1 us, so the cap is well above any legal wait and
-// far below a hang.
+// Iteration cap of every inter-block spin (decoupled look-back).  An
+// iteration is one L2 round trip (~1 us at most), so the cap is well above
+// any legal wait and far below a hang.
 constexpr int SPIN_LIMIT = 1 << 22;
 
 // 64-bit orientation of (o, a, b): > 0 for a counter-clockwise turn.
@@ -58,14 +58,21 @@ size_t reduce_partials_bytes(const ReducePlan &plan, int p);
 // zero/nzero: words (the chain look-back state) that the last kernel before
 // the main pass clears, or nullptr.  ev0/ev1: events recorded right before
 // and after the main reduction kernel (the dominant one), or nullptr.
+// prefilled: the culling step has already written L (modes 1-2) and the
+// filter (mode 1, at the start of `scratch`), so the warm-up is skipped.
 cudaError_t reduce_launch(const ReducePlan &plan, const int32_t *pts, int64_t n, int p,
                           void *scratch, int32_t *L, unsigned *status, cudaStream_t s,
                           unsigned long long *zero = nullptr, int nzero = 0,
-                          cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+                          cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
+                          bool prefilled = false);
 int reduce_kernel_count(const ReducePlan &plan);
-// L = column-wise merge of `copies` packed partial arrays.
+// L = column-wise merge of `copies` packed partial arrays (folded with the
+// culling start array Linit when given).
 cudaError_t reduce_merge_launch(const void *partials, int copies, int p, int32_t *L,
-                                cudaStream_t s, unsigned long long *zero = nullptr, int nzero = 0);
+                                cudaStream_t s, unsigned long long *zero = nullptr, int nzero = 0,
+                                const int32_t *Linit = nullptr);
+// Filter shift of the filtered form: (p - 1) >> shift <= 255.
+int reduce_filter_shift(int p);
 
 // ---- chain (chain.cu) ----
 int chain_tiles(int p);
@@ -74,9 +81,11 @@ size_t chain_state_bytes(int p);
 // each 1024-column tile and writes its survivors in the hull layout (so that
 // hull_final_launch can follow directly).  state: chain_state_bytes(p),
 // zeroed here unless state_zeroed.
+// Linit != nullptr: chains of a culled reduction (see k_chain); counts[0] and
+// counts[1] then differ.
 cudaError_t chain_launch(const int32_t *L, int p, int32_t *lower, int32_t *upper, int32_t *counts,
                          uint32_t *mask, void *state, bool state_zeroed, int2 *cand, int *ccnt,
-                         unsigned *status, cudaStream_t s);
+                         unsigned *status, cudaStream_t s, const int32_t *Linit = nullptr);
 
 // ---- hull (hull.cu) ----
 struct HullLayout {
@@ -107,6 +116,34 @@ int batch_prepare(int B, const int64_t *off, const int32_t *ps, int chunk_mult, 
 int batch_launch(const int32_t *pts, int2 *hull_out, const int64_t *hull_offsets, int *hull_counts,
                  void *ws, size_t ws_bytes, const BatchPlanInfo &info, unsigned *status,
                  cudaStream_t s);
+
+// ---- MLP (mlp.cu) ----
+// C[M x N] = epi(A[M x K] B[K x N] (+ bias)) (+ beta * C); element (r, c) of A
+// at A[r * a_sr + c * a_sc], likewise B.  epi: 0 plain, 1 ReLU, 2 times
+// (mask[r * ldm + c] > 0).
+cudaError_t gemm_launch(const float *A, long long a_sr, long long a_sc, const float *B, long long b_sr,
+                        long long b_sc, float *C, long long ldc, int M, int N, int K,
+                        const float *bias, int epi, const float *mask, long long ldm, float beta,
+                        cudaStream_t s);
+cudaError_t colsum_launch(const float *X, long long ld, int M, int N, float *out, cudaStream_t s);
+cudaError_t tanh_mse_launch(const float *Y, const float *T, int count, float *dY, float *loss,
+                            cudaStream_t s);
+cudaError_t adam_launch(float *w, const float *g, float *m, float *v, long long n, float lr_t,
+                        float b1, float b2, float eps, cudaStream_t s);
+
+// ---- learned culling (cull.cu) ----
+size_t cull_ws_bytes(int p);
+// Sample histogram -> network (params != nullptr; else the K sector centres)
+// -> extreme sample points -> culling polygon -> Linit for every column.  L
+// and G (filter words) are written too when given; zero/nzero as in
+// reduce_launch.  features, y_out, dirs_out, poly_out, poly_count, ext_out
+// are optional diagnostic outputs.
+cudaError_t cull_launch(const int32_t *pts, int64_t n, int p, const float *params, void *ws,
+                        int32_t *Linit, int32_t *L, uint16_t *G, int shift,
+                        unsigned long long *zero, int nzero, float *features, float *y_out,
+                        float *dirs_out, int32_t *poly_out, int32_t *poly_count, int64_t *ext_out,
+                        cudaStream_t s);
+int cull_kernel_count(bool net);
 
 // ---- api.cu ----
 unsigned *device_status_ptr();  // this device's status word (nullptr on failure)

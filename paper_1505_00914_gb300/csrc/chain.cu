@@ -109,14 +109,24 @@ struct FilterSmem {
     short M[2][2 * TILE];
 };
 
-template <bool FILTER>
+// CULL: the chains of a culled reduction (L started from a culling start
+// array Linit): column c has a lower point when L[c].lo < Linit[c].lo and an
+// upper point when L[c].hi > Linit[c].hi, so the two chains are ranked
+// separately; the look-back then carries both counts in one word
+// ((lower << 31) | upper, no carry since each total is below 2^31).  Without
+// culling Linit is (p+1, -1) everywhere and both tests reduce to "column
+// non-empty".
+constexpr int CNT_SHIFT = 31;
+constexpr long long CNT_LOW = (1ll << CNT_SHIFT) - 1;
+
+template <bool FILTER, bool CULL>
 __global__ void __launch_bounds__(TILE)
-    k_chain(const int2 *__restrict__ L, int p, int2 *lower, int2 *upper, int *counts,
-            uint32_t *mask, unsigned long long *state, int ntiles, int2 *cand, int *ccnt,
-            unsigned *status)
+    k_chain(const int2 *__restrict__ L, const int2 *__restrict__ Linit, int p, int2 *lower,
+            int2 *upper, int *counts, uint32_t *mask, unsigned long long *state, int ntiles,
+            int2 *cand, int *ccnt, unsigned *status)
 {
-    __shared__ int s_tile, s_cnt;
-    __shared__ int s_wc[WPB + 1];
+    __shared__ int s_tile, s_cnt0, s_cnt1;
+    __shared__ int s_wc[2][WPB + 1];
     __shared__ long long s_prefix;
     __shared__ typename std::conditional<FILTER, FilterSmem, int>::type fs;
     if (threadIdx.x == 0)
@@ -126,42 +136,59 @@ __global__ void __launch_bounds__(TILE)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int c = tile * TILE + threadIdx.x;  // 0-based column
     const int2 e = c < p ? L[c] : make_int2(p + 1, -1);
-    const bool valid = c < p && !(e.x == p + 1 && e.y == -1);
-    const unsigned bal = __ballot_sync(0xFFFFFFFFu, valid);
+    bool v0, v1;
+    if constexpr (CULL) {
+        const int2 li = c < p ? Linit[c] : make_int2(p + 1, -1);
+        v0 = c < p && e.x < li.x;
+        v1 = c < p && e.y > li.y;
+    } else {
+        v0 = v1 = c < p && !(e.x == p + 1 && e.y == -1);
+    }
+    const unsigned bal0 = __ballot_sync(0xFFFFFFFFu, v0);
+    const unsigned bal1 = CULL ? __ballot_sync(0xFFFFFFFFu, v1) : bal0;
     if (lane == 0) {
-        s_wc[w] = __popc(bal);
+        s_wc[0][w] = __popc(bal0);
+        if (CULL)
+            s_wc[1][w] = __popc(bal1);
         if (mask && c < p)
-            mask[c >> 5] = bal;
+            mask[c >> 5] = bal0;
     }
     __syncthreads();
     if (w == 0) {
-        const int v = s_wc[lane];
-        int incl = v;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o)
-                incl += t;
+        for (int ch = 0; ch < (CULL ? 2 : 1); ++ch) {
+            const int v = s_wc[ch][lane];
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o)
+                    incl += t;
+            }
+            s_wc[ch][lane] = incl - v;
+            if (lane == 31)
+                (ch == 0 ? s_cnt0 : s_cnt1) = incl;
         }
-        s_wc[lane] = incl - v;
         if (lane == 31) {
-            s_cnt = incl;
-            publish_aggregate(state + 1, tile, incl);  // early: successors need only this
+            const long long agg = CULL ? ((long long)s_cnt0 << CNT_SHIFT) | s_cnt1 : s_cnt0;
+            publish_aggregate(state + 1, tile, agg);  // early: successors need only this
         }
     }
     __syncthreads();
-    const int cnt = s_cnt;
-    const int r = s_wc[w] + __popc(bal & ((1u << lane) - 1u));  // rank within the tile
+    const int cnt0 = s_cnt0, cnt1 = CULL ? s_cnt1 : cnt0;
+    const unsigned below = (1u << lane) - 1u;
+    const int r0 = s_wc[0][w] + __popc(bal0 & below);  // ranks within the tile
+    const int r1 = CULL ? s_wc[1][w] + __popc(bal1 & below) : r0;
     if constexpr (FILTER) {
         // the hull pre-filter needs no global position: run it before waiting
-        if (valid) {
-            fs.P[0][r] = make_int2(c + 1, e.x);
-            fs.P[1][r] = make_int2(c + 1, -e.y);
-        }
+        if (v0)
+            fs.P[0][r0] = make_int2(c + 1, e.x);
+        if (v1)
+            fs.P[1][r1] = make_int2(c + 1, -e.y);
         __syncthreads();
-        build_min_trees(fs.P[0], fs.M[0], fs.P[1], fs.M[1], cnt);
-        const bool k0 = run_keeps(fs.P[0], fs.M[0], cnt, threadIdx.x);
-        const bool k1 = run_keeps(fs.P[1], fs.M[1], cnt, threadIdx.x);
+        build_min_trees(fs.P[0], fs.M[0], cnt0, fs.P[1], fs.M[1], cnt1);
+        const bool k0 = run_keeps(fs.P[0], fs.M[0], cnt0, threadIdx.x);
+        const bool k1 = run_keeps(fs.P[1], fs.M[1], cnt1, threadIdx.x);
         __shared__ int s_cw[WPB + 1];
         const int n0 = compact_run(fs.P[0], k0, cand + (size_t)tile * TILE, s_cw);
         const int n1 = compact_run(fs.P[1], k1, cand + ((size_t)ntiles + tile) * TILE, s_cw);
@@ -171,21 +198,24 @@ __global__ void __launch_bounds__(TILE)
         }
     }
     if (w == 0) {
-        const long long pre = warp_look_back(state + 1, tile, cnt, lane, status);
+        const long long agg = CULL ? ((long long)cnt0 << CNT_SHIFT) | cnt1 : cnt0;
+        const long long pre = warp_look_back(state + 1, tile, agg, lane, status);
         if (lane == 0) {
             s_prefix = pre;
             if (tile == ntiles - 1) {
-                counts[0] = (int)(pre + cnt);
-                counts[1] = (int)(pre + cnt);
+                const long long tot = pre + agg;
+                counts[0] = (int)(CULL ? tot >> CNT_SHIFT : tot);
+                counts[1] = (int)(CULL ? tot & CNT_LOW : tot);
             }
         }
     }
     __syncthreads();
-    if (valid) {
-        const long long pos = s_prefix + r;
-        lower[pos] = make_int2(c + 1, e.x);
-        upper[pos] = make_int2(c + 1, e.y);
-    }
+    const long long pre0 = CULL ? s_prefix >> CNT_SHIFT : s_prefix;
+    const long long pre1 = CULL ? s_prefix & CNT_LOW : s_prefix;
+    if (v0)
+        lower[pre0 + r0] = make_int2(c + 1, e.x);
+    if (v1)
+        upper[pre1 + r1] = make_int2(c + 1, e.y);
 }
 
 }  // namespace
@@ -196,7 +226,7 @@ size_t chain_state_bytes(int p) { return (size_t)(chain_tiles(p) + 1) * 8; }
 
 cudaError_t chain_launch(const int32_t *L, int p, int32_t *lower, int32_t *upper, int32_t *counts,
                          uint32_t *mask, void *state, bool state_zeroed, int2 *cand, int *ccnt,
-                         unsigned *status, cudaStream_t s)
+                         unsigned *status, cudaStream_t s, const int32_t *Linit)
 {
     const int nt = chain_tiles(p);
     if (!state_zeroed) {
@@ -205,16 +235,20 @@ cudaError_t chain_launch(const int32_t *L, int p, int32_t *lower, int32_t *upper
             return e;
     }
     auto *st = reinterpret_cast<unsigned long long *>(state);
-    if (cand)
-        k_chain<true><<<nt, TILE, 0, s>>>(reinterpret_cast<const int2 *>(L), p,
-                                          reinterpret_cast<int2 *>(lower),
-                                          reinterpret_cast<int2 *>(upper), counts, mask, st, nt,
-                                          cand, ccnt, status);
+    const int2 *L2 = reinterpret_cast<const int2 *>(L), *Li = reinterpret_cast<const int2 *>(Linit);
+    int2 *lo = reinterpret_cast<int2 *>(lower), *up = reinterpret_cast<int2 *>(upper);
+    if (cand && Linit)
+        k_chain<true, true><<<nt, TILE, 0, s>>>(L2, Li, p, lo, up, counts, mask, st, nt, cand, ccnt,
+                                                status);
+    else if (cand)
+        k_chain<true, false><<<nt, TILE, 0, s>>>(L2, nullptr, p, lo, up, counts, mask, st, nt, cand,
+                                                 ccnt, status);
+    else if (Linit)
+        k_chain<false, true><<<nt, TILE, 0, s>>>(L2, Li, p, lo, up, counts, mask, st, nt, nullptr,
+                                                 nullptr, status);
     else
-        k_chain<false><<<nt, TILE, 0, s>>>(reinterpret_cast<const int2 *>(L), p,
-                                           reinterpret_cast<int2 *>(lower),
-                                           reinterpret_cast<int2 *>(upper), counts, mask, st, nt,
-                                           nullptr, nullptr, status);
+        k_chain<false, false><<<nt, TILE, 0, s>>>(L2, nullptr, p, lo, up, counts, mask, st, nt,
+                                                  nullptr, nullptr, status);
     return cudaGetLastError();
 }
 

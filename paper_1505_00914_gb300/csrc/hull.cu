@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(RUN)
         P[threadIdx.x] = q;
     }
     __syncthreads();
-    build_min_trees(P, M, P, M, nin);
+    build_min_trees(P, M, nin, P, M, nin);
     const bool keep = run_keeps(P, M, nin, threadIdx.x);
     const int n = compact_run(P, keep, cand + (size_t)blockIdx.x * RUN, s_wc);
     if (threadIdx.x == 0)

@@ -23,10 +23,10 @@ constexpr int RUN_LOG = 10;
 // tree_off(k); 2 * RUN shorts hold every level.
 __device__ __forceinline__ int tree_off(int k) { return 2 * RUN - ((2 * RUN) >> (k - 1)); }
 
-// Builds the min-y index trees of two runs, P0[0..n) and P1[0..n), level by
+// Builds the min-y index trees of two runs, P0[0..n0) and P1[0..n1), level by
 // level; every thread of the CTA calls it.
-__device__ __forceinline__ void build_min_trees(const int2 *P0, short *M0, const int2 *P1, short *M1,
-                                                int n)
+__device__ __forceinline__ void build_min_trees(const int2 *P0, short *M0, int n0, const int2 *P1,
+                                                short *M1, int n1)
 {
     const int i = threadIdx.x;
     for (int k = 1; k <= RUN_LOG; ++k) {
@@ -41,8 +41,8 @@ __device__ __forceinline__ void build_min_trees(const int2 *P0, short *M0, const
                 a1 = M1[tree_off(k - 1) + 2 * i];
                 b1 = M1[tree_off(k - 1) + 2 * i + 1];
             }
-            const bool va0 = a0 >= 0 && a0 < n, vb0 = b0 >= 0 && b0 < n;
-            const bool va1 = a1 >= 0 && a1 < n, vb1 = b1 >= 0 && b1 < n;
+            const bool va0 = a0 >= 0 && a0 < n0, vb0 = b0 >= 0 && b0 < n0;
+            const bool va1 = a1 >= 0 && a1 < n1, vb1 = b1 >= 0 && b1 < n1;
             const int ya0 = va0 ? P0[a0].y : 0, yb0 = vb0 ? P0[b0].y : 0;
             const int ya1 = va1 ? P1[a1].y : 0, yb1 = vb1 ? P1[b1].y : 0;
             M0[tree_off(k) + i] = (short)(va0 ? ((vb0 && yb0 < ya0) ? b0 : a0) : (vb0 ? b0 : -1));

@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(RT)
 // thread in flight together), and the groups combine through shared memory.
 __global__ void __launch_bounds__(1024)
     k_merge_partials(const uint32_t *__restrict__ part, int copies, int p, int2 *L,
-                     unsigned long long *zero, int nzero)
+                     unsigned long long *zero, int nzero, const int2 *__restrict__ Linit)
 {
     if (zero && blockIdx.x == 0)
         for (int i = threadIdx.x; i < nzero; i += blockDim.x)
@@ -393,7 +393,12 @@ __global__ void __launch_bounds__(1024)
             lo = min(lo, s_lo[h][v]);
             hi = max(hi, s_hi[h][v]);
         }
-        L[c] = lo <= hi ? make_int2((int)lo + 1, (int)hi + 1) : make_int2(p + 1, -1);
+        int2 r = lo <= hi ? make_int2((int)lo + 1, (int)hi + 1) : make_int2(p + 1, -1);
+        if (Linit) {  // a culled reduction starts from Linit instead of (p+1, -1)
+            const int2 li = Linit[c];
+            r = make_int2(min(r.x, li.x), max(r.y, li.y));
+        }
+        L[c] = r;
     }
 }
 
@@ -496,6 +501,8 @@ int reduce_plan(int64_t n, int p, ReducePlan *pl)
     return CH_OK;
 }
 
+int reduce_filter_shift(int p) { return filter_shift(p); }
+
 int reduce_kernel_count(const ReducePlan &pl)
 {
     return pl.mode == 0 ? 1 : (pl.mode == 1 ? 3 : 2);
@@ -512,7 +519,8 @@ size_t reduce_partials_bytes(const ReducePlan &pl, int p)
 
 cudaError_t reduce_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, int p,
                           void *part, int32_t *L, unsigned *status, cudaStream_t s,
-                          unsigned long long *zero, int nzero, cudaEvent_t ev0, cudaEvent_t ev1)
+                          unsigned long long *zero, int nzero, cudaEvent_t ev0, cudaEvent_t ev1,
+                          bool prefilled)
 {
     auto mark = [&](cudaEvent_t ev) { return ev ? cudaEventRecord(ev, s) : cudaSuccess; };
     if (pl.mode == 0) {
@@ -528,8 +536,9 @@ cudaError_t reduce_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, i
     int2 *L2 = reinterpret_cast<int2 *>(L);
     const int sms = sm_count();
     if (pl.mode == 2) {
-        k_fill_empty<<<std::max(1, std::min((p + 255) / 256, sms * 4)), 256, 0, s>>>(L2, p, zero,
-                                                                                    nzero);
+        if (!prefilled)
+            k_fill_empty<<<std::max(1, std::min((p + 255) / 256, sms * 4)), 256, 0, s>>>(L2, p, zero,
+                                                                                        nzero);
         mark(ev0);
         k_reduce_global<<<sms * 8, 256, 0, s>>>(pts, n, p, L2, status);
         mark(ev1);
@@ -538,10 +547,12 @@ cudaError_t reduce_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, i
     uint16_t *G = reinterpret_cast<uint16_t *>(part);
     uint16_t *slots = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(part) +
                                                    ((((size_t)p * 2) + 255) & ~size_t(255)));
-    k_filter_warm<1024><<<pl.grid, 1024, pl.smem, s>>>(pts, n, p, pl.shift, pl.grid, slots);
-    const int words = (p + 7) / 8;
-    k_filter_merge<<<(words + MG_V - 1) / MG_V, MG_V * MG_GROUPS, 0, s>>>(slots, pl.grid, p, G, L2,
-                                                                         zero, nzero);
+    if (!prefilled) {
+        k_filter_warm<1024><<<pl.grid, 1024, pl.smem, s>>>(pts, n, p, pl.shift, pl.grid, slots);
+        const int words = (p + 7) / 8;
+        k_filter_merge<<<(words + MG_V - 1) / MG_V, MG_V * MG_GROUPS, 0, s>>>(slots, pl.grid, p, G,
+                                                                             L2, zero, nzero);
+    }
     mark(ev0);
     k_reduce_filtered<1024><<<pl.grid, 1024, pl.smem, s>>>(pts, n, p, pl.shift, G, L2, status);
     mark(ev1);
@@ -549,11 +560,12 @@ cudaError_t reduce_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, i
 }
 
 cudaError_t reduce_merge_launch(const void *part, int copies, int p, int32_t *L, cudaStream_t s,
-                                unsigned long long *zero, int nzero)
+                                unsigned long long *zero, int nzero, const int32_t *Linit)
 {
     k_merge_partials<<<(p + 31) / 32, 1024, 0, s>>>(reinterpret_cast<const uint32_t *>(part),
                                                          copies, p, reinterpret_cast<int2 *>(L),
-                                                         zero, nzero);
+                                                         zero, nzero,
+                                                         reinterpret_cast<const int2 *>(Linit));
     return cudaGetLastError();
 }
 
