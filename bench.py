@@ -14,6 +14,18 @@ reduction), timed per launch with CUDA events recorded on its stream;
 `cpu_baseline` is the CPU oracle on the host cores.
 
 --impl reference times the CPU oracle itself on the same workload (rank 0 only).
+
+Other workloads (--workload):
+  learned   p = 65536, n = 2^27 per instance, one instance each of uniform,
+            disc, Gaussian and thin annulus (r in [0.45p, 0.5p]); the path
+            with the trained culling network (ch_hull_learned) against the
+            plain path and against culling from the sector centres (no
+            network) on the same inputs, with the cull rates and a check that
+            all three hulls agree.
+  batched   10,000 sets, n log-uniform in [1e2, 1e6], p from {256, 1024,
+            4096, 16384}, uniform/disc/Gaussian by seeded choice, in one
+            ragged buffer: ch_hull_batched (autotuned chunk size, replayed
+            from a captured CUDA graph) against one ch_convex_hull per set.
 """
 from __future__ import annotations
 
@@ -52,6 +64,10 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+KERNEL_OF_FORM = ("k_reduce_private", "k_reduce_filtered", "k_reduce_global",
+                  "k_reduce_filtered_bulk")
 
 
 def _kernel_sha(src_path, name):
@@ -160,31 +176,65 @@ def cpu_oracle_rate(p, inputs, budget_s):
     return done / dt / 1e9, dt, passes
 
 
+def _reference_units(workload):
+    """The workload as a list of (p, name, points) problems for the oracle."""
+    from paper_1505_00914_gb300 import synth
+    if workload == "learned":
+        p, n, dists = LEARNED
+        return [(p, d, synth.points(d, n, p, seed=101 + i)) for i, d in enumerate(dists)]
+    if workload == "batched":
+        pts, off, ps, _ = synth.batched(BATCH_SETS, seed=4)
+        return [(int(ps[s]), f"set{s}", pts[off[s]:off[s + 1]]) for s in range(len(ps))]
+    p, n, inputs = gen_inputs(workload, 0)
+    return [(p, d, P) for d, P in inputs]
+
+
 def run_reference(args):
+    """The CPU oracle as it stands (Algorithm 1 + the hull of the reduced set,
+    single thread) on the same workload.  A step is a bounded sample of it:
+    the whole step for the plain workloads, one instance per step (in turn)
+    for `learned`, the next sets up to 1e8 points for `batched`."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    p, n, inputs = gen_inputs(args.workload, 0)
     import oracle
     oracle.build()
+    units = _reference_units(args.workload)
+    per_step = {"learned": 1}.get(args.workload)
+    cursor = [0]
+
+    def step():
+        done = 0
+        if args.workload == "batched":
+            while done < 100_000_000:
+                p, _, P = units[cursor[0] % len(units)]
+                cursor[0] += 1
+                oracle.hull_chain(oracle.reduce(P, p))
+                done += P.shape[0]
+            return done
+        todo = units if per_step is None else [units[cursor[0] % len(units)]]
+        cursor[0] += 1
+        for p, _, P in todo:
+            oracle.hull_chain(oracle.reduce(P, p))
+            done += P.shape[0]
+        return done
+
     for _ in range(args.warmup):
-        for _, P in inputs[:1]:
-            oracle.hull_chain(oracle.reduce(P, p))
+        step()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for _, P in inputs:
-            oracle.hull_chain(oracle.reduce(P, p))
+    pts = sum(step() for _ in range(args.steps))
     dt = time.perf_counter() - t0
-    pts = args.steps * n * len(inputs)
     v = pts / dt / 1e9
+    sample = {"learned": "one n = 2^27 instance per step, in turn",
+              "batched": "consecutive sets up to 1e8 points per step"}.get(
+                  args.workload, f"the whole step ({len(units)} instances)")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "Gpoints/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "config": {"workload": args.workload, "p": p, "n_per_instance": n,
-                                        "distributions": [d for d, _ in inputs]},
+        "data": "synthetic", "config": {"workload": args.workload, "problems": len(units)},
         "cpu_baseline": {"value": v, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
-                         "sample": f"full workload, {args.steps} steps x {len(inputs)} instances"},
+                         "sample": sample},
         "e2e": {"value": v, "unit": "Gpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -297,7 +347,7 @@ def run_ours(args):
 
     kernel_bytes = 8 * n + 8 * p  # points read + L produced, per launch
     achieved = kernel_bytes / (red_avg / 1e3) / 1e9
-    kname = ["k_reduce_private", "k_reduce_filtered", "k_reduce_global"][ch.ch_plan_info(n, p)[0]]
+    kname = KERNEL_OF_FORM[ch.ch_plan_info(n, p)[0]]
     cpu_v, cpu_dt, cpu_passes = cpu_oracle_rate(p, inputs, args.cpu_budget)
     line = {
         "metric": METRIC,
@@ -335,19 +385,334 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+LEARNED = (65536, 1 << 27, ("uniform", "disc", "gaussian", "annulus"))
+WEIGHTS = os.path.join(ROOT, "paper_1505_00914_gb300", "weights", "cull_mlp_k16.npz")
+BATCH_SETS = 10_000
+
+
+def _setup_dist():
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return torch, dist, world, rank
+
+
+def _max_over_ranks(torch, dist, world, v):
+    if world == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _timed(torch, dist, world, fn, steps, stream):
+    """Device time in ms of `steps` calls of fn, barrier + synchronize on
+    both sides, max over ranks."""
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    return _max_over_ranks(torch, dist, world, a.elapsed_time(b))
+
+
+def run_learned(args):
+    torch, dist, world, rank = _setup_dist()
+    from paper_1505_00914_gb300 import ch, synth, train
+    ch.lib()
+    p, n, dists = LEARNED
+    inputs = [(d, synth.points(d, n, p, seed=101 + 1000 * rank + i)) for i, d in enumerate(dists)]
+    dev_in = [torch.from_numpy(P).cuda() for _, P in inputs]
+    have_w = os.path.exists(WEIGHTS)
+    params = train.load_params(WEIGHTS) if have_w else None
+    nws = max(ch.ch_hull_learned_workspace_size(n, p), ch.ch_convex_hull_workspace_size(n, p))
+    ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    arms = ("learned", "centres", "plain")
+    hulls = {a: [torch.empty((2 * p, 2), dtype=torch.int32, device="cuda") for _ in inputs] for a in arms}
+    hcs = {a: [torch.empty(1, dtype=torch.int32, device="cuda") for _ in inputs] for a in arms}
+    Linit = {a: [torch.empty((p, 2), dtype=torch.int32, device="cuda") for _ in inputs]
+             for a in ("learned", "centres")}
+
+    def step(arm):
+        for i, d in enumerate(dev_in):
+            h, c = hulls[arm][i], hcs[arm][i]
+            if arm == "plain":
+                ch.ch_convex_hull(d, p, hull=h, hull_count=c, workspace=ws, stream=stream)
+            else:
+                ch.ch_hull_learned(d, p, params=params if arm == "learned" else None,
+                                   Linit=Linit[arm][i], hull=h, hull_count=c, workspace=ws,
+                                   stream=stream)
+
+    for arm in arms:
+        for _ in range(args.warmup):
+            step(arm)
+    torch.cuda.synchronize()
+    rc = ch.ch_sync_status()
+    if rc != ch.CH_OK:
+        raise RuntimeError(f"warm-up failed: {ch.strerror(rc)}")
+    # every arm must give the same hull
+    exact = True
+    hv = []
+    for i in range(len(inputs)):
+        ref = hulls["plain"][i][: int(hcs["plain"][i].item())].cpu()
+        hv.append(ref.shape[0])
+        for arm in ("learned", "centres"):
+            got = hulls[arm][i][: int(hcs[arm][i].item())].cpu()
+            exact &= bool(torch.equal(got, ref))
+    # cull rate: share of the points strictly inside the culling polygon,
+    # i.e. Linit.lo <= y <= Linit.hi in their column
+    cull = {}
+    for i, (dname, _) in enumerate(inputs):
+        cull[dname] = {}
+        for arm in ("learned", "centres"):
+            li = Linit[arm][i].long()
+            d = dev_in[i].long()
+            col = li[d[:, 0] - 1]
+            inside = (d[:, 1] >= col[:, 0]) & (d[:, 1] <= col[:, 1])
+            cull[dname][arm] = float(inside.float().mean().item())
+
+    nl = args.steps * len(inputs)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nl)]
+    for a, b in evs:
+        a.record(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    ch.ch_trace_set(evs)
+    ms = {"learned": _timed(torch, dist, world, lambda: step("learned"), args.steps, stream)}
+    ch.ch_trace_set([])
+    for arm in ("plain", "centres"):
+        ms[arm] = _timed(torch, dist, world, lambda arm=arm: step(arm), args.steps, stream)
+    clocks = sampler.stop()
+    rc = ch.ch_sync_status()
+    if rc != ch.CH_OK:
+        raise RuntimeError(f"timed run failed: {ch.strerror(rc)}")
+    red_avg = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+    pts_step = n * len(inputs)
+    rate = {arm: world * pts_step * args.steps / (t / 1e3) / 1e9 for arm, t in ms.items()}
+
+    # e2e: pinned host points -> device, the learned path, hull back to the host
+    e2e_steps = max(1, min(args.steps, 3))
+    host_in = [torch.from_numpy(P).pin_memory() for _, P in inputs]
+    hh = torch.empty((2 * p, 2), dtype=torch.int32).pin_memory()
+    hc_h = torch.empty(1, dtype=torch.int32).pin_memory()
+    d2h = 0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for i, hp in enumerate(host_in):
+            dev_in[i].copy_(hp, non_blocking=True)
+            ch.ch_hull_learned(dev_in[i], p, params=params, hull=hulls["learned"][i],
+                               hull_count=hcs["learned"][i], workspace=ws, stream=stream)
+            hc_h.copy_(hcs["learned"][i], non_blocking=True)
+            torch.cuda.synchronize()
+            k = int(hc_h[0])
+            hh[:k].copy_(hulls["learned"][i][:k], non_blocking=True)
+            torch.cuda.synchronize()
+            d2h += 4 + 8 * k
+    e2e_s = _max_over_ranks(torch, dist, world, time.perf_counter() - w0)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = _peaks()
+    kernel_bytes = 8 * n + 8 * p
+    achieved = kernel_bytes / (red_avg / 1e3) / 1e9
+    cpu_v, cpu_dt, cpu_passes = cpu_oracle_rate(p, inputs[:1], args.cpu_budget)
+    kl = ch.ch_hull_learned_kernel_count(n, p, params is not None)
+    line = {
+        "metric": METRIC, "value": rate["learned"], "unit": "Gpoints/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms["learned"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "learned", "p": p, "n_per_instance": n, "distributions": list(dists),
+                   "instances_per_step": len(inputs),
+                   "network": "trained weights" if have_w else "none found: sector centres",
+                   "l2": "inputs 8n bytes per instance, larger than L2; no flush"},
+        "learned": {"plain_gpoints_s": rate["plain"], "centres_gpoints_s": rate["centres"],
+                    "speedup_vs_plain": rate["learned"] / rate["plain"],
+                    "speedup_vs_centres": rate["learned"] / rate["centres"],
+                    "ms_per_step": {a: t / args.steps for a, t in ms.items()},
+                    "cull_rate": cull, "hulls_identical": exact, "hull_vertices": hv},
+        "roofline": {"bound": "hbm", "kernel": KERNEL_OF_FORM[ch.ch_plan_info(n, p)[0]],
+                     "achieved": achieved,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "algorithmic_bytes_per_launch": kernel_bytes, "avg_launch_ms": red_avg,
+                     "traffic": _traffic(KERNEL_OF_FORM[ch.ch_plan_info(n, p)[0]], n, p)},
+        "e2e": {"value": world * pts_step * e2e_steps / e2e_s / 1e9, "unit": "Gpoints/s",
+                "h2d_bytes_per_step": pts_step * 8, "d2h_bytes_per_step": d2h // e2e_steps,
+                "steps": e2e_steps},
+        "cpu_baseline": {"value": cpu_v, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{cpu_passes} pass(es) over the {inputs[0][0]} instance "
+                                   f"({cpu_dt:.1f} s, single thread, Algorithm 1 + hull)"},
+        "gpu_launches": args.steps * len(inputs) * kl,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_batched(args):
+    torch, dist, world, rank = _setup_dist()
+    from paper_1505_00914_gb300 import autotune, ch, synth
+    ch.lib()
+    pts, off, ps, _ = synth.batched(BATCH_SETS, seed=4 + 1000 * rank)
+    ps = ps.astype(np.int32)
+    B = len(ps)
+    n_tot = int(off[-1])
+    d_pts = torch.from_numpy(pts).cuda()
+    d_off = torch.from_numpy(off).cuda()
+    d_ps = torch.from_numpy(ps).cuda()
+    hoff = ch.hull_capacity_offsets(off, ps)
+    d_hoff = torch.from_numpy(hoff).cuda()
+    hull = torch.zeros((int(hoff[-1]), 2), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(B, dtype=torch.int32, device="cuda")
+    best, tune_ms = autotune.tune_batched(d_pts, off, ps, d_off, d_ps, hull, d_hoff, cnt)
+    ws = torch.empty(ch.ch_batched_workspace_size(off, ps, best), dtype=torch.uint8, device="cuda")
+    ch.ch_batched_prepare(off, ps, ws, best)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ch.ch_hull_batched(d_pts, d_off, d_ps, hull, d_hoff, cnt, ws)  # first call: set-up
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        ch.ch_hull_batched(d_pts, d_off, d_ps, hull, d_hoff, cnt, ws)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    rc = ch.ch_sync_status()
+    if rc != ch.CH_OK:
+        raise RuntimeError(f"warm-up failed: {ch.strerror(rc)}")
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    cur = torch.cuda.current_stream()
+    ms = _timed(torch, dist, world, graph.replay, args.steps, cur)
+    clocks = sampler.stop()
+    # per-set plain launches on the same data (one pass, same stream)
+    pmax = int(ps.max())
+    ws1 = torch.empty(ch.ch_convex_hull_workspace_size(int(np.diff(off).max()), pmax),
+                      dtype=torch.uint8, device="cuda")
+    h1 = torch.empty((B, 2 * pmax, 2), dtype=torch.int32, device="cuda")
+    c1 = torch.empty((B, 1), dtype=torch.int32, device="cuda")
+    views = [d_pts[off[s]:off[s + 1]] for s in range(B)]
+
+    def per_set():
+        for s in range(B):
+            ch.ch_convex_hull(views[s], int(ps[s]), hull=h1[s], hull_count=c1[s], workspace=ws1,
+                              stream=cur)
+
+    per_set()  # warm-up
+    ms_plain = _timed(torch, dist, world, per_set, 1, cur)
+    rc = ch.ch_sync_status()
+    if rc != ch.CH_OK:
+        raise RuntimeError(f"timed run failed: {ch.strerror(rc)}")
+    # identical hulls, set by set
+    cnt_h, c1_h = cnt.cpu().numpy(), c1.cpu().numpy()[:, 0]
+    hull_h, h1_h = hull.cpu().numpy(), h1.cpu().numpy()
+    exact = bool(np.array_equal(cnt_h, c1_h)) and all(
+        np.array_equal(hull_h[hoff[s]:hoff[s] + cnt_h[s]], h1_h[s, :cnt_h[s]]) for s in range(B))
+    # e2e: points from pinned host memory, the graph, hull counts and hulls back
+    host_pts = torch.from_numpy(pts).pin_memory()
+    host_hull = torch.empty_like(hull, device="cpu").pin_memory()
+    host_cnt = torch.empty_like(cnt, device="cpu").pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        d_pts.copy_(host_pts, non_blocking=True)
+        graph.replay()
+        host_cnt.copy_(cnt, non_blocking=True)
+        host_hull.copy_(hull, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = _max_over_ranks(torch, dist, world, time.perf_counter() - w0)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = _peaks()
+    rate = world * n_tot * args.steps / (ms / 1e3) / 1e9
+    kernel_bytes = 8 * n_tot
+    achieved = kernel_bytes / (ms / args.steps / 1e3) / 1e9
+    # CPU oracle on a bounded sample of the sets
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    done = 0
+    s = 0
+    while time.perf_counter() - t0 < args.cpu_budget and s < B:
+        oracle.hull_chain(oracle.reduce(pts[off[s]:off[s + 1]], int(ps[s])))
+        done += int(off[s + 1] - off[s])
+        s += 1
+    cpu_dt = time.perf_counter() - t0
+    line = {
+        "metric": METRIC, "value": rate, "unit": "Gpoints/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "batched", "sets": B, "points": n_tot, "chunk_mult": best,
+                   "ps": [256, 1024, 4096, 16384], "n_range": [100, 1_000_000],
+                   "launch": "one captured CUDA graph replay per step",
+                   "l2": f"{8 * n_tot / 1e9:.1f} GB of points per step, larger than L2; no flush"},
+        "batched": {"per_set_plain_gpoints_s": world * n_tot / (ms_plain / 1e3) / 1e9,
+                    "per_set_plain_ms": ms_plain, "speedup_vs_per_set": ms_plain / (ms / args.steps),
+                    "hulls_identical": exact, "autotune_ms": tune_ms},
+        "roofline": {"bound": "hbm", "kernel": "k_batched", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "algorithmic_bytes_per_launch": kernel_bytes,
+                     "avg_launch_ms": ms / args.steps, "traffic": None},
+        "e2e": {"value": world * n_tot * e2e_steps / e2e_s / 1e9, "unit": "Gpoints/s",
+                "h2d_bytes_per_step": 8 * n_tot,
+                "d2h_bytes_per_step": int(host_hull.numel() * 4 + host_cnt.numel() * 4),
+                "steps": e2e_steps},
+        "cpu_baseline": {"value": done / cpu_dt / 1e9, "unit": "Gpoints/s", "cores": 1,
+                         "kind": "oracle", "sample": f"first {s} of {B} sets ({done} points, "
+                                                     f"{cpu_dt:.1f} s, single thread)"},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="plain_at_scale")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["learned", "batched"],
+                    default="plain_at_scale")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "learned":
+        run_learned(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -95,13 +95,19 @@ def sample_index(n: int) -> np.ndarray:
     return (starts[:, None] + np.arange(R_RUN, dtype=np.int64)[None, :]).reshape(-1)
 
 
-def histogram(pts, p: int) -> np.ndarray:
-    """Occupancy histogram of the given points (no sampling): float32 (1024,)."""
+def histogram_counts(pts, p: int) -> np.ndarray:
+    """Points per cell of the 32 x 32 occupancy grid: int64 (1024,)."""
     pts = np.asarray(pts, dtype=np.int64).reshape(-1, 2)
-    m = pts.shape[0]
     bx = ((pts[:, 0] - 1) * 32) // p
     by = ((pts[:, 1] - 1) * 32) // p
-    counts = np.bincount(by * 32 + bx, minlength=IN).astype(np.float32)
+    return np.bincount(by * 32 + bx, minlength=IN)
+
+
+def histogram(pts, p: int) -> np.ndarray:
+    """Occupancy histogram of the given points (no sampling): float32 (1024,),
+    count * fl32(1024 / m)."""
+    m = np.asarray(pts).reshape(-1, 2).shape[0]
+    counts = histogram_counts(pts, p).astype(np.float32)
     if m == 0:
         return counts
     scale = np.float32(1024.0) / np.float32(m)
