@@ -198,6 +198,22 @@ int ch_hull_batched(const int32_t *pts, const int64_t *offsets, const int32_t *p
                     int32_t *hull_out, const int64_t *hull_offsets, int32_t *hull_counts,
                     void *workspace, size_t ws_bytes, ch_stream_t stream);
 
+/* ch_chain without a workspace (the paper has no counterpart: it is an     */
+/* interface for callers that cannot allocate device memory, e.g. plain C  */
+/* code without a device allocator, or loops that must not call cudaMalloc */
+/* / cudaFree because those synchronise the device).  Same arguments and   */
+/* results as ch_chain; the look-back scratch is a fixed device array of    */
+/* the library sized for p <= CH_CHAIN_NOALLOC_MAX_P (128 KiB); larger p    */
+/* returns CH_ERR_CAPACITY.  Nothing needs to be zeroed by the caller: each */
+/* call clears the scratch words it uses on `stream` before its kernel.     */
+/* The first call on a device looks up the array's address with            */
+/* cudaGetSymbolAddress, so make it before any stream capture begins.  One  */
+/* array serves all calls on a device: calls that overlap in time race on   */
+/* it and must be serialised by the caller. */
+#define CH_CHAIN_NOALLOC_MAX_P (1 << 24)
+int ch_chain_noalloc(const int32_t *L, int32_t p, int32_t *lower, int32_t *upper, int32_t *counts,
+                     uint32_t *mask, ch_stream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* Learned culling proposal: MLP 1024 -> 256 -> 256 -> K on a 32x32        */
 /* occupancy histogram (not in the paper; the hull stays exact whatever    */

@@ -65,6 +65,7 @@ def _declare(lib):
         "ch_mlp_backward": (ctypes.c_int, [P, P, P, P, P, i32, P, P, sz, P]),
         "ch_mlp_adam": (ctypes.c_int, [P, P, P, P, i32, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, ctypes.c_float, P]),
+        "ch_chain_noalloc": (ctypes.c_int, [P, i32, P, P, P, P, P]),
         "ch_cull_workspace_size": (ctypes.c_int, [i32, szp]),
         "ch_cull_propose": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P, P, P, sz, P]),
         "ch_hull_learned_workspace_size": (ctypes.c_int, [i64, i32, szp]),
@@ -210,6 +211,16 @@ def ch_chain(L, p: int | None = None, lower=None, upper=None, counts=None, mask=
     if mask is not None:
         return lower, upper, counts, mask
     return lower, upper, counts
+
+
+CH_CHAIN_NOALLOC_MAX_P = 1 << 24
+
+
+def ch_chain_noalloc(L, p: int, lower, upper, counts, mask=None, stream=None):
+    """ch_chain with the library's own fixed scratch (no workspace, no
+    allocation in the call); outputs are the caller's tensors."""
+    _check(lib().ch_chain_noalloc(_ptr(L), int(p), _ptr(lower), _ptr(upper), _ptr(counts),
+                                  _ptr(mask), _stream(stream)), "ch_chain_noalloc")
 
 
 def ch_hull_workspace_size(p: int) -> int:
