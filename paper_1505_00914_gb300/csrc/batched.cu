@@ -74,13 +74,21 @@ __device__ void fold_range(const int32_t *__restrict__ base, int64_t n, int p, i
             fold(slo, shi, up, base[2 * (n - 1)], base[2 * (n - 1) + 1], bad);
     }
     const int4 *p4 = reinterpret_cast<const int4 *>(base + 2 * head);
+    // U loads in flight per thread; the next U are issued before the current
+    // ones are folded (register double buffering)
     constexpr int U = 4;
+    int4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t j = threadIdx.x + (int64_t)u * BT;
+        v[u] = j < npairs ? __ldcs(p4 + j) : make_int4(0, 0, 0, 0);
+    }
     for (int64_t i = threadIdx.x; i < npairs; i += (int64_t)BT * U) {
-        int4 v[U];
+        int4 nx[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t j = i + (int64_t)u * BT;
-            v[u] = j < npairs ? __ldcs(p4 + j) : make_int4(0, 0, 0, 0);
+            const int64_t j = i + (int64_t)(U + u) * BT;
+            nx[u] = j < npairs ? __ldcs(p4 + j) : make_int4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -89,8 +97,13 @@ __device__ void fold_range(const int32_t *__restrict__ base, int64_t n, int p, i
                 fold(slo, shi, up, v[u].z, v[u].w, bad);
             }
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            v[u] = nx[u];
     }
 }
+
+constexpr int SPARSE_TILE = 64;  // tiles with at most this many columns skip the pre-filter
 
 // Hull of the set whose L is in slo/shi (p columns); whole CTA.
 __device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 *scr,
@@ -127,6 +140,17 @@ __device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 
         }
         __syncthreads();
         const int cnt = *s_cnt;
+        if (cnt <= SPARSE_TILE) {  // few columns: keep them all, the merge copes
+            if (valid) {
+                const int r = s_warp[w] + __popc(bal & ((1u << lane) - 1u));
+                glo[T0 + r] = make_int2(c + 1, slo[c]);
+                gup[T1 + r] = make_int2(c + 1, -shi[c]);
+            }
+            T0 += cnt;
+            T1 += cnt;
+            __syncthreads();  // s_warp and s_cnt are rewritten by the next tile
+            continue;
+        }
         if (valid) {
             const int r = s_warp[w] + __popc(bal & ((1u << lane) - 1u));
             P0[r] = make_int2(c + 1, slo[c]);

@@ -100,8 +100,14 @@ __global__ void __launch_bounds__(SR) k_sample_hist(const int2 *__restrict__ pts
     for (int u = 0; u < HU; ++u) {
         // points outside [1,p]^2 are left out here; the reduction reports them
         if (have[u] && (unsigned)(q[u].x - 1) < up && (unsigned)(q[u].y - 1) < up) {
-            const int bx = (int)(((unsigned long long)(q[u].x - 1) * 32ull) / up);
-            const int by = (int)(((unsigned long long)(q[u].y - 1) * 32ull) / up);
+            int bx, by;
+            if (up <= (1u << 27)) {  // (x-1) * 32 fits 32 bits: the cheap division
+                bx = (int)(((unsigned)(q[u].x - 1) * 32u) / up);
+                by = (int)(((unsigned)(q[u].y - 1) * 32u) / up);
+            } else {
+                bx = (int)(((unsigned long long)(q[u].x - 1) * 32ull) / up);
+                by = (int)(((unsigned long long)(q[u].y - 1) * 32ull) / up);
+            }
             atomicAdd(&h[by * 32 + bx], 1);
         }
     }

@@ -62,6 +62,39 @@ __device__ __forceinline__ PairView pair_view(const int32_t *pts, int64_t n)
     return v;
 }
 
+// Streams the 16-byte pairs [s0, e0) of a CTA's slice: each thread keeps RU
+// loads in flight and issues its next RU before folding the current ones
+// (register double buffering), so the loads never wait for the folding.
+// fold(v) takes one pair of points.  KEEP: load through L2 with the
+// normal policy (the data is read again soon) instead of evict-first.
+template <int RT, bool KEEP = false, typename Fold>
+__device__ __forceinline__ void stream_pairs(const int4 *__restrict__ p4, int64_t s0, int64_t e0,
+                                             Fold &&fold)
+{
+    auto ld = [&](int64_t j) { return KEEP ? __ldcg(p4 + j) : __ldcs(p4 + j); };
+    int4 v[RU];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+        const int64_t j = s0 + threadIdx.x + (int64_t)u * RT;
+        v[u] = j < e0 ? ld(j) : make_int4(0, 0, 0, 0);
+    }
+    for (int64_t i = s0 + threadIdx.x; i < e0; i += (int64_t)RT * RU) {
+        int4 w[RU];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int64_t j = i + (int64_t)(RU + u) * RT;
+            w[u] = j < e0 ? ld(j) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < RU; ++u)
+            if (i + (int64_t)u * RT < e0)
+                fold(v[u]);
+#pragma unroll
+        for (int u = 0; u < RU; ++u)
+            v[u] = w[u];
+    }
+}
+
 // ---------------------------------------------------------------- private
 template <int RT>
 __global__ void __launch_bounds__(RT)
@@ -94,21 +127,10 @@ __global__ void __launch_bounds__(RT)
     const int64_t per = (pv.npairs + gridDim.x - 1) / gridDim.x;
     const int64_t s0 = (int64_t)blockIdx.x * per;
     const int64_t e0 = min(pv.npairs, s0 + per);
-    for (int64_t i = s0 + threadIdx.x; i < e0; i += (int64_t)RT * RU) {
-        int4 v[RU];
-#pragma unroll
-        for (int u = 0; u < RU; ++u) {
-            const int64_t j = i + (int64_t)u * RT;
-            v[u] = j < e0 ? __ldcs(pv.p4 + j) : make_int4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int u = 0; u < RU; ++u) {
-            if (i + (int64_t)u * RT < e0) {
-                fold(v[u].x, v[u].y);
-                fold(v[u].z, v[u].w);
-            }
-        }
-    }
+    stream_pairs<RT>(pv.p4, s0, e0, [&](const int4 &v) {
+        fold(v.x, v.y);
+        fold(v.z, v.w);
+    });
     __syncthreads();
     uint32_t *out = part + (size_t)blockIdx.x * p;
     for (int i = threadIdx.x; i < p; i += RT)
@@ -215,20 +237,10 @@ __global__ void __launch_bounds__(RT)
     int64_t s0, e0;
     slice_of(pv.npairs, blockIdx.x, grid, s0, e0);
     const int64_t warm = s0 + (e0 - s0) / WARM_DIV;
-    constexpr int WU = 4 * RU;  // short loop: more loads in flight
-    for (int64_t i = s0 + threadIdx.x; i < warm; i += (int64_t)RT * WU) {
-        int4 v[WU];
-#pragma unroll
-        for (int u = 0; u < WU; ++u) {
-            const int64_t j = i + (int64_t)u * RT;
-            v[u] = j < warm ? __ldcg(pv.p4 + j) : make_int4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int u = 0; u < WU; ++u) {
-            learn(v[u].x, v[u].y);
-            learn(v[u].z, v[u].w);
-        }
-    }
+    stream_pairs<RT, true>(pv.p4, s0, warm, [&](const int4 &v) {
+        learn(v.x, v.y);
+        learn(v.z, v.w);
+    });
     __syncthreads();
     uint4 *out = reinterpret_cast<uint4 *>(slots) + (size_t)blockIdx.x * words;
     for (int i = threadIdx.x; i < words; i += RT)
@@ -332,21 +344,10 @@ __global__ void __launch_bounds__(RT)
         fold(pts[2 * (n - 1)], pts[2 * (n - 1) + 1]);
     int64_t s0, e0;
     slice_of(pv.npairs, blockIdx.x, gridDim.x, s0, e0);
-    for (int64_t i = s0 + threadIdx.x; i < e0; i += (int64_t)RT * RU) {
-        int4 v[RU];
-#pragma unroll
-        for (int u = 0; u < RU; ++u) {
-            const int64_t j = i + (int64_t)u * RT;
-            v[u] = j < e0 ? __ldcs(pv.p4 + j) : make_int4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int u = 0; u < RU; ++u) {
-            if (i + (int64_t)u * RT < e0) {
-                fold(v[u].x, v[u].y);
-                fold(v[u].z, v[u].w);
-            }
-        }
-    }
+    stream_pairs<RT>(pv.p4, s0, e0, [&](const int4 &v) {
+        fold(v.x, v.y);
+        fold(v.z, v.w);
+    });
     if (__syncthreads_or(bad) && threadIdx.x == 0)
         atomicOr(status, ST_RANGE);
 }
