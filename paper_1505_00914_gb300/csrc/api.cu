@@ -540,8 +540,8 @@ int ch_cull_propose(const int32_t *pts, int64_t n, int32_t p, const float *param
         return CH_ERR_ARG;
     if (ws_bytes < cull_ws_bytes(p) || !workspace)
         return CH_ERR_WORKSPACE;
-    return cuda_rc(cull_launch(pts, n, p, params, workspace, Linit, nullptr, nullptr, 0, nullptr, 0,
-                               features, net_out, dirs, poly, poly_count, extremes,
+    return cuda_rc(cull_launch(pts, n, p, params, workspace, Linit, nullptr, nullptr, false, 0,
+                               nullptr, 0, features, net_out, dirs, poly, poly_count, extremes,
                                reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -565,8 +565,10 @@ int ch_hull_learned_kernel_count(int64_t n, int32_t p, int32_t with_net, int32_t
     int rc = reduce_plan(n, p, &pl);
     if (rc != CH_OK)
         return rc;
-    // culling step, one reduction kernel (+ merge of private copies), chain, final hull
-    *kernels = cull_kernel_count(with_net != 0) + 1 + (pl.mode == 0 ? 1 : 0) + 2;
+    // warm-up (filtered forms), culling step, the reduction (+ merge of
+    // private copies), chain, final hull
+    *kernels = reduce_kernel_count(pl) + cull_kernel_count(with_net != 0) +
+               (pl.mode == 0 ? 1 : 0) + 2;
     return CH_OK;
 }
 
@@ -603,12 +605,16 @@ int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *param
     unsigned long long *zero = reinterpret_cast<unsigned long long *>(b + pw.state);
     const int nzero = (int)(chain_state_bytes(p) / 8);
     const int mode = pw.plan.mode;
-    // the culling step writes Linit, the start of L (filtered forms), the
-    // filter (mode 1) and clears the chain's look-back state
-    cudaError_t e = cull_launch(pts, n, p, params, b + w.cull, Linit, mode != 0 ? L : nullptr,
-                                mode == 1 ? reinterpret_cast<uint16_t *>(part) : nullptr,
-                                pw.plan.shift, zero, nzero, nullptr, nullptr, nullptr, nullptr,
-                                nullptr, nullptr, s);
+    // the filtered forms warm their filter up as the plain path does (and
+    // clear the chain's look-back state); the culling step then writes
+    // Linit, the start of L (filtered forms) and tightens the filter with
+    // the polygon (mode 1); in mode 0 it clears the look-back state itself
+    cudaError_t e = reduce_warm_launch(pw.plan, pts, n, p, part, L, s, zero, nzero);
+    if (e == cudaSuccess)
+        e = cull_launch(pts, n, p, params, b + w.cull, Linit, mode != 0 ? L : nullptr,
+                        mode == 1 ? reinterpret_cast<uint16_t *>(part) : nullptr, mode == 1,
+                        pw.plan.shift, mode == 0 ? zero : nullptr, mode == 0 ? nzero : 0, nullptr,
+                        nullptr, nullptr, nullptr, nullptr, nullptr, s);
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
     cudaEvent_t ev0, ev1;

@@ -29,6 +29,36 @@ __device__ __forceinline__ long long cross3(int2 o, int2 a, int2 b)
            (long long)(a.y - o.y) * (long long)(b.x - o.x);
 }
 
+// Launch with programmatic dependent launch allowed: the grid may be
+// scheduled while the previous kernel of the stream finishes, which hides the
+// launch latency between the dependent kernels of the path.  Every kernel
+// launched this way calls pdl_wait() before it touches global memory, so it
+// still sees (and does not overwrite) anything its predecessor works on, and
+// pdl_trigger() to let its own successor be scheduled.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                         cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// Waits until the previous grid of the stream has completed and its memory
+// operations are visible (a no-op for a grid launched without the attribute).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next grid of the stream be scheduled once every CTA of this grid
+// has issued it (or exited).
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 // Bump allocator for workspace layouts (256-byte aligned regions).
 struct WsLayout {
     size_t off = 0;
@@ -66,6 +96,12 @@ cudaError_t reduce_launch(const ReducePlan &plan, const int32_t *pts, int64_t n,
                           cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
                           bool prefilled = false);
 int reduce_kernel_count(const ReducePlan &plan);
+// The part of reduce_launch before the main pass: mode 1 the filter warm-up
+// and merge (L = (p+1, -1), G ready), mode 2 the fill of L; both clear
+// zero/nzero.  Mode 0 launches nothing.
+cudaError_t reduce_warm_launch(const ReducePlan &plan, const int32_t *pts, int64_t n, int p,
+                               void *scratch, int32_t *L, cudaStream_t s, unsigned long long *zero,
+                               int nzero);
 // L = column-wise merge of `copies` packed partial arrays (folded with the
 // culling start array Linit when given).
 cudaError_t reduce_merge_launch(const void *partials, int copies, int p, int32_t *L,
@@ -135,11 +171,12 @@ cudaError_t adam_launch(float *w, const float *g, float *m, float *v, long long 
 size_t cull_ws_bytes(int p);
 // Sample histogram -> network (params != nullptr; else the K sector centres)
 // -> extreme sample points -> culling polygon -> Linit for every column.  L
-// and G (filter words) are written too when given; zero/nzero as in
+// and G (filter words) are written too when given (G_warm: G holds the
+// warm-up filter, which is tightened rather than replaced); zero/nzero as in
 // reduce_launch.  features, y_out, dirs_out, poly_out, poly_count, ext_out
 // are optional diagnostic outputs.
 cudaError_t cull_launch(const int32_t *pts, int64_t n, int p, const float *params, void *ws,
-                        int32_t *Linit, int32_t *L, uint16_t *G, int shift,
+                        int32_t *Linit, int32_t *L, uint16_t *G, bool G_warm, int shift,
                         unsigned long long *zero, int nzero, float *features, float *y_out,
                         float *dirs_out, int32_t *poly_out, int32_t *poly_count, int64_t *ext_out,
                         cudaStream_t s);

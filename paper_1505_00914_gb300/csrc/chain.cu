@@ -117,6 +117,7 @@ struct FilterSmem {
 // culling Linit is (p+1, -1) everywhere and both tests reduce to "column
 // non-empty".
 constexpr int CNT_SHIFT = 31;
+constexpr int SPARSE_TILE = 64;  // tiles with at most this many points per chain skip the pre-filter
 constexpr long long CNT_LOW = (1ll << CNT_SHIFT) - 1;
 
 template <bool FILTER, bool CULL>
@@ -125,6 +126,8 @@ __global__ void __launch_bounds__(TILE)
             int2 *upper, int *counts, uint32_t *mask, unsigned long long *state, int ntiles,
             int2 *cand, int *ccnt, unsigned *status)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int s_tile, s_cnt0, s_cnt1;
     __shared__ int s_wc[2][WPB + 1];
     __shared__ long long s_prefix;
@@ -181,20 +184,33 @@ __global__ void __launch_bounds__(TILE)
     const int r1 = CULL ? s_wc[1][w] + __popc(bal1 & below) : r0;
     if constexpr (FILTER) {
         // the hull pre-filter needs no global position: run it before waiting
-        if (v0)
-            fs.P[0][r0] = make_int2(c + 1, e.x);
-        if (v1)
-            fs.P[1][r1] = make_int2(c + 1, -e.y);
-        __syncthreads();
-        build_min_trees(fs.P[0], fs.M[0], cnt0, fs.P[1], fs.M[1], cnt1);
-        const bool k0 = run_keeps(fs.P[0], fs.M[0], cnt0, threadIdx.x);
-        const bool k1 = run_keeps(fs.P[1], fs.M[1], cnt1, threadIdx.x);
-        __shared__ int s_cw[WPB + 1];
-        const int n0 = compact_run(fs.P[0], k0, cand + (size_t)tile * TILE, s_cw);
-        const int n1 = compact_run(fs.P[1], k1, cand + ((size_t)ntiles + tile) * TILE, s_cw);
-        if (threadIdx.x == 0) {
-            ccnt[tile] = n0;
-            ccnt[ntiles + tile] = n1;
+        if (cnt0 <= SPARSE_TILE && cnt1 <= SPARSE_TILE) {
+            // few points (a culled chain): all of them are candidates, the
+            // final merge copes, and the tile skips the trees
+            if (v0)
+                cand[(size_t)tile * TILE + r0] = make_int2(c + 1, e.x);
+            if (v1)
+                cand[((size_t)ntiles + tile) * TILE + r1] = make_int2(c + 1, -e.y);
+            if (threadIdx.x == 0) {
+                ccnt[tile] = cnt0;
+                ccnt[ntiles + tile] = cnt1;
+            }
+        } else {
+            if (v0)
+                fs.P[0][r0] = make_int2(c + 1, e.x);
+            if (v1)
+                fs.P[1][r1] = make_int2(c + 1, -e.y);
+            __syncthreads();
+            build_min_trees(fs.P[0], fs.M[0], cnt0, fs.P[1], fs.M[1], cnt1);
+            const bool k0 = run_keeps(fs.P[0], fs.M[0], cnt0, threadIdx.x);
+            const bool k1 = run_keeps(fs.P[1], fs.M[1], cnt1, threadIdx.x);
+            __shared__ int s_cw[WPB + 1];
+            const int n0 = compact_run(fs.P[0], k0, cand + (size_t)tile * TILE, s_cw);
+            const int n1 = compact_run(fs.P[1], k1, cand + ((size_t)ntiles + tile) * TILE, s_cw);
+            if (threadIdx.x == 0) {
+                ccnt[tile] = n0;
+                ccnt[ntiles + tile] = n1;
+            }
         }
     }
     if (w == 0) {
@@ -238,16 +254,16 @@ cudaError_t chain_launch(const int32_t *L, int p, int32_t *lower, int32_t *upper
     const int2 *L2 = reinterpret_cast<const int2 *>(L), *Li = reinterpret_cast<const int2 *>(Linit);
     int2 *lo = reinterpret_cast<int2 *>(lower), *up = reinterpret_cast<int2 *>(upper);
     if (cand && Linit)
-        k_chain<true, true><<<nt, TILE, 0, s>>>(L2, Li, p, lo, up, counts, mask, st, nt, cand, ccnt,
+        launch(k_chain<true, true>, nt, TILE, 0, s, L2, Li, p, lo, up, counts, mask, st, nt, cand, ccnt,
                                                 status);
     else if (cand)
-        k_chain<true, false><<<nt, TILE, 0, s>>>(L2, nullptr, p, lo, up, counts, mask, st, nt, cand,
+        launch(k_chain<true, false>, nt, TILE, 0, s, L2, nullptr, p, lo, up, counts, mask, st, nt, cand,
                                                  ccnt, status);
     else if (Linit)
-        k_chain<false, true><<<nt, TILE, 0, s>>>(L2, Li, p, lo, up, counts, mask, st, nt, nullptr,
+        launch(k_chain<false, true>, nt, TILE, 0, s, L2, Li, p, lo, up, counts, mask, st, nt, nullptr,
                                                  nullptr, status);
     else
-        k_chain<false, false><<<nt, TILE, 0, s>>>(L2, nullptr, p, lo, up, counts, mask, st, nt,
+        launch(k_chain<false, false>, nt, TILE, 0, s, L2, nullptr, p, lo, up, counts, mask, st, nt,
                                                   nullptr, nullptr, status);
     return cudaGetLastError();
 }

@@ -19,7 +19,8 @@
 // k_cull_init    every CTA folds the per-CTA winners, takes the strict hull
 //                of the K winners in one warp (exact int64 orientation), and
 //                writes for its columns the start array Linit, L = Linit and
-//                the filtered reduction's row-bin filter.
+//                the filtered reduction's row-bin filter (tightening the
+//                warm-up filter when there is one).
 // The reduction then runs unchanged from that filter and start array, and
 // the chain step keeps a lower (upper) point only where L moved below
 // (above) Linit.
@@ -81,6 +82,8 @@ __device__ __forceinline__ bool better(float s, long long i, float bs, long long
 __global__ void __launch_bounds__(SR) k_sample_hist(const int2 *__restrict__ pts, long long n, int p,
                                                     int *__restrict__ rows)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int h[NI];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -118,6 +121,8 @@ __global__ void __launch_bounds__(SR) k_sample_hist(const int2 *__restrict__ pts
 // features[i] = fl32(count_i * fl32(1024 / m)) (diagnostic output only)
 __global__ void k_features(const int *__restrict__ rows, float scale, float *__restrict__ X)
 {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NI)
         return;
@@ -135,6 +140,8 @@ __global__ void __launch_bounds__(256)
     k_gemv1(const int *__restrict__ rows, float scale, const float *__restrict__ W,
             float *__restrict__ part)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float xs[KC];
     __shared__ float red[8][32];
     const int jc = blockIdx.x, kc = blockIdx.y;
@@ -176,6 +183,8 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_gemv2(const float *__restrict__ part1, const float *__restrict__ W, float *__restrict__ part2)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float hs[KC];
     __shared__ float red[8][32];
     const int jc = blockIdx.x, kc = blockIdx.y;
@@ -218,6 +227,8 @@ __global__ void __launch_bounds__(EXT)
     k_extremes(const int2 *__restrict__ pts, long long n, const float *__restrict__ part2,
                const float *__restrict__ W, Cand *__restrict__ cand, float *y_out, float *dirs_out)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float h2[NH];
     __shared__ float red[16][NK];
     __shared__ float s_c[NK], s_s[NK];
@@ -366,9 +377,11 @@ __device__ __forceinline__ void chain_at(const int2 *V, int nv, int x, long long
 
 __global__ void __launch_bounds__(256)
     k_cull_init(const int2 *__restrict__ pts, const Cand *__restrict__ cand, int ncand, int p,
-                int2 *Linit, int2 *L, uint16_t *G, int shift, unsigned long long *zero, int nzero,
-                int2 *poly_out, int *poly_count, long long *ext_out)
+                int2 *Linit, int2 *L, uint16_t *G, bool G_warm, int shift, unsigned long long *zero,
+                int nzero, int2 *poly_out, int *poly_count, long long *ext_out)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ long long s_idx[NK];
     __shared__ int2 s_sorted[NK];
     __shared__ int2 s_lo[NK], s_up[NK];
@@ -488,10 +501,18 @@ __global__ void __launch_bounds__(256)
     if (L)
         L[c] = li;
     if (G) {
-        // pass every point that could move L below li.x or above li.y
+        // pass every point that could move L below li.x or above li.y; the
+        // warm-up filter already in G is another such bound, so keep the
+        // tighter of the two (each is the bin of a value every point that
+        // can set the final L.lo is at or below, likewise for L.hi)
         const unsigned top = (unsigned)(p - 1) >> shift;
-        const unsigned qlo = li.x <= 1 ? 0u : (unsigned)(li.x - 2) >> shift;
-        const unsigned qhi = li.y + 1 < 1 ? 0u : (li.y + 1 > p ? top : (unsigned)li.y >> shift);
+        unsigned qlo = li.x <= 1 ? 0u : (unsigned)(li.x - 2) >> shift;
+        unsigned qhi = li.y + 1 < 1 ? 0u : (li.y + 1 > p ? top : (unsigned)li.y >> shift);
+        if (G_warm) {
+            const unsigned g = G[c];
+            qlo = min(qlo, g >> 8);
+            qhi = max(qhi, g & 0xFFu);
+        }
         G[c] = (uint16_t)((qlo << 8) | qhi);
     }
 }
@@ -510,7 +531,7 @@ size_t cull_ws_bytes(int p)
 }
 
 cudaError_t cull_launch(const int32_t *pts, int64_t n, int p, const float *params, void *ws,
-                        int32_t *Linit, int32_t *L, uint16_t *G, int shift,
+                        int32_t *Linit, int32_t *L, uint16_t *G, bool G_warm, int shift,
                         unsigned long long *zero, int nzero, float *features, float *y_out,
                         float *dirs_out, int32_t *poly_out, int32_t *poly_count, int64_t *ext_out,
                         cudaStream_t s)
@@ -525,18 +546,18 @@ cudaError_t cull_launch(const int32_t *pts, int64_t n, int p, const float *param
     const long long m = sample_size(n);
     const float scale = m > 0 ? 1024.0f / (float)m : 0.f;
     if (params || features) {
-        k_sample_hist<<<HB, SR, 0, s>>>(P, n, p, rows);
+        launch(k_sample_hist, HB, SR, 0, s, P, n, p, rows);
         if (features)
-            k_features<<<NI / 256, 256, 0, s>>>(rows, scale, features);
+            launch(k_features, NI / 256, 256, 0, s, rows, scale, features);
     }
     if (params) {
-        k_gemv1<<<dim3(NH / 32, KS1), 256, 0, s>>>(rows, scale, params, part1);
-        k_gemv2<<<dim3(NH / 32, KS2), 256, 0, s>>>(part1, params, part2);
+        launch(k_gemv1, dim3(NH / 32, KS1), 256, 0, s, rows, scale, params, part1);
+        launch(k_gemv2, dim3(NH / 32, KS2), 256, 0, s, part1, params, part2);
     }
-    k_extremes<<<EXB, EXT, 0, s>>>(P, n, part2, params, cand, y_out, dirs_out);
-    k_cull_init<<<(p + 255) / 256, 256, 0, s>>>(
-        P, cand, EXB, p, reinterpret_cast<int2 *>(Linit), reinterpret_cast<int2 *>(L), G, shift,
-        zero, nzero, reinterpret_cast<int2 *>(poly_out), poly_count,
+    launch(k_extremes, EXB, EXT, 0, s, P, n, part2, params, cand, y_out, dirs_out);
+    launch(k_cull_init, (p + 255) / 256, 256, 0, s,
+        P, cand, EXB, p, reinterpret_cast<int2 *>(Linit), reinterpret_cast<int2 *>(L), G, G_warm,
+        shift, zero, nzero, reinterpret_cast<int2 *>(poly_out), poly_count,
         reinterpret_cast<long long *>(ext_out));
     return cudaGetLastError();
 }

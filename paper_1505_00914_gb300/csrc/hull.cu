@@ -44,6 +44,8 @@ __global__ void __launch_bounds__(RUN)
     k_hull_filter(const int2 *__restrict__ lower, const int2 *__restrict__ upper,
                   const int *__restrict__ counts, int p, int nblk, int2 *cand, int *ccnt)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int2 P[RUN];
     __shared__ short M[2 * RUN];
     __shared__ int s_wc[RUN / 32 + 1];
@@ -105,6 +107,8 @@ __global__ void __launch_bounds__(FT, 1)
     k_hull_final(const int2 *__restrict__ cand, const int *__restrict__ ccnt, int nblk, int2 *gA,
                  int2 *gB, int *gF, int *gix, int2 *hull, int *hull_count)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int s_warp[32];
     __shared__ int s_total, s_t0;
     __shared__ int s_offs[2 * 128 + 1];
@@ -175,7 +179,7 @@ cudaError_t hull_final_launch(const HullLayout &h, void *ws, int32_t *hull, int3
     if (e != cudaSuccess)
         return e;
     char *b = reinterpret_cast<char *>(ws);
-    k_hull_final<<<1, FT, FINAL_SMEM, s>>>(
+    launch(k_hull_final, 1, FT, FINAL_SMEM, s,
         reinterpret_cast<const int2 *>(b + h.cand), reinterpret_cast<const int *>(b + h.ccnt), h.nblk,
         reinterpret_cast<int2 *>(b + h.gA), reinterpret_cast<int2 *>(b + h.gB),
         reinterpret_cast<int *>(b + h.gF), reinterpret_cast<int *>(b + h.gix),
@@ -190,7 +194,7 @@ cudaError_t hull_launch(const int32_t *lower, const int32_t *upper, const int32_
     (void)status;
     const HullLayout h = hull_layout(p);
     char *b = reinterpret_cast<char *>(ws);
-    k_hull_filter<<<2 * h.nblk, RUN, 0, s>>>(reinterpret_cast<const int2 *>(lower),
+    launch(k_hull_filter, 2 * h.nblk, RUN, 0, s, reinterpret_cast<const int2 *>(lower),
                                              reinterpret_cast<const int2 *>(upper), counts, p,
                                              h.nblk, reinterpret_cast<int2 *>(b + h.cand),
                                              reinterpret_cast<int *>(b + h.ccnt));

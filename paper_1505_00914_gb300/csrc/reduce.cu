@@ -101,6 +101,8 @@ __global__ void __launch_bounds__(RT)
     k_reduce_private(const int32_t *__restrict__ pts, int64_t n, int p,
                      uint32_t *__restrict__ part, unsigned *status)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) int sI[];
     int *slo = sI, *shi = sI + p;
     for (int i = threadIdx.x; i < p; i += RT) {
@@ -142,6 +144,8 @@ __global__ void __launch_bounds__(RT)
 // --------------------------------------------------------------- filtered
 __global__ void k_fill_empty(int2 *L, int p, unsigned long long *zero, int nzero)
 {
+    pdl_wait();
+    pdl_trigger();
     if (zero && blockIdx.x == 0)
         for (int i = threadIdx.x; i < nzero; i += blockDim.x)
             zero[i] = 0;
@@ -167,6 +171,8 @@ __device__ __forceinline__ bool fold_global(int2 *L, uint32_t up, int x, int y)
 __global__ void __launch_bounds__(256)
     k_reduce_global(const int32_t *__restrict__ pts, int64_t n, int p, int2 *L, unsigned *status)
 {
+    pdl_wait();
+    pdl_trigger();
     const PairView pv = pair_view(pts, n);
     const uint32_t up = (uint32_t)p;
     bool bad = false;
@@ -215,6 +221,8 @@ __global__ void __launch_bounds__(RT)
     k_filter_warm(const int32_t *__restrict__ pts, int64_t n, int p, int shift, int grid,
                   uint16_t *__restrict__ slots)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) uint16_t F[];
     unsigned char *fb = reinterpret_cast<unsigned char *>(F);
     const int words = (p + 7) / 8;
@@ -256,6 +264,8 @@ __global__ void __launch_bounds__(MG_V *MG_GROUPS)
     k_filter_merge(const uint16_t *__restrict__ slots, int rows, int p, uint16_t *__restrict__ G,
                    int2 *__restrict__ L, unsigned long long *zero, int nzero)
 {
+    pdl_wait();
+    pdl_trigger();
     if (zero && blockIdx.x == 0)
         for (int i = threadIdx.x; i < nzero; i += blockDim.x)
             zero[i] = 0;
@@ -297,6 +307,8 @@ __global__ void __launch_bounds__(RT)
     k_reduce_filtered(const int32_t *__restrict__ pts, int64_t n, int p, int shift,
                       const uint16_t *__restrict__ G, int2 *L, unsigned *status)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) uint16_t F[];
     unsigned char *fb = reinterpret_cast<unsigned char *>(F);
     {
@@ -359,6 +371,8 @@ __global__ void __launch_bounds__(1024)
     k_merge_partials(const uint32_t *__restrict__ part, int copies, int p, int2 *L,
                      unsigned long long *zero, int nzero, const int2 *__restrict__ Linit)
 {
+    pdl_wait();
+    pdl_trigger();
     if (zero && blockIdx.x == 0)
         for (int i = threadIdx.x; i < nzero; i += blockDim.x)
             zero[i] = 0;
@@ -528,9 +542,9 @@ cudaError_t reduce_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, i
         uint32_t *pp = reinterpret_cast<uint32_t *>(part);
         mark(ev0);
         if (pl.threads == 512)
-            k_reduce_private<512><<<pl.grid, 512, pl.smem, s>>>(pts, n, p, pp, status);
+            launch(k_reduce_private<512>, pl.grid, 512, pl.smem, s, pts, n, p, pp, status);
         else
-            k_reduce_private<1024><<<pl.grid, 1024, pl.smem, s>>>(pts, n, p, pp, status);
+            launch(k_reduce_private<1024>, pl.grid, 1024, pl.smem, s, pts, n, p, pp, status);
         mark(ev1);
         return cudaGetLastError();
     }
@@ -538,10 +552,10 @@ cudaError_t reduce_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, i
     const int sms = sm_count();
     if (pl.mode == 2) {
         if (!prefilled)
-            k_fill_empty<<<std::max(1, std::min((p + 255) / 256, sms * 4)), 256, 0, s>>>(L2, p, zero,
+            launch(k_fill_empty, std::max(1, std::min((p + 255) / 256, sms * 4)), 256, 0, s, L2, p, zero,
                                                                                         nzero);
         mark(ev0);
-        k_reduce_global<<<sms * 8, 256, 0, s>>>(pts, n, p, L2, status);
+        launch(k_reduce_global, sms * 8, 256, 0, s, pts, n, p, L2, status);
         mark(ev1);
         return cudaGetLastError();
     }
@@ -549,21 +563,41 @@ cudaError_t reduce_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, i
     uint16_t *slots = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(part) +
                                                    ((((size_t)p * 2) + 255) & ~size_t(255)));
     if (!prefilled) {
-        k_filter_warm<1024><<<pl.grid, 1024, pl.smem, s>>>(pts, n, p, pl.shift, pl.grid, slots);
+        launch(k_filter_warm<1024>, pl.grid, 1024, pl.smem, s, pts, n, p, pl.shift, pl.grid, slots);
         const int words = (p + 7) / 8;
-        k_filter_merge<<<(words + MG_V - 1) / MG_V, MG_V * MG_GROUPS, 0, s>>>(slots, pl.grid, p, G,
+        launch(k_filter_merge, (words + MG_V - 1) / MG_V, MG_V * MG_GROUPS, 0, s, slots, pl.grid, p, G,
                                                                              L2, zero, nzero);
     }
     mark(ev0);
-    k_reduce_filtered<1024><<<pl.grid, 1024, pl.smem, s>>>(pts, n, p, pl.shift, G, L2, status);
+    launch(k_reduce_filtered<1024>, pl.grid, 1024, pl.smem, s, pts, n, p, pl.shift, G, L2, status);
     mark(ev1);
+    return cudaGetLastError();
+}
+
+cudaError_t reduce_warm_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, int p,
+                               void *part, int32_t *L, cudaStream_t s, unsigned long long *zero,
+                               int nzero)
+{
+    int2 *L2 = reinterpret_cast<int2 *>(L);
+    if (pl.mode == 2) {
+        launch(k_fill_empty, std::max(1, std::min((p + 255) / 256, sm_count() * 4)), 256, 0, s, L2, p, zero,
+                                                                                        nzero);
+    } else if (pl.mode == 1) {
+        uint16_t *G = reinterpret_cast<uint16_t *>(part);
+        uint16_t *slots = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(part) +
+                                                       ((((size_t)p * 2) + 255) & ~size_t(255)));
+        launch(k_filter_warm<1024>, pl.grid, 1024, pl.smem, s, pts, n, p, pl.shift, pl.grid, slots);
+        const int words = (p + 7) / 8;
+        launch(k_filter_merge, (words + MG_V - 1) / MG_V, MG_V * MG_GROUPS, 0, s, slots, pl.grid, p, G,
+                                                                             L2, zero, nzero);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t reduce_merge_launch(const void *part, int copies, int p, int32_t *L, cudaStream_t s,
                                 unsigned long long *zero, int nzero, const int32_t *Linit)
 {
-    k_merge_partials<<<(p + 31) / 32, 1024, 0, s>>>(reinterpret_cast<const uint32_t *>(part),
+    launch(k_merge_partials, (p + 31) / 32, 1024, 0, s, reinterpret_cast<const uint32_t *>(part),
                                                          copies, p, reinterpret_cast<int2 *>(L),
                                                          zero, nzero,
                                                          reinterpret_cast<const int2 *>(Linit));
