@@ -264,7 +264,10 @@ int ch_mlp_adam(float *params, const float *grads, float *m, float *v, int32_t s
 /* giving y[16]; directions theta_k = 2*pi*k/16 + (pi/16)*tanh(y_k) (the    */
 /* sector centres when params is NULL).  Extremes: per direction the sample */
 /* point maximising fl32(fl32(cos*x) + fl32(sin*y)), ties to the smaller    */
-/* index.  Polygon: strict hull of the extremes.  Start array Linit: for    */
+/* index.  Polygon: strict hull of the extremes; with a network, the larger */
+/* (exact area, ties to the centres) of the network's and the sector        */
+/* centres' polygons, so the network can only enlarge the culled region.    */
+/* Start array Linit: for                                                   */
 /* columns strictly between the polygon's extreme x values, (floor(b(x))+1, */
 /* ceil(u(x))-1) with b, u its lower and upper boundary; (p+1, -1) else.    */
 /* ---------------------------------------------------------------------- */
@@ -276,15 +279,19 @@ int ch_cull_workspace_size(int32_t p, size_t *bytes);
 
 /* The culling proposal alone, with its intermediate results.  Linit: device
  * int32[p][2] (required).  Optional (NULL to skip) device outputs: features
- * float[1024], net_out float[16] (y), dirs float[32] (16 cosines then 16
- * sines), poly int32[16][2] + poly_count (counter-clockwise from the
- * lexicographic minimum), extremes int64[16] (point indices, -1 if none).
- * params: device float[CH_MLP_PARAMS] or NULL.  Workspace: device memory of
- * ch_cull_workspace_size bytes, no initial contents. */
+ * float[1024], net_out float[16] (y), for both direction sets (set 0 the
+ * sector centres, set 1 the network's, zero / -1 without a network) dirs
+ * float[2][32] (16 cosines then 16 sines) and extremes int64[2][16] (point
+ * indices, -1 if none), and for the polygon used poly int32[16][2] +
+ * poly_count (counter-clockwise from the lexicographic minimum) and chosen
+ * int32 (1: the network's polygon, 0: the sector centres', -1: no network).
+ * params: device float[CH_MLP_PARAMS]
+ * or NULL.  Workspace: device memory of ch_cull_workspace_size bytes, no
+ * initial contents. */
 int ch_cull_propose(const int32_t *pts, int64_t n, int32_t p, const float *params, int32_t *Linit,
                     float *features, float *net_out, float *dirs, int32_t *poly,
-                    int32_t *poly_count, int64_t *extremes, void *workspace, size_t ws_bytes,
-                    ch_stream_t stream);
+                    int32_t *poly_count, int64_t *extremes, int32_t *chosen, void *workspace,
+                    size_t ws_bytes, ch_stream_t stream);
 
 int ch_hull_learned_workspace_size(int64_t n, int32_t p, size_t *bytes);
 

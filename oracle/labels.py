@@ -5,7 +5,8 @@ input generators; the CUDA library never runs here.
 
 Set i draws m points of one of the plain workloads' shapes (uniform square,
 inscribed disc, Gaussian sigma = p/8, projected 3D shells) at a side p from
-{1024, 4096, 16384, 65536}, both by a seeded choice.  Its features are the
+{1024, 4096, 16384, 65536}, both by a seeded choice; three sets in four are
+then stretched and rotated by a seeded random map (synth.affine).  Its features are the
 occupancy histogram counts (oracle/learned.py's cells; the network input is
 count * fl32(1024 / m)) and its label the K per-sector direction offsets that
 maximise the area of the polygon of the extreme hull vertices
@@ -30,8 +31,13 @@ PS = (1024, 4096, 16384, 65536)
 
 
 def set_spec(i: int, seed: int):
+    """(distribution, p, stretched): three sets in four go through a seeded
+    random stretch and rotation (synth.affine), so that the network sees
+    tilted, elongated variants of the shapes as well as the shapes."""
     rng = np.random.default_rng([seed, i, 7])
-    return DISTS[int(rng.integers(0, len(DISTS)))], PS[int(rng.integers(0, len(PS)))]
+    d = DISTS[int(rng.integers(0, len(DISTS)))]
+    p = PS[int(rng.integers(0, len(PS)))]
+    return d, p, bool(rng.random() < 0.75)
 
 
 def _chunk(args):
@@ -45,8 +51,10 @@ def _chunk(args):
     ps = np.empty(n, dtype=np.int32)
     dist_ix = np.empty(n, dtype=np.int8)
     for j, i in enumerate(range(lo, hi)):
-        d, p = set_spec(i, seed)
+        d, p, stretched = set_spec(i, seed)
         P = synth.points(d, m, p, seed=seed * 1_000_003 + i)
+        if stretched:
+            P = synth.affine(P, p, seed=seed * 1_000_003 + i)
         pts[j * m:(j + 1) * m] = P
         ps[j] = p
         dist_ix[j] = DISTS.index(d)
@@ -57,7 +65,7 @@ def _chunk(args):
 
 
 def build(sets: int, m: int = 8192, seed: int = 1, k: int = 16, workers: int | None = None,
-          chunk: int = 2048):
+          chunk: int = 1024):
     workers = workers or os.cpu_count() or 1
     jobs = [(lo, min(sets, lo + chunk), m, seed, k) for lo in range(0, sets, chunk)]
     counts = np.zeros((sets, 1024), dtype=np.uint16)

@@ -188,3 +188,28 @@ def extremes(pts, index, c, s) -> np.ndarray:
         score = score.astype(np.float32)
         out[k] = index[score == score.max()].min()
     return out
+
+
+def area2(poly) -> int:
+    """Twice the area of a counter-clockwise polygon (exact integers); 0 for
+    fewer than three vertices."""
+    P = [(int(x), int(y)) for x, y in np.asarray(poly).reshape(-1, 2)]
+    if len(P) < 3:
+        return 0
+    return sum(P[i][0] * P[(i + 1) % len(P)][1] - P[i][1] * P[(i + 1) % len(P)][0]
+               for i in range(len(P)))
+
+
+def choose_polygon(pts, index, dirs, has_net: bool):
+    """The culling polygon: the strict hull of the sample points extreme in
+    the sector-centre directions (dirs[0] = (cos, sin)), or, with a network,
+    that of its directions (dirs[1]) when its area is strictly larger.
+    Returns (polygon, chosen set, extremes of both sets)."""
+    import oracle
+    pts = np.asarray(pts).reshape(-1, 2)
+    sets = 2 if has_net else 1
+    ext = [extremes(pts, index, dirs[s][0], dirs[s][1]) if len(index) else
+           np.full(len(dirs[s][0]), -1, np.int64) for s in range(sets)]
+    polys = [oracle.hull_points(pts[e[e >= 0]]) for e in ext]
+    sel = 1 if sets == 2 and area2(polys[1]) > area2(polys[0]) else 0
+    return polys[sel], sel, ext

@@ -67,7 +67,7 @@ def _declare(lib):
                                        ctypes.c_float, ctypes.c_float, P]),
         "ch_chain_noalloc": (ctypes.c_int, [P, i32, P, P, P, P, P]),
         "ch_cull_workspace_size": (ctypes.c_int, [i32, szp]),
-        "ch_cull_propose": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P, P, P, sz, P]),
+        "ch_cull_propose": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P, P, P, P, sz, P]),
         "ch_hull_learned_workspace_size": (ctypes.c_int, [i64, i32, szp]),
         "ch_hull_learned_kernel_count": (ctypes.c_int, [i64, i32, i32, ctypes.POINTER(i32)]),
         "ch_hull_learned": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P, P, P, sz, P]),
@@ -394,8 +394,10 @@ def ch_cull_workspace_size(p: int) -> int:
 
 def ch_cull_propose(pts, p: int, params=None, workspace=None, stream=None):
     """The culling proposal and its intermediate results, as a dict of device
-    tensors: Linit (p, 2), features (1024,), net_out (16,), dirs (2, 16),
-    poly (16, 2) with poly_count (1,), extremes (16,) int64."""
+    tensors: Linit (p, 2), features (1024,), net_out (16,), for both
+    direction sets (0 sector centres, 1 network) dirs (2, 2, 16) and
+    extremes (2, 16) int64, and for the polygon used poly (16, 2) with
+    poly_count (1,) and chosen (1,) (1 network, 0 centres, -1 no network)."""
     pts = _pts(pts)
     dev = _dev(pts)
     if params is not None:
@@ -404,17 +406,19 @@ def ch_cull_propose(pts, p: int, params=None, workspace=None, stream=None):
         "Linit": torch.empty((p, 2), dtype=torch.int32, device=dev),
         "features": torch.empty(CH_MLP_IN, dtype=torch.float32, device=dev),
         "net_out": torch.zeros(CH_MLP_K, dtype=torch.float32, device=dev),
-        "dirs": torch.empty((2, CH_MLP_K), dtype=torch.float32, device=dev),
+        "dirs": torch.empty((2, 2, CH_MLP_K), dtype=torch.float32, device=dev),
         "poly": torch.zeros((CH_MLP_K, 2), dtype=torch.int32, device=dev),
         "poly_count": torch.empty(1, dtype=torch.int32, device=dev),
-        "extremes": torch.empty(CH_MLP_K, dtype=torch.int64, device=dev),
+        "extremes": torch.empty((2, CH_MLP_K), dtype=torch.int64, device=dev),
+        "chosen": torch.empty(1, dtype=torch.int32, device=dev),
     }
     ws = _ws(ch_cull_workspace_size(p), dev, workspace)
     o = out
     _check(lib().ch_cull_propose(_ptr(pts), pts.shape[0], int(p), _ptr(params), _ptr(o["Linit"]),
                                  _ptr(o["features"]), _ptr(o["net_out"]), _ptr(o["dirs"]),
                                  _ptr(o["poly"]), _ptr(o["poly_count"]), _ptr(o["extremes"]),
-                                 _ptr(ws), ws.numel(), _stream(stream)), "ch_cull_propose")
+                                 _ptr(o["chosen"]), _ptr(ws), ws.numel(), _stream(stream)),
+           "ch_cull_propose")
     return out
 
 

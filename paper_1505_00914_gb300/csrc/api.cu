@@ -532,8 +532,8 @@ int ch_cull_workspace_size(int32_t p, size_t *bytes)
 
 int ch_cull_propose(const int32_t *pts, int64_t n, int32_t p, const float *params, int32_t *Linit,
                     float *features, float *net_out, float *dirs, int32_t *poly,
-                    int32_t *poly_count, int64_t *extremes, void *workspace, size_t ws_bytes,
-                    ch_stream_t stream)
+                    int32_t *poly_count, int64_t *extremes, int32_t *chosen, void *workspace,
+                    size_t ws_bytes, ch_stream_t stream)
 {
     if (check_np(n, p) != CH_OK || (n > 0 && !pts) || !Linit || !aligned8(pts) ||
         !aligned8(Linit) || !aligned8(poly))
@@ -542,6 +542,7 @@ int ch_cull_propose(const int32_t *pts, int64_t n, int32_t p, const float *param
         return CH_ERR_WORKSPACE;
     return cuda_rc(cull_launch(pts, n, p, params, workspace, Linit, nullptr, nullptr, false, 0,
                                nullptr, 0, features, net_out, dirs, poly, poly_count, extremes,
+                               chosen,
                                reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -614,7 +615,7 @@ int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *param
         e = cull_launch(pts, n, p, params, b + w.cull, Linit, mode != 0 ? L : nullptr,
                         mode == 1 ? reinterpret_cast<uint16_t *>(part) : nullptr, mode == 1,
                         pw.plan.shift, mode == 0 ? zero : nullptr, mode == 0 ? nzero : 0, nullptr,
-                        nullptr, nullptr, nullptr, nullptr, nullptr, s);
+                        nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, s);
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
     cudaEvent_t ev0, ev1;

@@ -173,13 +173,14 @@ size_t cull_ws_bytes(int p);
 // -> extreme sample points -> culling polygon -> Linit for every column.  L
 // and G (filter words) are written too when given (G_warm: G holds the
 // warm-up filter, which is tightened rather than replaced); zero/nzero as in
-// reduce_launch.  features, y_out, dirs_out, poly_out, poly_count, ext_out
-// are optional diagnostic outputs.
+// reduce_launch.  features, y_out, dirs_out, poly_out, poly_count, ext_out,
+// chosen are optional diagnostic outputs (of the polygon used: the network's
+// or the sector centres', whichever has the larger area).
 cudaError_t cull_launch(const int32_t *pts, int64_t n, int p, const float *params, void *ws,
                         int32_t *Linit, int32_t *L, uint16_t *G, bool G_warm, int shift,
                         unsigned long long *zero, int nzero, float *features, float *y_out,
                         float *dirs_out, int32_t *poly_out, int32_t *poly_count, int64_t *ext_out,
-                        cudaStream_t s);
+                        int32_t *chosen, cudaStream_t s);
 int cull_kernel_count(bool net);
 
 // ---- api.cu ----

@@ -15,10 +15,13 @@
 // k_extremes     output layer, directions theta_k = 2 pi k / K +
 //                (pi / K) tanh(y_k), and per CTA the sample point with the
 //                largest fl32(c_k x + s_k y) (two rounded products, one
-//                rounded sum; ties to the smaller index) for each k;
+//                rounded sum; ties to the smaller index) for each k, for the
+//                network's directions and for the sector centres;
 // k_cull_init    every CTA folds the per-CTA winners, takes the strict hull
-//                of the K winners in one warp (exact int64 orientation), and
-//                writes for its columns the start array Linit, L = Linit and
+//                of each set's K winners in one warp (exact int64
+//                orientation), keeps the polygon of larger area (exact, ties
+//                to the sector centres), and writes for its columns the
+//                start array Linit, L = Linit and
 //                the filtered reduction's row-bin filter (tightening the
 //                warm-up filter when there is one).
 // The reduction then runs unchanged from that filter and start array, and
@@ -223,18 +226,22 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------------- extremes
+// Direction set 0 is the sector centres theta_k = 2 pi k / K; set 1 (only
+// with a network) adds (pi / K) tanh(y_k).  Each set's winners go to
+// cand[(set * gridDim.x + CTA) * K + k] and its directions to dirs[set].
 __global__ void __launch_bounds__(EXT)
     k_extremes(const int2 *__restrict__ pts, long long n, const float *__restrict__ part2,
-               const float *__restrict__ W, Cand *__restrict__ cand, float *y_out, float *dirs_out)
+               const float *__restrict__ W, Cand *__restrict__ cand, float *y_out, float *dirs)
 {
     pdl_wait();
     pdl_trigger();
     __shared__ float h2[NH];
     __shared__ float red[16][NK];
-    __shared__ float s_c[NK], s_s[NK];
+    __shared__ float s_c[2][NK], s_s[2][NK];
     __shared__ float s_best[EXT / 32][NK];
     __shared__ long long s_idx[EXT / 32][NK];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int nsets = W ? 2 : 1;
     if (W) {
         float v[KS2];
 #pragma unroll
@@ -254,98 +261,101 @@ __global__ void __launch_bounds__(EXT)
         red[js][k] = acc;
         __syncthreads();
     }
-    if (t < NK) {
-        float y = 0.f;
-        if (W) {
+    if (t < 2 * NK) {
+        const int set = t / NK, k = t % NK;
+        float th = 0.f;
+        if (set == 1 && W) {
+            float y = 0.f;
 #pragma unroll
             for (int js = 0; js < 16; ++js)
-                y += red[js][t];
-            y += W[OFF_B3 + t];
+                y += red[js][k];
+            y += W[OFF_B3 + k];
+            th = tanhf(y);
+            if (!(fabsf(th) <= 1.f))
+                th = 0.f;  // a non-finite output falls back to the sector centre
+            if (blockIdx.x == 0 && y_out)
+                y_out[k] = y;
         }
-        float th = tanhf(y);
-        if (!(fabsf(th) <= 1.f))
-            th = 0.f;  // a non-finite output falls back to the sector centre
-        const float theta = (float)(2.0 * CUDART_PI / NK) * (float)t + (float)(CUDART_PI / NK) * th;
+        const float theta = (float)(2.0 * CUDART_PI / NK) * (float)k + (float)(CUDART_PI / NK) * th;
         float sn, cs;
         sincosf(theta, &sn, &cs);
-        s_c[t] = cs;
-        s_s[t] = sn;
-        if (blockIdx.x == 0) {
-            if (y_out)
-                y_out[t] = y;
-            if (dirs_out) {
-                dirs_out[t] = cs;
-                dirs_out[NK + t] = sn;
-            }
+        s_c[set][k] = cs;
+        s_s[set][k] = sn;
+        if (blockIdx.x == 0 && set < nsets) {
+            dirs[set * 2 * NK + k] = cs;
+            dirs[set * 2 * NK + NK + k] = sn;
         }
     }
     __syncthreads();
-    float c[NK], s[NK], best[NK];
-    long long bi[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) {
-        c[k] = s_c[k];
-        s[k] = s_s[k];
-        best[k] = -CUDART_INF_F;
-        bi[k] = NONE;
-    }
     long long nruns, step;
     sample_shape(n, nruns, step);
     const long long m = sample_size(n);
     const long long stride = (long long)gridDim.x * EXT;
-    for (long long q0 = (long long)blockIdx.x * EXT + t; q0 < m; q0 += stride * EXU) {
-        int2 v[EXU];
-        long long gi[EXU];
+    for (int set = 0; set < nsets; ++set) {
+        float c[NK], s[NK], best[NK];
+        long long bi[NK];
 #pragma unroll
-        for (int u = 0; u < EXU; ++u) {
-            const long long q = q0 + u * stride;
-            gi[u] = (q / SR) * step + (q % SR);
-            v[u] = q < m ? pts[gi[u]] : make_int2(0, 0);
+        for (int k = 0; k < NK; ++k) {
+            c[k] = s_c[set][k];
+            s[k] = s_s[set][k];
+            best[k] = -CUDART_INF_F;
+            bi[k] = NONE;
         }
+        for (long long q0 = (long long)blockIdx.x * EXT + t; q0 < m; q0 += stride * EXU) {
+            int2 v[EXU];
+            long long gi[EXU];
 #pragma unroll
-        for (int u = 0; u < EXU; ++u) {
-            if (q0 + u * stride >= m)
-                break;
-            const float xf = __int2float_rn(v[u].x), yf = __int2float_rn(v[u].y);
+            for (int u = 0; u < EXU; ++u) {
+                const long long q = q0 + u * stride;
+                gi[u] = (q / SR) * step + (q % SR);
+                v[u] = q < m ? pts[gi[u]] : make_int2(0, 0);
+            }
 #pragma unroll
-            for (int k = 0; k < NK; ++k) {
-                const float sc = __fadd_rn(__fmul_rn(c[k], xf), __fmul_rn(s[k], yf));
-                if (sc > best[k]) {  // visits increase in index: ties keep the first
-                    best[k] = sc;
-                    bi[k] = gi[u];
+            for (int u = 0; u < EXU; ++u) {
+                if (q0 + u * stride >= m)
+                    break;
+                const float xf = __int2float_rn(v[u].x), yf = __int2float_rn(v[u].y);
+#pragma unroll
+                for (int k = 0; k < NK; ++k) {
+                    const float sc = __fadd_rn(__fmul_rn(c[k], xf), __fmul_rn(s[k], yf));
+                    if (sc > best[k]) {  // visits increase in index: ties keep the first
+                        best[k] = sc;
+                        bi[k] = gi[u];
+                    }
                 }
             }
         }
-    }
-#pragma unroll
-    for (int k = 0; k < NK; ++k) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xFFFFFFFFu, best[k], o);
-            const long long oi = __shfl_xor_sync(0xFFFFFFFFu, bi[k], o);
-            if (better(ob, oi, best[k], bi[k])) {
-                best[k] = ob;
-                bi[k] = oi;
-            }
-        }
-    }
-    if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < NK; ++k) {
-            s_best[w][k] = best[k];
-            s_idx[w][k] = bi[k];
-        }
-    }
-    __syncthreads();
-    if (t < NK) {
-        float b = s_best[0][t];
-        long long i = s_idx[0][t];
-        for (int v = 1; v < EXT / 32; ++v)
-            if (better(s_best[v][t], s_idx[v][t], b, i)) {
-                b = s_best[v][t];
-                i = s_idx[v][t];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xFFFFFFFFu, best[k], o);
+                const long long oi = __shfl_xor_sync(0xFFFFFFFFu, bi[k], o);
+                if (better(ob, oi, best[k], bi[k])) {
+                    best[k] = ob;
+                    bi[k] = oi;
+                }
             }
-        cand[blockIdx.x * NK + t] = Cand{b, 0, i};
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                s_best[w][k] = best[k];
+                s_idx[w][k] = bi[k];
+            }
+        }
+        __syncthreads();
+        if (t < NK) {
+            float b = s_best[0][t];
+            long long i = s_idx[0][t];
+            for (int v = 1; v < EXT / 32; ++v)
+                if (better(s_best[v][t], s_idx[v][t], b, i)) {
+                    b = s_best[v][t];
+                    i = s_idx[v][t];
+                }
+            cand[((size_t)set * gridDim.x + blockIdx.x) * NK + t] = Cand{b, 0, i};
+        }
+        __syncthreads();
     }
 }
 
@@ -375,50 +385,77 @@ __device__ __forceinline__ void chain_at(const int2 *V, int nv, int x, long long
     num = (long long)a.y * ((long long)b.x - x) + (long long)b.y * ((long long)x - a.x);
 }
 
+// Twice the signed area of the polygon s_lo[0..nlo) ++ s_up[nup-2..1]
+// (counter-clockwise), exact.
+__device__ __forceinline__ __int128 area2(const int2 *lo, int nlo, const int2 *up, int nup)
+{
+    __int128 a = 0;
+    const int nv = nlo + nup - 2;
+    if (nv < 3)
+        return 0;
+    const int2 o = lo[0];
+    auto vert = [&](int i) { return i < nlo ? lo[i] : up[nup - 2 - (i - nlo)]; };
+    for (int i = 0; i < nv; ++i) {
+        const int2 u = vert(i), v = vert(i + 1 < nv ? i + 1 : 0);
+        a += (__int128)((long long)u.x - o.x) * ((long long)v.y - o.y) -
+             (__int128)((long long)u.y - o.y) * ((long long)v.x - o.x);
+    }
+    return a;
+}
+
+// nsets = 1: the sector-centre polygon; nsets = 2: also the network's, and
+// the one of larger area is used (ties: the sector centres), so the network
+// can only enlarge the culled region.
 __global__ void __launch_bounds__(256)
-    k_cull_init(const int2 *__restrict__ pts, const Cand *__restrict__ cand, int ncand, int p,
-                int2 *Linit, int2 *L, uint16_t *G, bool G_warm, int shift, unsigned long long *zero,
-                int nzero, int2 *poly_out, int *poly_count, long long *ext_out)
+    k_cull_init(const int2 *__restrict__ pts, const Cand *__restrict__ cand, int ncand, int nsets,
+                int p, int2 *Linit, int2 *L, uint16_t *G, bool G_warm, int shift,
+                unsigned long long *zero, int nzero, const float *dirs_in, float *dirs_out,
+                int2 *poly_out, int *poly_count, long long *ext_out, int *chosen)
 {
     pdl_wait();
     pdl_trigger();
-    __shared__ long long s_idx[NK];
-    __shared__ int2 s_sorted[NK];
-    __shared__ int2 s_lo[NK], s_up[NK];
-    __shared__ int s_nlo, s_nup, s_m;
+    __shared__ long long s_idx[2][NK];
+    __shared__ int2 s_sorted[2][NK];
+    __shared__ int2 s_lo2[2][NK], s_up2[2][NK];
+    __shared__ int s_nlo[2], s_nup[2], s_m[2];
+    __shared__ int s_sel;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     if (zero && blockIdx.x == 0)
         for (int i = t; i < nzero; i += blockDim.x)
             zero[i] = 0;
     // winner of each direction over the extremes CTAs: warp w takes k = 2w, 2w+1
+    for (int set = 0; set < nsets; ++set) {
 #pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-        const int k = 2 * w + kk;
-        float b = -CUDART_INF_F;
-        long long bi = NONE;
-        for (int r = lane; r < ncand; r += 32) {
-            const Cand cd = cand[r * NK + k];
-            if (better(cd.score, cd.idx, b, bi)) {
-                b = cd.score;
-                bi = cd.idx;
+        for (int kk = 0; kk < 2; ++kk) {
+            const int k = 2 * w + kk;
+            float b = -CUDART_INF_F;
+            long long bi = NONE;
+            for (int r = lane; r < ncand; r += 32) {
+                const Cand cd = cand[((size_t)set * ncand + r) * NK + k];
+                if (better(cd.score, cd.idx, b, bi)) {
+                    b = cd.score;
+                    bi = cd.idx;
+                }
             }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xFFFFFFFFu, b, o);
-            const long long oi = __shfl_xor_sync(0xFFFFFFFFu, bi, o);
-            if (better(ob, oi, b, bi)) {
-                b = ob;
-                bi = oi;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xFFFFFFFFu, b, o);
+                const long long oi = __shfl_xor_sync(0xFFFFFFFFu, bi, o);
+                if (better(ob, oi, b, bi)) {
+                    b = ob;
+                    bi = oi;
+                }
             }
+            if (lane == 0)
+                s_idx[set][k] = bi;
         }
-        if (lane == 0)
-            s_idx[k] = bi;
     }
     __syncthreads();
-    // strict hull of the winners (warp 0; lane k holds winner k)
-    if (w == 0) {
-        const long long my = lane < NK ? s_idx[lane] : NONE;
+    // strict hull of each set's winners (warp `set`; lane k holds winner k)
+    if (w < nsets) {
+        const int set = w;
+        int2 *srt = s_sorted[set];
+        const long long my = lane < NK ? s_idx[set][lane] : NONE;
         const bool have = my != NONE;
         const int2 P = have ? pts[my] : make_int2(0, 0);
         const unsigned hv = __ballot_sync(0xFFFFFFFFu, have);
@@ -435,7 +472,7 @@ __global__ void __launch_bounds__(256)
             rank += keep && ((kv >> j) & 1u) && (qx < P.x || (qx == P.x && qy < P.y));
         }
         if (keep)
-            s_sorted[rank] = P;
+            srt[rank] = P;
         __syncwarp();
         const int m = __popc(kv);
         // lane i (< m): sorted point i is a strict lower (upper) hull vertex
@@ -443,12 +480,12 @@ __global__ void __launch_bounds__(256)
         // before it to a point after it; the end points belong to both
         bool lo = false, upf = false;
         if (lane < m) {
-            const int2 q = s_sorted[lane];
+            const int2 q = srt[lane];
             lo = upf = true;
             if (lane > 0 && lane < m - 1) {
                 for (int a = 0; a < lane; ++a)
                     for (int b = lane + 1; b < m; ++b) {
-                        const long long cr = cross3(s_sorted[a], s_sorted[b], q);
+                        const long long cr = cross3(srt[a], srt[b], q);
                         lo &= cr < 0;
                         upf &= cr > 0;
                     }
@@ -457,21 +494,35 @@ __global__ void __launch_bounds__(256)
         const unsigned bl = __ballot_sync(0xFFFFFFFFu, lo), bu = __ballot_sync(0xFFFFFFFFu, upf);
         const unsigned below = (1u << lane) - 1u;
         if (lo)
-            s_lo[__popc(bl & below)] = s_sorted[lane];
+            s_lo2[set][__popc(bl & below)] = srt[lane];
         if (upf)
-            s_up[__popc(bu & below)] = s_sorted[lane];
+            s_up2[set][__popc(bu & below)] = srt[lane];
         if (lane == 0) {
-            s_nlo = __popc(bl);
-            s_nup = __popc(bu);
-            s_m = m;
+            s_nlo[set] = __popc(bl);
+            s_nup[set] = __popc(bu);
+            s_m[set] = m;
         }
     }
     __syncthreads();
-    const int nlo = s_nlo, nup = s_nup, m = s_m;
+    if (t == 0) {
+        int sel = 0;
+        if (nsets == 2 && area2(s_lo2[1], s_m[1] <= 1 ? 0 : s_nlo[1], s_up2[1], s_nup[1]) >
+                              area2(s_lo2[0], s_m[0] <= 1 ? 0 : s_nlo[0], s_up2[0], s_nup[0]))
+            sel = 1;
+        s_sel = sel;
+    }
+    __syncthreads();
+    const int sel = s_sel;
+    const int2 *s_lo = s_lo2[sel], *s_up = s_up2[sel];
+    const int nlo = s_nlo[sel], nup = s_nup[sel], m = s_m[sel];
     const int nv = m <= 1 ? m : nlo + nup - 2;  // strict vertices of the polygon
     if (blockIdx.x == 0) {
-        if (t < NK && ext_out)
-            ext_out[t] = s_idx[t] == NONE ? -1 : s_idx[t];
+        if (t < 2 * NK && ext_out) {  // both sets: [set][k]
+            const int set = t / NK;
+            ext_out[t] = set >= nsets || s_idx[set][t % NK] == NONE ? -1 : s_idx[set][t % NK];
+        }
+        if (t < 4 * NK && dirs_out)  // both sets: [set][cos k | sin k]
+            dirs_out[t] = t < nsets * 2 * NK ? dirs_in[t] : 0.f;
         if (poly_out && t == 0) {
             // counter-clockwise from the lexicographic minimum
             int o = 0;
@@ -482,6 +533,8 @@ __global__ void __launch_bounds__(256)
         }
         if (poly_count && t == 0)
             *poly_count = nv;
+        if (chosen && t == 0)
+            *chosen = nsets == 2 ? sel : -1;
     }
     const int c = blockIdx.x * blockDim.x + t;
     if (c >= p)
@@ -526,7 +579,8 @@ size_t cull_ws_bytes(int p)
     l.take((size_t)HB * NI * sizeof(int));
     l.take((size_t)KS1 * NH * sizeof(float));
     l.take((size_t)KS2 * NH * sizeof(float));
-    l.take((size_t)EXB * NK * sizeof(Cand));
+    l.take((size_t)2 * EXB * NK * sizeof(Cand));
+    l.take((size_t)2 * 2 * NK * sizeof(float));
     return l.off;
 }
 
@@ -534,14 +588,15 @@ cudaError_t cull_launch(const int32_t *pts, int64_t n, int p, const float *param
                         int32_t *Linit, int32_t *L, uint16_t *G, bool G_warm, int shift,
                         unsigned long long *zero, int nzero, float *features, float *y_out,
                         float *dirs_out, int32_t *poly_out, int32_t *poly_count, int64_t *ext_out,
-                        cudaStream_t s)
+                        int32_t *chosen, cudaStream_t s)
 {
     WsLayout l;
     char *b = reinterpret_cast<char *>(ws);
     int *rows = reinterpret_cast<int *>(b + l.take((size_t)HB * NI * sizeof(int)));
     float *part1 = reinterpret_cast<float *>(b + l.take((size_t)KS1 * NH * sizeof(float)));
     float *part2 = reinterpret_cast<float *>(b + l.take((size_t)KS2 * NH * sizeof(float)));
-    Cand *cand = reinterpret_cast<Cand *>(b + l.take((size_t)EXB * NK * sizeof(Cand)));
+    Cand *cand = reinterpret_cast<Cand *>(b + l.take((size_t)2 * EXB * NK * sizeof(Cand)));
+    float *dirs = reinterpret_cast<float *>(b + l.take((size_t)2 * 2 * NK * sizeof(float)));
     const int2 *P = reinterpret_cast<const int2 *>(pts);
     const long long m = sample_size(n);
     const float scale = m > 0 ? 1024.0f / (float)m : 0.f;
@@ -554,11 +609,11 @@ cudaError_t cull_launch(const int32_t *pts, int64_t n, int p, const float *param
         launch(k_gemv1, dim3(NH / 32, KS1), 256, 0, s, rows, scale, params, part1);
         launch(k_gemv2, dim3(NH / 32, KS2), 256, 0, s, part1, params, part2);
     }
-    launch(k_extremes, EXB, EXT, 0, s, P, n, part2, params, cand, y_out, dirs_out);
-    launch(k_cull_init, (p + 255) / 256, 256, 0, s,
-        P, cand, EXB, p, reinterpret_cast<int2 *>(Linit), reinterpret_cast<int2 *>(L), G, G_warm,
-        shift, zero, nzero, reinterpret_cast<int2 *>(poly_out), poly_count,
-        reinterpret_cast<long long *>(ext_out));
+    launch(k_extremes, EXB, EXT, 0, s, P, n, part2, params, cand, y_out, dirs);
+    launch(k_cull_init, (p + 255) / 256, 256, 0, s, P, cand, EXB, params ? 2 : 1, p,
+           reinterpret_cast<int2 *>(Linit), reinterpret_cast<int2 *>(L), G, G_warm, shift, zero,
+           nzero, dirs, dirs_out, reinterpret_cast<int2 *>(poly_out), poly_count,
+           reinterpret_cast<long long *>(ext_out), chosen);
     return cudaGetLastError();
 }
 

@@ -141,6 +141,26 @@ _GEN = {"uniform": uniform, "disc": disc, "gaussian": gaussian,
         "annulus": annulus, "shells": shells}
 
 
+def affine(pts: np.ndarray, p: int, seed: int = 0, min_scale: float = 0.25) -> np.ndarray:
+    """The set under a seeded random similarity-plus-stretch: scaled by
+    (s1, s2) in [min_scale, 1] along its own axes, rotated by a uniform angle
+    about the box centre, shifted by a random offset that keeps it inside,
+    then rounded and clamped to [1, p] (elongated, tilted variants of a
+    shape)."""
+    rng = _rng(seed, 7)
+    s = rng.uniform(min_scale, 1.0, size=2)
+    t = rng.uniform(0.0, 2.0 * np.pi)
+    c = (p + 1) / 2.0
+    z = (np.asarray(pts, dtype=np.float64) - c) * s
+    R = np.array([[np.cos(t), -np.sin(t)], [np.sin(t), np.cos(t)]])
+    z = z @ R.T
+    lo, hi = z.min(axis=0) if len(z) else np.zeros(2), z.max(axis=0) if len(z) else np.zeros(2)
+    room = np.maximum(0.0, (p - 1) / 2.0 - np.maximum(-lo, hi))
+    z += c + rng.uniform(-1.0, 1.0, size=2) * room
+    out = np.clip(np.rint(z), 1, p).astype(np.int32)
+    return np.ascontiguousarray(out)
+
+
 def points(dist: str, n: int, p: int, seed: int = 0) -> np.ndarray:
     """Dispatch by distribution name."""
     return _GEN[dist](n, p, seed)

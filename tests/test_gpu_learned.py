@@ -39,25 +39,28 @@ def check_proposal(P, p, params=None):
     o = {k: host(v) for k, v in out.items()}
     idx = Lm.sample_index(n)
     np.testing.assert_array_equal(o["features"], Lm.histogram(P[idx], p))
-    c, s = o["dirs"][0], o["dirs"][1]
-    if params is None:
-        th = 2 * np.pi * np.arange(16) / 16
-        np.testing.assert_allclose(c, np.cos(th), atol=2e-6)
-        np.testing.assert_allclose(s, np.sin(th), atol=2e-6)
-    else:
+    th0 = 2 * np.pi * np.arange(16) / 16
+    np.testing.assert_allclose(o["dirs"][0][0], np.cos(th0), atol=2e-6)
+    np.testing.assert_allclose(o["dirs"][0][1], np.sin(th0), atol=2e-6)
+    if params is not None:
         y = o["net_out"].astype(np.float64)
         Y = Lm.forward(host(params).astype(np.float64), o["features"])[2][0]
         assert np.max(np.abs(y - Y)) <= 2.0 ** -6 * (np.max(np.abs(Y)) + 1)
         th = Lm.directions(y)
-        np.testing.assert_allclose(c, np.cos(th), atol=4e-6)
-        np.testing.assert_allclose(s, np.sin(th), atol=4e-6)
+        np.testing.assert_allclose(o["dirs"][1][0], np.cos(th), atol=4e-6)
+        np.testing.assert_allclose(o["dirs"][1][1], np.sin(th), atol=4e-6)
+    else:
+        assert o["chosen"][0] == -1
     if n == 0:
         assert np.all(o["extremes"] == -1) and o["poly_count"][0] == 0
         np.testing.assert_array_equal(o["Linit"], oracle.polygon_init(np.zeros((0, 2)), p))
         return o
-    ext = Lm.extremes(P, idx, c, s)
-    np.testing.assert_array_equal(o["extremes"], ext)
-    poly = oracle.hull_points(P[ext])
+    # both sides take the argmax with the GPU's float32 directions
+    poly, sel, ext = Lm.choose_polygon(P, idx, o["dirs"], params is not None)
+    for s_, e in enumerate(ext):
+        np.testing.assert_array_equal(o["extremes"][s_], e)
+    if params is not None:
+        assert o["chosen"][0] == sel
     assert o["poly_count"][0] == poly.shape[0]
     np.testing.assert_array_equal(o["poly"][: poly.shape[0]], poly)
     np.testing.assert_array_equal(o["Linit"], oracle.polygon_init(poly, p))
