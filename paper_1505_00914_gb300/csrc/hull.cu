@@ -7,15 +7,11 @@
 // lower-hull routine serves both.
 //
 // k_hull_filter - per block of 1024 consecutive chain points (in shared
-//                 memory), one thread per point i drops the point when it lies
-//                 on or above the segment between two other points of the
-//                 block, one on each side: the lowest points of the sibling
-//                 sub-blocks of i at every level of a binary min-tree, and the
-//                 points at distances d, e in {s, 2s}, s = 1, 2, 4, ...  Such a
-//                 point is a convex combination of two input points, so it is
-//                 not a strict vertex of the hull and every drop is exact; on
-//                 chains of real data nearly all non-vertices go.  Survivors
-//                 of each block are compacted in order.
+//                 memory), the exact pre-filter of hull_filter.cuh: a point
+//                 on or above a segment between two other points of the
+//                 block, one on each side, is not a strict vertex and goes;
+//                 on chains of real data nearly all non-vertices go.
+//                 Survivors of each block are compacted in order.
 // k_hull_final  - one CTA gathers the survivors, runs Andrew's scan (pop while
 //                 the turn is not strictly counter-clockwise, int64
 //                 orientation) over runs of 16 of them per thread, merges the
