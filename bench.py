@@ -176,6 +176,23 @@ def cpu_oracle_rate(p, inputs, budget_s):
     return done / dt / 1e9, dt, passes
 
 
+def workload_config(workload):
+    """The `config` object of a workload, the same for both arms."""
+    if workload == "learned":
+        p, n, dists = LEARNED
+        return {"workload": "learned", "p": p, "n_per_instance": n, "distributions": list(dists),
+                "instances_per_step": len(dists),
+                "l2": "inputs 8n bytes per instance, larger than L2; no flush"}
+    if workload == "batched":
+        return {"workload": "batched", "sets": BATCH_SETS, "ps": [256, 1024, 4096, 16384],
+                "n_range": [100, 1_000_000], "distributions": ["uniform", "disc", "gaussian"],
+                "l2": "about 8.5 GB of points per step, larger than L2; no flush"}
+    p, n, dists = WORKLOADS[workload]
+    return {"workload": workload, "p": p, "n_per_instance": n, "distributions": list(dists),
+            "instances_per_step": len(dists),
+            "l2": "inputs 8n bytes per instance, larger than L2; no flush"}
+
+
 def _reference_units(workload):
     """The workload as a list of (p, name, points) problems for the oracle."""
     from paper_1505_00914_gb300 import synth
@@ -232,7 +249,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "Gpoints/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "config": {"workload": args.workload, "problems": len(units)},
+        "data": "synthetic", "config": workload_config(args.workload),
         "cpu_baseline": {"value": v, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "Gpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -362,9 +379,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "p": p, "n_per_instance": n,
-                   "distributions": [d for d, _ in inputs], "instances_per_step": len(inputs),
-                   "l2": "inputs 8n bytes per instance, larger than L2; no flush"},
+        "config": workload_config(args.workload),
         "hbm_frac_step": (pts_step * 8 / (ms / args.steps / 1e3) / 1e9) / peak,
         "roofline": {"bound": "hbm", "kernel": kname,
                      "achieved": achieved, "peak": peak,
@@ -485,6 +500,29 @@ def run_learned(args):
             inside = (d[:, 1] >= col[:, 0]) & (d[:, 1] <= col[:, 1])
             cull[dname][arm] = float(inside.float().mean().item())
 
+    # the network's gain on held-out stretched and rotated shapes of the
+    # training family (seeds the training set never used)
+    stretched = {"network": [], "centres": [], "network_polygon_used": 0, "sets": 0}
+    if params is not None:
+        rng = np.random.default_rng(4242)
+        for t in range(16):
+            dname = ("uniform", "disc", "gaussian", "shells")[t % 4]
+            ps_ = int(rng.choice([1024, 4096, 16384, 65536]))
+            Q = synth.affine(synth.points(dname, 300_000, ps_, seed=20_000_000 + t), ps_,
+                             seed=20_000_000 + t)
+            dq = torch.from_numpy(Q).cuda()
+            for arm, prm in (("network", params), ("centres", None)):
+                o = ch.ch_cull_propose(dq, ps_, params=prm)
+                li = o["Linit"].long()
+                col = li[dq[:, 0].long() - 1]
+                yq = dq[:, 1].long()
+                stretched[arm].append(float(((yq >= col[:, 0]) & (yq <= col[:, 1])).float().mean()))
+                if arm == "network":
+                    stretched["network_polygon_used"] += int(o["chosen"].item() == 1)
+            stretched["sets"] += 1
+        for arm in ("network", "centres"):
+            stretched[arm] = float(np.mean(stretched[arm]))
+
     nl = args.steps * len(inputs)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nl)]
     for a, b in evs:
@@ -543,15 +581,14 @@ def run_learned(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms["learned"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": "learned", "p": p, "n_per_instance": n, "distributions": list(dists),
-                   "instances_per_step": len(inputs),
-                   "network": "trained weights" if have_w else "none found: sector centres",
-                   "l2": "inputs 8n bytes per instance, larger than L2; no flush"},
-        "learned": {"plain_gpoints_s": rate["plain"], "centres_gpoints_s": rate["centres"],
+        "config": workload_config("learned"),
+        "learned": {"network": "trained weights" if have_w else "none found: sector centres",
+                    "plain_gpoints_s": rate["plain"], "centres_gpoints_s": rate["centres"],
                     "speedup_vs_plain": rate["learned"] / rate["plain"],
                     "speedup_vs_centres": rate["learned"] / rate["centres"],
                     "ms_per_step": {a: t / args.steps for a, t in ms.items()},
-                    "cull_rate": cull, "hulls_identical": exact, "hull_vertices": hv},
+                    "cull_rate": cull, "hulls_identical": exact, "hull_vertices": hv,
+                    "cull_rate_stretched_heldout": stretched},
         "roofline": {"bound": "hbm", "kernel": KERNEL_OF_FORM[ch.ch_plan_info(n, p)[0]],
                      "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -669,11 +706,10 @@ def run_batched(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": "batched", "sets": B, "points": n_tot, "chunk_mult": best,
-                   "ps": [256, 1024, 4096, 16384], "n_range": [100, 1_000_000],
-                   "launch": "one captured CUDA graph replay per step",
-                   "l2": f"{8 * n_tot / 1e9:.1f} GB of points per step, larger than L2; no flush"},
-        "batched": {"per_set_plain_gpoints_s": world * n_tot / (ms_plain / 1e3) / 1e9,
+        "config": workload_config("batched"),
+        "batched": {"points": n_tot, "chunk_mult": best,
+                    "launch": "one captured CUDA graph replay per step",
+                    "per_set_plain_gpoints_s": world * n_tot / (ms_plain / 1e3) / 1e9,
                     "per_set_plain_ms": ms_plain, "speedup_vs_per_set": ms_plain / (ms / args.steps),
                     "hulls_identical": exact, "autotune_ms": tune_ms},
         "roofline": {"bound": "hbm", "kernel": "k_batched", "achieved": achieved, "peak": peak,
