@@ -198,6 +198,33 @@ int ch_hull_batched(const int32_t *pts, const int64_t *offsets, const int32_t *p
                     int32_t *hull_out, const int64_t *hull_offsets, int32_t *hull_counts,
                     void *workspace, size_t ws_bytes, ch_stream_t stream);
 
+/* ---------------------------------------------------------------------- */
+/* Integer points anywhere in int32: Steps 1 and 2 of the paper's general   */
+/* procedure (Section 2, "Implementation of the proposed heuristic": find   */
+/* the bounding box, translate the points into it, then Algorithm 1), with  */
+/* the columns of L along the shorter side of the box (the sweep along      */
+/* min(p, q) recommended in the same passage).                              */
+/* ---------------------------------------------------------------------- */
+
+int ch_bbox_workspace_size(size_t *bytes);
+
+/* box: device int32[4] = (xmin, xmax, ymin, ymax) of the n points (for
+ * n = 0: (INT32_MAX, INT32_MIN, INT32_MAX, INT32_MIN)).  pts 8-byte aligned. */
+int ch_bbox(const int32_t *pts, int64_t n, int32_t *box, void *workspace, size_t ws_bytes,
+            ch_stream_t stream);
+
+/* host_box: HOST int32[4] = (xmin, xmax, ymin, ymax) enclosing every point
+ * (typically ch_bbox's result copied to the host); each side
+ * (max - min + 1) must be 1 .. CH_MAX_P, else CH_ERR_ARG.  A point outside
+ * the box is reported as CH_ERR_RANGE by ch_sync_status. */
+int ch_convex_hull_box_workspace_size(int64_t n, const int32_t *host_box, size_t *bytes);
+
+/* The strict hull of the points in their own coordinates, counter-clockwise
+ * from the lexicographic minimum: hull capacity 2 * min(p, q) + 2 points
+ * (p, q the box sides). */
+int ch_convex_hull_box(const int32_t *pts, int64_t n, const int32_t *host_box, int32_t *hull,
+                       int32_t *hull_count, void *workspace, size_t ws_bytes, ch_stream_t stream);
+
 /* ch_chain without a workspace (the paper has no counterpart: it is an     */
 /* interface for callers that cannot allocate device memory, e.g. plain C  */
 /* code without a device allocator, or loops that must not call cudaMalloc */

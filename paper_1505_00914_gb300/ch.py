@@ -66,6 +66,10 @@ def _declare(lib):
         "ch_mlp_adam": (ctypes.c_int, [P, P, P, P, i32, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, ctypes.c_float, P]),
         "ch_chain_noalloc": (ctypes.c_int, [P, i32, P, P, P, P, P]),
+        "ch_bbox_workspace_size": (ctypes.c_int, [szp]),
+        "ch_bbox": (ctypes.c_int, [P, i64, P, P, sz, P]),
+        "ch_convex_hull_box_workspace_size": (ctypes.c_int, [i64, P, szp]),
+        "ch_convex_hull_box": (ctypes.c_int, [P, i64, P, P, P, P, sz, P]),
         "ch_cull_workspace_size": (ctypes.c_int, [i32, szp]),
         "ch_cull_propose": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P, P, P, P, sz, P]),
         "ch_hull_learned_workspace_size": (ctypes.c_int, [i64, i32, szp]),
@@ -451,3 +455,55 @@ def ch_hull_learned(pts, p: int, params=None, L=None, Linit=None, lower=None, up
                                  _ptr(hull_count), _ptr(ws), ws.numel(), _stream(stream)),
            "ch_hull_learned")
     return hull, hull_count
+
+
+# ---------------------------------------------------------------- any integer points
+def ch_bbox(pts, box=None, workspace=None, stream=None):
+    """(xmin, xmax, ymin, ymax) of the points as a device int32 tensor (4,)."""
+    pts = _pts(pts)
+    dev = _dev(pts)
+    box = box if box is not None else torch.empty(4, dtype=torch.int32, device=dev)
+    ws = _ws(_size(lib().ch_bbox_workspace_size), dev, workspace)
+    _check(lib().ch_bbox(_ptr(pts), pts.shape[0], _ptr(box), _ptr(ws), ws.numel(), _stream(stream)),
+           "ch_bbox")
+    return box
+
+
+def _host_box(box):
+    import numpy as np
+    b = np.ascontiguousarray(np.asarray(box, dtype=np.int32).reshape(4))
+    return b, b.ctypes.data_as(ctypes.c_void_p)
+
+
+def ch_convex_hull_box_workspace_size(n: int, box) -> int:
+    b, bp = _host_box(box)
+    return _size(lib().ch_convex_hull_box_workspace_size, int(n), bp)
+
+
+def ch_convex_hull_box(pts, box, hull=None, hull_count=None, workspace=None, stream=None):
+    """Hull of points anywhere in int32 given their bounding box (host values
+    xmin, xmax, ymin, ymax); returns (hull, hull_count)."""
+    pts = _pts(pts)
+    dev = _dev(pts)
+    b, bp = _host_box(box)
+    side = int(min(int(b[1]) - int(b[0]), int(b[3]) - int(b[2]))) + 1
+    if hull is None:
+        hull = torch.empty((2 * max(side, 1) + 2, 2), dtype=torch.int32, device=dev)
+    if hull_count is None:
+        hull_count = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = _ws(ch_convex_hull_box_workspace_size(pts.shape[0], b), dev, workspace)
+    _check(lib().ch_convex_hull_box(_ptr(pts), pts.shape[0], bp, _ptr(hull), _ptr(hull_count),
+                                    _ptr(ws), ws.numel(), _stream(stream)), "ch_convex_hull_box")
+    return hull, hull_count
+
+
+def convex_hull(pts, stream=None):
+    """Hull of any int32 points: ch_bbox, a 16-byte read of the box (the one
+    synchronisation), then ch_convex_hull_box.  Returns the vertices as a
+    device tensor (h, 2), counter-clockwise from the lexicographic minimum."""
+    pts = _pts(pts)
+    if pts.shape[0] == 0:
+        return torch.empty((0, 2), dtype=torch.int32, device=pts.device)
+    box = ch_bbox(pts, stream=stream).cpu().numpy()
+    hull, hc = ch_convex_hull_box(pts, box, stream=stream)
+    return hull[: int(hc.item())]

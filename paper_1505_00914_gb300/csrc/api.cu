@@ -79,20 +79,38 @@ struct PathWs {
     size_t state, part, L, lower, upper, counts, hull, end;
 };
 
-int path_layout(int64_t n, int p, PathWs *w)
+// nc columns of nr rows (the square: nc = nr = p).
+int path_layout(int64_t n, int nc, int nr, PathWs *w)
 {
-    int rc = reduce_plan(n, p, &w->plan);
+    int rc = reduce_plan(n, nc, nr, &w->plan);
     if (rc != CH_OK)
         return rc;
     WsLayout l;
-    w->state = l.take(chain_state_bytes(p));
-    w->part = l.take(reduce_partials_bytes(w->plan, p));
-    w->L = l.take((size_t)p * 8);
-    w->lower = l.take((size_t)p * 8);
-    w->upper = l.take((size_t)p * 8);
+    w->state = l.take(chain_state_bytes(nc));
+    w->part = l.take(reduce_partials_bytes(w->plan, nc));
+    w->L = l.take((size_t)nc * 8);
+    w->lower = l.take((size_t)nc * 8);
+    w->upper = l.take((size_t)nc * 8);
     w->counts = l.take(8);
-    w->hull = l.take(hull_ws_bytes(p));
+    w->hull = l.take(hull_ws_bytes(nc));
     w->end = l.off;
+    return CH_OK;
+}
+
+int path_layout(int64_t n, int p, PathWs *w) { return path_layout(n, p, p, w); }
+
+// The frame of a bounding box (xmin, xmax, ymin, ymax): columns along the
+// shorter side; CH_ERR_ARG for an empty box or a side above CH_MAX_P.
+int box_frame(const int32_t *box, Frame *f)
+{
+    const int64_t p = (int64_t)box[1] - box[0] + 1, q = (int64_t)box[3] - box[2] + 1;
+    if (p < 1 || q < 1 || p > CH_MAX_P || q > CH_MAX_P)
+        return CH_ERR_ARG;
+    f->tr = q < p;
+    f->c0 = f->tr ? box[2] : box[0];
+    f->r0 = f->tr ? box[0] : box[2];
+    f->nc = (int)std::min(p, q);
+    f->nr = (int)std::max(p, q);
     return CH_OK;
 }
 
@@ -219,9 +237,9 @@ int ch_reduce(const int32_t *pts, int64_t n, int32_t p, int32_t *L, void *worksp
     void *part = workspace;
     cudaEvent_t ev0, ev1;
     next_trace(&ev0, &ev1);
-    cudaError_t e = reduce_launch(pl, pts, n, p, part, L, st, s, nullptr, 0, ev0, ev1);
+    cudaError_t e = reduce_launch(pl, pts, n, square_frame(p), part, L, st, s, nullptr, 0, ev0, ev1);
     if (e == cudaSuccess && pl.mode == 0)
-        e = reduce_merge_launch(part, pl.copies, p, L, s);
+        e = reduce_merge_launch(part, pl.copies, p, p, L, s);
     return cuda_rc(e);
 }
 
@@ -320,14 +338,14 @@ int ch_convex_hull(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t
     unsigned long long *zero = reinterpret_cast<unsigned long long *>(b + w.state);
     const int nzero = (int)(chain_state_bytes(p) / 8);
     // the look-back state is cleared by the last kernel before the chain step
-    cudaError_t e = reduce_launch(w.plan, pts, n, p, part, L, st, s,
+    cudaError_t e = reduce_launch(w.plan, pts, n, square_frame(p), part, L, st, s,
                                   w.plan.mode == 0 ? nullptr : zero, nzero, ev0, ev1);
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
     if (w.plan.mode == 0) {
         if (!L)
             L = reinterpret_cast<int32_t *>(b + w.L);
-        e = reduce_merge_launch(part, w.plan.copies, p, L, s, zero, nzero);
+        e = reduce_merge_launch(part, w.plan.copies, p, p, L, s, zero, nzero);
         if (e != cudaSuccess)
             return CH_ERR_CUDA;
     }
@@ -610,7 +628,7 @@ int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *param
     // clear the chain's look-back state); the culling step then writes
     // Linit, the start of L (filtered forms) and tightens the filter with
     // the polygon (mode 1); in mode 0 it clears the look-back state itself
-    cudaError_t e = reduce_warm_launch(pw.plan, pts, n, p, part, L, s, zero, nzero);
+    cudaError_t e = reduce_warm_launch(pw.plan, pts, n, square_frame(p), part, L, s, zero, nzero);
     if (e == cudaSuccess)
         e = cull_launch(pts, n, p, params, b + w.cull, Linit, mode != 0 ? L : nullptr,
                         mode == 1 ? reinterpret_cast<uint16_t *>(part) : nullptr, mode == 1,
@@ -620,9 +638,9 @@ int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *param
         return CH_ERR_CUDA;
     cudaEvent_t ev0, ev1;
     next_trace(&ev0, &ev1);
-    e = reduce_launch(pw.plan, pts, n, p, part, L, st, s, nullptr, 0, ev0, ev1, true);
+    e = reduce_launch(pw.plan, pts, n, square_frame(p), part, L, st, s, nullptr, 0, ev0, ev1, true);
     if (e == cudaSuccess && mode == 0)
-        e = reduce_merge_launch(part, pw.plan.copies, p, L, s, nullptr, 0, Linit);
+        e = reduce_merge_launch(part, pw.plan.copies, p, p, L, s, nullptr, 0, Linit);
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
     const HullLayout hl = hull_layout(p);
@@ -633,6 +651,106 @@ int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *param
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
     return cuda_rc(hull_final_launch(hl, hw, hull, hull_count, s));
+}
+
+// ---------------------------------------------------------------- any integer points
+int ch_bbox_workspace_size(size_t *bytes)
+{
+    if (!bytes)
+        return CH_ERR_ARG;
+    *bytes = (size_t)bbox_parts() * 16;
+    return CH_OK;
+}
+
+int ch_bbox(const int32_t *pts, int64_t n, int32_t *box, void *workspace, size_t ws_bytes,
+            ch_stream_t stream)
+{
+    if (n < 0 || (n > 0 && !pts) || !box || !aligned8(pts))
+        return CH_ERR_ARG;
+    if (ws_bytes < (size_t)bbox_parts() * 16 || !workspace)
+        return CH_ERR_WORKSPACE;
+    return cuda_rc(bbox_launch(pts, n, box, workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+namespace {
+struct BoxWs {
+    PathWs path;
+    size_t hull, count, end;
+};
+
+int box_layout(int64_t n, const Frame &f, BoxWs *w)
+{
+    int rc = path_layout(n, f.nc, f.nr, &w->path);
+    if (rc != CH_OK)
+        return rc;
+    WsLayout l;
+    l.off = w->path.end;
+    w->hull = l.take((size_t)(2 * f.nc + 2) * 8);
+    w->count = l.take(8);
+    w->end = l.off;
+    return CH_OK;
+}
+}  // namespace
+
+int ch_convex_hull_box_workspace_size(int64_t n, const int32_t *host_box, size_t *bytes)
+{
+    Frame f;
+    if (!bytes || !host_box || n < 0 || box_frame(host_box, &f) != CH_OK)
+        return CH_ERR_ARG;
+    BoxWs w;
+    int rc = box_layout(n, f, &w);
+    if (rc != CH_OK)
+        return rc;
+    *bytes = w.end;
+    return CH_OK;
+}
+
+int ch_convex_hull_box(const int32_t *pts, int64_t n, const int32_t *host_box, int32_t *hull,
+                       int32_t *hull_count, void *workspace, size_t ws_bytes, ch_stream_t stream)
+{
+    Frame f;
+    if (n < 0 || (n > 0 && !pts) || !host_box || !hull || !hull_count || !aligned8(pts) ||
+        !aligned8(hull) || box_frame(host_box, &f) != CH_OK)
+        return CH_ERR_ARG;
+    BoxWs w;
+    int rc = box_layout(n, f, &w);
+    if (rc != CH_OK)
+        return rc;
+    if (ws_bytes < w.end || !workspace)
+        return CH_ERR_WORKSPACE;
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *b = reinterpret_cast<char *>(workspace);
+    const PathWs &pw = w.path;
+    int32_t *L = reinterpret_cast<int32_t *>(b + pw.L);
+    int32_t *lower = reinterpret_cast<int32_t *>(b + pw.lower);
+    int32_t *upper = reinterpret_cast<int32_t *>(b + pw.upper);
+    int32_t *counts = reinterpret_cast<int32_t *>(b + pw.counts);
+    void *part = b + pw.part;
+    unsigned long long *zero = reinterpret_cast<unsigned long long *>(b + pw.state);
+    const int nzero = (int)(chain_state_bytes(f.nc) / 8);
+    cudaEvent_t ev0, ev1;
+    next_trace(&ev0, &ev1);
+    cudaError_t e = reduce_launch(pw.plan, pts, n, f, part, L, st, s,
+                                  pw.plan.mode == 0 ? nullptr : zero, nzero, ev0, ev1);
+    if (e == cudaSuccess && pw.plan.mode == 0)
+        e = reduce_merge_launch(part, pw.plan.copies, f.nc, f.nr, L, s, zero, nzero);
+    if (e != cudaSuccess)
+        return CH_ERR_CUDA;
+    const HullLayout hl = hull_layout(f.nc);
+    char *hw = b + pw.hull;
+    e = chain_launch(L, f.nc, lower, upper, counts, nullptr, zero, true,
+                     reinterpret_cast<int2 *>(hw + hl.cand), reinterpret_cast<int *>(hw + hl.ccnt),
+                     st, s, nullptr, f.nr);
+    if (e == cudaSuccess)
+        e = hull_final_launch(hl, hw, reinterpret_cast<int32_t *>(b + w.hull),
+                              reinterpret_cast<int32_t *>(b + w.count), s);
+    if (e == cudaSuccess)
+        e = unframe_launch(reinterpret_cast<int32_t *>(b + w.hull),
+                           reinterpret_cast<int32_t *>(b + w.count), f, hull, hull_count, s);
+    return cuda_rc(e);
 }
 
 int ch_convex_hull_host_workspace_size(int64_t n, int32_t p, size_t *bytes)

@@ -70,6 +70,31 @@ struct WsLayout {
     }
 };
 
+// ---- frame of Algorithm 1 ----
+// The columns of L run along x (tr = 0) or along y (tr = 1, the sweep along
+// the shorter side of the bounding box); a point (x, y) with u = tr ? y : x,
+// v = tr ? x : y lands in column u - c0 (0-based, < nc) at row v - r0 + 1
+// (1-based, <= nr).  The square of side p of Section 2.1 is {1, 1, p, p, 0}.
+struct Frame {
+    int c0, r0;
+    int nc, nr;
+    int tr;
+};
+inline Frame square_frame(int p) { return Frame{1, 1, p, p, 0}; }
+
+// Column c (0-based) and row index rr = row - 1 of point (x, y); unsigned
+// arithmetic, so that any out-of-frame point gives c >= nc or rr >= nr.
+// FM: 0 the square (offsets 1, known at compile time), 1 a translated frame,
+// 2 a translated and transposed frame.
+template <int FM>
+__device__ __forceinline__ void frame_map(const Frame &f, int x, int y, uint32_t &c, uint32_t &rr)
+{
+    const int u = FM == 2 ? y : x, v = FM == 2 ? x : y;
+    c = (uint32_t)u - (uint32_t)(FM == 0 ? 1 : f.c0);
+    rr = (uint32_t)v - (uint32_t)(FM == 0 ? 1 : f.r0);
+}
+inline int frame_mode(const Frame &f) { return f.tr ? 2 : (f.c0 == 1 && f.r0 == 1 ? 0 : 1); }
+
 // ---- reduction (reduce.cu) ----
 struct ReducePlan {
     int mode;      // 0: private copies, 1: filtered global L, 2: global L only
@@ -80,8 +105,10 @@ struct ReducePlan {
     int shift;     // modes 1-2: row-bin shift of the filter
     size_t smem;   // dynamic shared memory per CTA
 };
-int reduce_plan(int64_t n, int p, ReducePlan *plan);
-size_t reduce_partials_bytes(const ReducePlan &plan, int p);
+// Plan for nc columns of nr rows (the square: nc = nr = p).
+int reduce_plan(int64_t n, int nc, int nr, ReducePlan *plan);
+inline int reduce_plan(int64_t n, int p, ReducePlan *plan) { return reduce_plan(n, p, p, plan); }
+size_t reduce_partials_bytes(const ReducePlan &plan, int nc);
 // Mode 0 writes plan.copies packed uint32[p] partial arrays to `scratch`
 // (((lo-1) << 16) | (hi-1), 0xFFFF0000 when empty); modes 1-2 write the final
 // L (mode 1 keeps its global filter in `scratch`).
@@ -90,7 +117,7 @@ size_t reduce_partials_bytes(const ReducePlan &plan, int p);
 // and after the main reduction kernel (the dominant one), or nullptr.
 // prefilled: the culling step has already written L (modes 1-2) and the
 // filter (mode 1, at the start of `scratch`), so the warm-up is skipped.
-cudaError_t reduce_launch(const ReducePlan &plan, const int32_t *pts, int64_t n, int p,
+cudaError_t reduce_launch(const ReducePlan &plan, const int32_t *pts, int64_t n, const Frame &f,
                           void *scratch, int32_t *L, unsigned *status, cudaStream_t s,
                           unsigned long long *zero = nullptr, int nzero = 0,
                           cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
@@ -99,12 +126,12 @@ int reduce_kernel_count(const ReducePlan &plan);
 // The part of reduce_launch before the main pass: mode 1 the filter warm-up
 // and merge (L = (p+1, -1), G ready), mode 2 the fill of L; both clear
 // zero/nzero.  Mode 0 launches nothing.
-cudaError_t reduce_warm_launch(const ReducePlan &plan, const int32_t *pts, int64_t n, int p,
-                               void *scratch, int32_t *L, cudaStream_t s, unsigned long long *zero,
-                               int nzero);
+cudaError_t reduce_warm_launch(const ReducePlan &plan, const int32_t *pts, int64_t n,
+                               const Frame &f, void *scratch, int32_t *L, cudaStream_t s,
+                               unsigned long long *zero, int nzero);
 // L = column-wise merge of `copies` packed partial arrays (folded with the
 // culling start array Linit when given).
-cudaError_t reduce_merge_launch(const void *partials, int copies, int p, int32_t *L,
+cudaError_t reduce_merge_launch(const void *partials, int copies, int nc, int nr, int32_t *L,
                                 cudaStream_t s, unsigned long long *zero = nullptr, int nzero = 0,
                                 const int32_t *Linit = nullptr);
 // Filter shift of the filtered form: (p - 1) >> shift <= 255.
@@ -118,10 +145,12 @@ size_t chain_state_bytes(int p);
 // hull_final_launch can follow directly).  state: chain_state_bytes(p),
 // zeroed here unless state_zeroed.
 // Linit != nullptr: chains of a culled reduction (see k_chain); counts[0] and
-// counts[1] then differ.
+// counts[1] then differ.  nr: rows of the frame (empty columns hold
+// (nr + 1, -1)); 0 means p.
 cudaError_t chain_launch(const int32_t *L, int p, int32_t *lower, int32_t *upper, int32_t *counts,
                          uint32_t *mask, void *state, bool state_zeroed, int2 *cand, int *ccnt,
-                         unsigned *status, cudaStream_t s, const int32_t *Linit = nullptr);
+                         unsigned *status, cudaStream_t s, const int32_t *Linit = nullptr,
+                         int nr = 0);
 
 // ---- hull (hull.cu) ----
 struct HullLayout {
@@ -182,6 +211,14 @@ cudaError_t cull_launch(const int32_t *pts, int64_t n, int p, const float *param
                         float *dirs_out, int32_t *poly_out, int32_t *poly_count, int64_t *ext_out,
                         int32_t *chosen, cudaStream_t s);
 int cull_kernel_count(bool net);
+
+// ---- bounding box and frames (box.cu) ----
+int bbox_parts();
+// box[4] = (xmin, xmax, ymin, ymax) of pts; ws: bbox_parts() * 16 bytes.
+cudaError_t bbox_launch(const int32_t *pts, int64_t n, int32_t *box, void *ws, cudaStream_t s);
+// Hull from frame coordinates back to the input's (see k_unframe).
+cudaError_t unframe_launch(const int32_t *hull_in, const int32_t *count_in, const Frame &f,
+                           int32_t *hull_out, int32_t *count_out, cudaStream_t s);
 
 // ---- api.cu ----
 unsigned *device_status_ptr();  // this device's status word (nullptr on failure)

@@ -122,7 +122,7 @@ constexpr long long CNT_LOW = (1ll << CNT_SHIFT) - 1;
 
 template <bool FILTER, bool CULL>
 __global__ void __launch_bounds__(TILE)
-    k_chain(const int2 *__restrict__ L, const int2 *__restrict__ Linit, int p, int2 *lower,
+    k_chain(const int2 *__restrict__ L, const int2 *__restrict__ Linit, int p, int nr, int2 *lower,
             int2 *upper, int *counts, uint32_t *mask, unsigned long long *state, int ntiles,
             int2 *cand, int *ccnt, unsigned *status)
 {
@@ -138,14 +138,14 @@ __global__ void __launch_bounds__(TILE)
     const int tile = s_tile;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int c = tile * TILE + threadIdx.x;  // 0-based column
-    const int2 e = c < p ? L[c] : make_int2(p + 1, -1);
+    const int2 e = c < p ? L[c] : make_int2(nr + 1, -1);
     bool v0, v1;
     if constexpr (CULL) {
-        const int2 li = c < p ? Linit[c] : make_int2(p + 1, -1);
+        const int2 li = c < p ? Linit[c] : make_int2(nr + 1, -1);
         v0 = c < p && e.x < li.x;
         v1 = c < p && e.y > li.y;
     } else {
-        v0 = v1 = c < p && !(e.x == p + 1 && e.y == -1);
+        v0 = v1 = c < p && !(e.x == nr + 1 && e.y == -1);
     }
     const unsigned bal0 = __ballot_sync(0xFFFFFFFFu, v0);
     const unsigned bal1 = CULL ? __ballot_sync(0xFFFFFFFFu, v1) : bal0;
@@ -242,8 +242,10 @@ size_t chain_state_bytes(int p) { return (size_t)(chain_tiles(p) + 1) * 8; }
 
 cudaError_t chain_launch(const int32_t *L, int p, int32_t *lower, int32_t *upper, int32_t *counts,
                          uint32_t *mask, void *state, bool state_zeroed, int2 *cand, int *ccnt,
-                         unsigned *status, cudaStream_t s, const int32_t *Linit)
+                         unsigned *status, cudaStream_t s, const int32_t *Linit, int nr)
 {
+    if (nr <= 0)
+        nr = p;
     const int nt = chain_tiles(p);
     if (!state_zeroed) {
         cudaError_t e = cudaMemsetAsync(state, 0, chain_state_bytes(p), s);
@@ -254,16 +256,16 @@ cudaError_t chain_launch(const int32_t *L, int p, int32_t *lower, int32_t *upper
     const int2 *L2 = reinterpret_cast<const int2 *>(L), *Li = reinterpret_cast<const int2 *>(Linit);
     int2 *lo = reinterpret_cast<int2 *>(lower), *up = reinterpret_cast<int2 *>(upper);
     if (cand && Linit)
-        launch(k_chain<true, true>, nt, TILE, 0, s, L2, Li, p, lo, up, counts, mask, st, nt, cand, ccnt,
+        launch(k_chain<true, true>, nt, TILE, 0, s, L2, Li, p, nr, lo, up, counts, mask, st, nt, cand, ccnt,
                                                 status);
     else if (cand)
-        launch(k_chain<true, false>, nt, TILE, 0, s, L2, nullptr, p, lo, up, counts, mask, st, nt, cand,
+        launch(k_chain<true, false>, nt, TILE, 0, s, L2, nullptr, p, nr, lo, up, counts, mask, st, nt, cand,
                                                  ccnt, status);
     else if (Linit)
-        launch(k_chain<false, true>, nt, TILE, 0, s, L2, Li, p, lo, up, counts, mask, st, nt, nullptr,
+        launch(k_chain<false, true>, nt, TILE, 0, s, L2, Li, p, nr, lo, up, counts, mask, st, nt, nullptr,
                                                  nullptr, status);
     else
-        launch(k_chain<false, false>, nt, TILE, 0, s, L2, nullptr, p, lo, up, counts, mask, st, nt,
+        launch(k_chain<false, false>, nt, TILE, 0, s, L2, nullptr, p, nr, lo, up, counts, mask, st, nt,
                                                   nullptr, nullptr, status);
     return cudaGetLastError();
 }

@@ -96,30 +96,31 @@ __device__ __forceinline__ void stream_pairs(const int4 *__restrict__ p4, int64_
 }
 
 // ---------------------------------------------------------------- private
-template <int RT>
+template <int RT, int FM>
 __global__ void __launch_bounds__(RT)
-    k_reduce_private(const int32_t *__restrict__ pts, int64_t n, int p,
+    k_reduce_private(const int32_t *__restrict__ pts, int64_t n, Frame f,
                      uint32_t *__restrict__ part, unsigned *status)
 {
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) int sI[];
-    int *slo = sI, *shi = sI + p;
-    for (int i = threadIdx.x; i < p; i += RT) {
-        slo[i] = p + 1;
+    const int nc = f.nc;
+    int *slo = sI, *shi = sI + nc;
+    for (int i = threadIdx.x; i < nc; i += RT) {
+        slo[i] = f.nr + 1;
         shi[i] = -1;
     }
     __syncthreads();
-    const uint32_t up = (uint32_t)p;
     bool bad = false;
     auto fold = [&](int x, int y) {
-        const uint32_t c = (uint32_t)(x - 1);
-        if (c >= up || (uint32_t)(y - 1) >= up) {
+        uint32_t c, rr;
+        frame_map<FM>(f, x, y, c, rr);
+        if (c >= (uint32_t)nc || rr >= (uint32_t)f.nr) {
             bad = true;
             return;
         }
-        atomicMin(slo + c, y);
-        atomicMax(shi + c, y);
+        atomicMin(slo + c, (int)rr + 1);
+        atomicMax(shi + c, (int)rr + 1);
     };
     const PairView pv = pair_view(pts, n);
     if (blockIdx.x == 0 && threadIdx.x == 0 && pv.head)
@@ -134,65 +135,68 @@ __global__ void __launch_bounds__(RT)
         fold(v.z, v.w);
     });
     __syncthreads();
-    uint32_t *out = part + (size_t)blockIdx.x * p;
-    for (int i = threadIdx.x; i < p; i += RT)
-        out[i] = slo[i] <= p ? ((uint32_t)(slo[i] - 1) << 16) | (uint32_t)(shi[i] - 1) : 0xFFFF0000u;
+    uint32_t *out = part + (size_t)blockIdx.x * nc;
+    for (int i = threadIdx.x; i < nc; i += RT)  // rows <= 65536 in this form
+        out[i] = slo[i] <= f.nr ? ((uint32_t)(slo[i] - 1) << 16) | (uint32_t)(shi[i] - 1)
+                                : 0xFFFF0000u;
     if (__syncthreads_or(bad) && threadIdx.x == 0)
         atomicOr(status, ST_RANGE);
 }
 
 // --------------------------------------------------------------- filtered
-__global__ void k_fill_empty(int2 *L, int p, unsigned long long *zero, int nzero)
+__global__ void k_fill_empty(int2 *L, int nc, int nr, unsigned long long *zero, int nzero)
 {
     pdl_wait();
     pdl_trigger();
     if (zero && blockIdx.x == 0)
         for (int i = threadIdx.x; i < nzero; i += blockDim.x)
             zero[i] = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p; i += gridDim.x * blockDim.x)
-        L[i] = make_int2(p + 1, -1);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+        L[i] = make_int2(nr + 1, -1);
 }
 
 // Read-then-atomic fold of one point into the global L.
-__device__ __forceinline__ bool fold_global(int2 *L, uint32_t up, int x, int y)
+template <int FM>
+__device__ __forceinline__ bool fold_global(int2 *L, const Frame &f, int x, int y)
 {
-    const uint32_t c = (uint32_t)(x - 1);
-    if (c >= up || (uint32_t)(y - 1) >= up)
+    uint32_t c, rr;
+    frame_map<FM>(f, x, y, c, rr);
+    if (c >= (uint32_t)f.nc || rr >= (uint32_t)f.nr)
         return false;
+    const int r = (int)rr + 1;
     const int2 e = L[c];
-    if (y < e.x)
-        atomicMin(&L[c].x, y);
-    if (y > e.y)
-        atomicMax(&L[c].y, y);
+    if (r < e.x)
+        atomicMin(&L[c].x, r);
+    if (r > e.y)
+        atomicMax(&L[c].y, r);
     return true;
 }
 
-// Whole input through the read-then-atomic test (p too large for a filter).
+// Whole input through the read-then-atomic test (too many columns for a filter).
+template <int FM>
 __global__ void __launch_bounds__(256)
-    k_reduce_global(const int32_t *__restrict__ pts, int64_t n, int p, int2 *L, unsigned *status)
+    k_reduce_global(const int32_t *__restrict__ pts, int64_t n, Frame f, int2 *L, unsigned *status)
 {
     pdl_wait();
     pdl_trigger();
     const PairView pv = pair_view(pts, n);
-    const uint32_t up = (uint32_t)p;
     bool bad = false;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < pv.npairs;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int4 v = __ldcs(pv.p4 + j);
-        bad |= !fold_global(L, up, v.x, v.y);
-        bad |= !fold_global(L, up, v.z, v.w);
+        bad |= !fold_global<FM>(L, f, v.x, v.y);
+        bad |= !fold_global<FM>(L, f, v.z, v.w);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (pv.head)
-            bad |= !fold_global(L, up, pts[0], pts[1]);
+            bad |= !fold_global<FM>(L, f, pts[0], pts[1]);
         if (pv.tail)
-            bad |= !fold_global(L, up, pts[2 * (n - 1)], pts[2 * (n - 1) + 1]);
+            bad |= !fold_global<FM>(L, f, pts[2 * (n - 1)], pts[2 * (n - 1) + 1]);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0)
         atomicOr(status, ST_RANGE);
 }
 
-__device__ __forceinline__ uint32_t bin_of(int y, int shift) { return (uint32_t)(y - 1) >> shift; }
 
 constexpr int WARM_DIV = 16;  // the warm-up reads the first 1/WARM_DIV of each slice
 
@@ -216,26 +220,26 @@ __device__ __forceinline__ uint4 tighter8(uint4 a, uint4 b)
     return make_uint4(tighter2(a.x, b.x), tighter2(a.y, b.y), tighter2(a.z, b.z), tighter2(a.w, b.w));
 }
 
-template <int RT>
+template <int RT, int FM>
 __global__ void __launch_bounds__(RT)
-    k_filter_warm(const int32_t *__restrict__ pts, int64_t n, int p, int shift, int grid,
+    k_filter_warm(const int32_t *__restrict__ pts, int64_t n, Frame fr, int shift, int grid,
                   uint16_t *__restrict__ slots)
 {
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) uint16_t F[];
     unsigned char *fb = reinterpret_cast<unsigned char *>(F);
-    const int words = (p + 7) / 8;
+    const int words = (fr.nc + 7) / 8;
     uint4 *F4 = reinterpret_cast<uint4 *>(F);
     for (int i = threadIdx.x; i < words; i += RT)
         F4[i] = make_uint4(0xFF00FF00u, 0xFF00FF00u, 0xFF00FF00u, 0xFF00FF00u);
     __syncthreads();
-    const uint32_t up = (uint32_t)p;
     auto learn = [&](int x, int y) {
-        const uint32_t c = (uint32_t)(x - 1);
-        if (c >= up || (uint32_t)(y - 1) >= up)
+        uint32_t c, rr;
+        frame_map<FM>(fr, x, y, c, rr);
+        if (c >= (uint32_t)fr.nc || rr >= (uint32_t)fr.nr)
             return;
-        const uint32_t f = F[c], b = bin_of(y, shift);
+        const uint32_t f = F[c], b = rr >> shift;
         if (b < (f >> 8))
             fb[2 * c + 1] = (unsigned char)b;
         if (b > (f & 0xFFu))
@@ -261,7 +265,7 @@ __global__ void __launch_bounds__(RT)
 constexpr int MG_V = 32, MG_GROUPS = 32;
 
 __global__ void __launch_bounds__(MG_V *MG_GROUPS)
-    k_filter_merge(const uint16_t *__restrict__ slots, int rows, int p, uint16_t *__restrict__ G,
+    k_filter_merge(const uint16_t *__restrict__ slots, int rows, int p, int nr, uint16_t *__restrict__ G,
                    int2 *__restrict__ L, unsigned long long *zero, int nzero)
 {
     pdl_wait();
@@ -299,12 +303,12 @@ __global__ void __launch_bounds__(MG_V *MG_GROUPS)
     }
     const int c0 = blockIdx.x * MG_V * 8;
     for (int c = c0 + threadIdx.x; c < min(p, c0 + MG_V * 8); c += MG_V * MG_GROUPS)
-        L[c] = make_int2(p + 1, -1);
+        L[c] = make_int2(nr + 1, -1);
 }
 
-template <int RT>
+template <int RT, int FM>
 __global__ void __launch_bounds__(RT)
-    k_reduce_filtered(const int32_t *__restrict__ pts, int64_t n, int p, int shift,
+    k_reduce_filtered(const int32_t *__restrict__ pts, int64_t n, Frame fr, int shift,
                       const uint16_t *__restrict__ G, int2 *L, unsigned *status)
 {
     pdl_wait();
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(RT)
     extern __shared__ __align__(16) uint16_t F[];
     unsigned char *fb = reinterpret_cast<unsigned char *>(F);
     {
-        const int words = (p + 7) / 8;
+        const int words = (fr.nc + 7) / 8;
         const uint4 *G4 = reinterpret_cast<const uint4 *>(G);
         uint4 *F4 = reinterpret_cast<uint4 *>(F);
         for (int i0 = threadIdx.x; i0 < words; i0 += RT * 8) {
@@ -328,23 +332,24 @@ __global__ void __launch_bounds__(RT)
         }
     }
     __syncthreads();
-    const uint32_t up = (uint32_t)p;
     bool bad = false;
     auto fold = [&](int x, int y) {
-        const uint32_t c = (uint32_t)(x - 1);
-        if (c >= up || (uint32_t)(y - 1) >= up) {
+        uint32_t c, rr;
+        frame_map<FM>(fr, x, y, c, rr);
+        if (c >= (uint32_t)fr.nc || rr >= (uint32_t)fr.nr) {
             bad = true;
             return;
         }
-        const uint32_t f = F[c], b = bin_of(y, shift);
+        const int r = (int)rr + 1;
+        const uint32_t f = F[c], b = rr >> shift;
         const uint32_t qlo = f >> 8, qhi = f & 0xFFu;
         if (b <= qlo) {
-            atomicMin(&L[c].x, y);
+            atomicMin(&L[c].x, r);
             if (b < qlo)
                 fb[2 * c + 1] = (unsigned char)b;
         }
         if (b >= qhi) {
-            atomicMax(&L[c].y, y);
+            atomicMax(&L[c].y, r);
             if (b > qhi)
                 fb[2 * c] = (unsigned char)b;
         }
@@ -368,7 +373,7 @@ __global__ void __launch_bounds__(RT)
 // with 32 thread groups; group g folds rows g, g + 32, ... (all loads of a
 // thread in flight together), and the groups combine through shared memory.
 __global__ void __launch_bounds__(1024)
-    k_merge_partials(const uint32_t *__restrict__ part, int copies, int p, int2 *L,
+    k_merge_partials(const uint32_t *__restrict__ part, int copies, int p, int nr, int2 *L,
                      unsigned long long *zero, int nzero, const int2 *__restrict__ Linit)
 {
     pdl_wait();
@@ -408,7 +413,7 @@ __global__ void __launch_bounds__(1024)
             lo = min(lo, s_lo[h][v]);
             hi = max(hi, s_hi[h][v]);
         }
-        int2 r = lo <= hi ? make_int2((int)lo + 1, (int)hi + 1) : make_int2(p + 1, -1);
+        int2 r = lo <= hi ? make_int2((int)lo + 1, (int)hi + 1) : make_int2(nr + 1, -1);
         if (Linit) {  // a culled reduction starts from Linit instead of (p+1, -1)
             const int2 li = Linit[c];
             r = make_int2(min(r.x, li.x), max(r.y, li.y));
@@ -440,33 +445,31 @@ int dev_setup(int *dev_out)
         if (cudaDeviceGetAttribute(&d.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
             cudaSuccess)
             return -1;
-        cudaFuncSetAttribute(k_reduce_private<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             d.optin);
-        cudaFuncSetAttribute(k_reduce_private<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             d.optin);
-        cudaFuncSetAttribute(k_reduce_filtered<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             d.optin);
-        cudaFuncSetAttribute(k_filter_warm<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             d.optin);
+        const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        cudaFuncSetAttribute(k_reduce_private<1024, 0>, a, d.optin);
+        cudaFuncSetAttribute(k_reduce_private<1024, 1>, a, d.optin);
+        cudaFuncSetAttribute(k_reduce_private<1024, 2>, a, d.optin);
+        cudaFuncSetAttribute(k_reduce_filtered<1024, 0>, a, d.optin);
+        cudaFuncSetAttribute(k_reduce_filtered<1024, 1>, a, d.optin);
+        cudaFuncSetAttribute(k_reduce_filtered<1024, 2>, a, d.optin);
+        cudaFuncSetAttribute(k_filter_warm<1024, 0>, a, d.optin);
+        cudaFuncSetAttribute(k_filter_warm<1024, 1>, a, d.optin);
+        cudaFuncSetAttribute(k_filter_warm<1024, 2>, a, d.optin);
         d.ready = true;
     }
     return d.optin;
 }
 
-int private_bps(int dev, int threads, size_t smem)
+int private_bps(int dev, size_t smem)
 {
     std::lock_guard<std::mutex> g(g_dev_mu);
-    auto key = std::make_pair(dev * 2 + (threads == 1024), smem);
+    auto key = std::make_pair(dev, smem);
     auto it = g_bps.find(key);
     if (it != g_bps.end())
         return it->second;
     int bps = 0;
-    cudaError_t e = threads == 512
-                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_reduce_private<512>,
-                                                                        512, smem)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                              &bps, k_reduce_private<1024>, 1024, smem);
-    if (e != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_reduce_private<1024, 0>, 1024,
+                                                      smem) != cudaSuccess)
         return -1;
     g_bps[key] = bps;
     return bps;
@@ -482,7 +485,7 @@ int filter_shift(int p)
 
 }  // namespace
 
-int reduce_plan(int64_t n, int p, ReducePlan *pl)
+int reduce_plan(int64_t n, int nc, int nr, ReducePlan *pl)
 {
     const int sms = sm_count();
     if (sms <= 0)
@@ -494,24 +497,23 @@ int reduce_plan(int64_t n, int p, ReducePlan *pl)
     const size_t optin = (size_t)optin_i;
     const int64_t npairs = n / 2;
     pl->cluster = 1;
-    if ((size_t)p * 8 <= optin) {
-        pl->mode = 0;  // private copies
-        pl->smem = (size_t)p * 8;
-        pl->threads = 1024;
+    pl->threads = 1024;
+    if ((size_t)nc * 8 <= optin && nr <= 65536) {
+        pl->mode = 0;  // private copies (rows packed in 16 bits for the merge)
+        pl->smem = (size_t)nc * 8;
         // at least ~16K points per CTA so a private copy pays for its merge
         const int64_t want = std::max<int64_t>(1, (npairs + 8191) / 8192);
-        const int bps = private_bps(dev, pl->threads, pl->smem);
+        const int bps = private_bps(dev, pl->smem);
         if (bps < 0)
             return CH_ERR_CUDA;
         pl->grid = (int)std::min<int64_t>(want, (int64_t)std::max(1, std::min(bps, 1)) * sms);
         pl->copies = pl->grid;
     } else {
-        pl->mode = (size_t)p * 2 <= optin ? 1 : 2;  // filtered / sampled-only
-        pl->threads = 1024;
-        pl->smem = pl->mode == 1 ? (((size_t)p * 2 + 15) & ~size_t(15)) : 0;
+        pl->mode = (size_t)nc * 2 <= optin ? 1 : 2;  // filtered / read-then-atomic
+        pl->smem = pl->mode == 1 ? (((size_t)nc * 2 + 15) & ~size_t(15)) : 0;
         pl->grid = sms;
         pl->copies = 0;
-        pl->shift = filter_shift(p);
+        pl->shift = filter_shift(nr);
     }
     return CH_OK;
 }
@@ -523,84 +525,94 @@ int reduce_kernel_count(const ReducePlan &pl)
     return pl.mode == 0 ? 1 : (pl.mode == 1 ? 3 : 2);
 }
 
-size_t reduce_partials_bytes(const ReducePlan &pl, int p)
+size_t reduce_partials_bytes(const ReducePlan &pl, int nc)
 {
     if (pl.mode == 0)
-        return (size_t)pl.copies * (size_t)p * 4;
+        return (size_t)pl.copies * (size_t)nc * 4;
     if (pl.mode == 1)  // merged filter G, then one slot row per CTA
-        return (((size_t)p * 2 + 255) & ~size_t(255)) + (size_t)pl.grid * (((size_t)p + 7) / 8) * 16;
+        return (((size_t)nc * 2 + 255) & ~size_t(255)) + (size_t)pl.grid * (((size_t)nc + 7) / 8) * 16;
     return 0;
 }
 
-cudaError_t reduce_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, int p,
+namespace {
+
+template <int FM>
+void launch_warm(const ReducePlan &pl, const int32_t *pts, int64_t n, const Frame &f, void *part,
+                 int2 *L2, cudaStream_t s, unsigned long long *zero, int nzero)
+{
+    uint16_t *G = reinterpret_cast<uint16_t *>(part);
+    uint16_t *slots = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(part) +
+                                                   ((((size_t)f.nc * 2) + 255) & ~size_t(255)));
+    launch(k_filter_warm<1024, FM>, pl.grid, 1024, pl.smem, s, pts, n, f, pl.shift, pl.grid, slots);
+    const int words = (f.nc + 7) / 8;
+    launch(k_filter_merge, (words + MG_V - 1) / MG_V, MG_V * MG_GROUPS, 0, s, slots, pl.grid, f.nc,
+           f.nr, G, L2, zero, nzero);
+}
+
+template <int FM>
+void launch_main(const ReducePlan &pl, const int32_t *pts, int64_t n, const Frame &f, void *part,
+                 int2 *L2, unsigned *status, cudaStream_t s)
+{
+    if (pl.mode == 0)
+        launch(k_reduce_private<1024, FM>, pl.grid, 1024, pl.smem, s, pts, n, f,
+               reinterpret_cast<uint32_t *>(part), status);
+    else if (pl.mode == 2)
+        launch(k_reduce_global<FM>, sm_count() * 8, 256, 0, s, pts, n, f, L2, status);
+    else
+        launch(k_reduce_filtered<1024, FM>, pl.grid, 1024, pl.smem, s, pts, n, f, pl.shift,
+               reinterpret_cast<const uint16_t *>(part), L2, status);
+}
+
+void launch_fill(const Frame &f, int2 *L2, cudaStream_t s, unsigned long long *zero, int nzero)
+{
+    launch(k_fill_empty, std::max(1, std::min((f.nc + 255) / 256, sm_count() * 4)), 256, 0, s, L2,
+           f.nc, f.nr, zero, nzero);
+}
+
+}  // namespace
+
+cudaError_t reduce_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, const Frame &f,
                           void *part, int32_t *L, unsigned *status, cudaStream_t s,
                           unsigned long long *zero, int nzero, cudaEvent_t ev0, cudaEvent_t ev1,
                           bool prefilled)
 {
     auto mark = [&](cudaEvent_t ev) { return ev ? cudaEventRecord(ev, s) : cudaSuccess; };
-    if (pl.mode == 0) {
-        uint32_t *pp = reinterpret_cast<uint32_t *>(part);
-        mark(ev0);
-        if (pl.threads == 512)
-            launch(k_reduce_private<512>, pl.grid, 512, pl.smem, s, pts, n, p, pp, status);
-        else
-            launch(k_reduce_private<1024>, pl.grid, 1024, pl.smem, s, pts, n, p, pp, status);
-        mark(ev1);
-        return cudaGetLastError();
-    }
     int2 *L2 = reinterpret_cast<int2 *>(L);
-    const int sms = sm_count();
-    if (pl.mode == 2) {
-        if (!prefilled)
-            launch(k_fill_empty, std::max(1, std::min((p + 255) / 256, sms * 4)), 256, 0, s, L2, p, zero,
-                                                                                        nzero);
-        mark(ev0);
-        launch(k_reduce_global, sms * 8, 256, 0, s, pts, n, p, L2, status);
-        mark(ev1);
-        return cudaGetLastError();
-    }
-    uint16_t *G = reinterpret_cast<uint16_t *>(part);
-    uint16_t *slots = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(part) +
-                                                   ((((size_t)p * 2) + 255) & ~size_t(255)));
-    if (!prefilled) {
-        launch(k_filter_warm<1024>, pl.grid, 1024, pl.smem, s, pts, n, p, pl.shift, pl.grid, slots);
-        const int words = (p + 7) / 8;
-        launch(k_filter_merge, (words + MG_V - 1) / MG_V, MG_V * MG_GROUPS, 0, s, slots, pl.grid, p, G,
-                                                                             L2, zero, nzero);
-    }
+    if (!prefilled && pl.mode == 2)
+        launch_fill(f, L2, s, zero, nzero);
+    const int fm = frame_mode(f);
+    if (!prefilled && pl.mode == 1)
+        (fm == 0 ? launch_warm<0> : fm == 1 ? launch_warm<1> : launch_warm<2>)(pl, pts, n, f, part, L2,
+                                                                             s, zero, nzero);
     mark(ev0);
-    launch(k_reduce_filtered<1024>, pl.grid, 1024, pl.smem, s, pts, n, p, pl.shift, G, L2, status);
+    (fm == 0 ? launch_main<0> : fm == 1 ? launch_main<1> : launch_main<2>)(pl, pts, n, f, part, L2,
+                                                                         status, s);
     mark(ev1);
     return cudaGetLastError();
 }
 
-cudaError_t reduce_warm_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, int p,
+cudaError_t reduce_warm_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, const Frame &f,
                                void *part, int32_t *L, cudaStream_t s, unsigned long long *zero,
                                int nzero)
 {
     int2 *L2 = reinterpret_cast<int2 *>(L);
-    if (pl.mode == 2) {
-        launch(k_fill_empty, std::max(1, std::min((p + 255) / 256, sm_count() * 4)), 256, 0, s, L2, p, zero,
-                                                                                        nzero);
-    } else if (pl.mode == 1) {
-        uint16_t *G = reinterpret_cast<uint16_t *>(part);
-        uint16_t *slots = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(part) +
-                                                       ((((size_t)p * 2) + 255) & ~size_t(255)));
-        launch(k_filter_warm<1024>, pl.grid, 1024, pl.smem, s, pts, n, p, pl.shift, pl.grid, slots);
-        const int words = (p + 7) / 8;
-        launch(k_filter_merge, (words + MG_V - 1) / MG_V, MG_V * MG_GROUPS, 0, s, slots, pl.grid, p, G,
-                                                                             L2, zero, nzero);
+    if (pl.mode == 2)
+        launch_fill(f, L2, s, zero, nzero);
+    else if (pl.mode == 1) {
+        const int fm = frame_mode(f);
+        (fm == 0 ? launch_warm<0> : fm == 1 ? launch_warm<1> : launch_warm<2>)(pl, pts, n, f, part, L2,
+                                                                             s, zero, nzero);
     }
     return cudaGetLastError();
 }
 
-cudaError_t reduce_merge_launch(const void *part, int copies, int p, int32_t *L, cudaStream_t s,
-                                unsigned long long *zero, int nzero, const int32_t *Linit)
+cudaError_t reduce_merge_launch(const void *part, int copies, int nc, int nr, int32_t *L,
+                                cudaStream_t s, unsigned long long *zero, int nzero,
+                                const int32_t *Linit)
 {
-    launch(k_merge_partials, (p + 31) / 32, 1024, 0, s, reinterpret_cast<const uint32_t *>(part),
-                                                         copies, p, reinterpret_cast<int2 *>(L),
-                                                         zero, nzero,
-                                                         reinterpret_cast<const int2 *>(Linit));
+    launch(k_merge_partials, (nc + 31) / 32, 1024, 0, s, reinterpret_cast<const uint32_t *>(part),
+           copies, nc, nr, reinterpret_cast<int2 *>(L), zero, nzero,
+           reinterpret_cast<const int2 *>(Linit));
     return cudaGetLastError();
 }
 
