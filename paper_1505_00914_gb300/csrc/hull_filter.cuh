@@ -58,25 +58,31 @@ __device__ __forceinline__ void build_min_trees(const int2 *P0, short *M0, int n
 // lowest point of the right one) is tested: pairing an anchor with a direct
 // neighbour as well dropped 7 % more points but cost a third more time than
 // the final hull saved.
+// SPARSE_EXIT: the variant the batched kernel uses, where most tiles are
+// short-lived: a warp stops testing once all its points are dropped, and the
+// lowest level (blocks of two points, next to the +-2 neighbour tests) is
+// left out; the chain kernel's dense tiles are faster without the vote.
+template <bool SPARSE_EXIT = false>
 __device__ __forceinline__ bool run_keeps(const int2 *P, const short *M, int n, int i)
 {
-    if (i >= n)
-        return false;
-    const int2 q = P[i];
-    const bool h1 = i >= 1 && i + 1 < n, l2 = i >= 2, r2 = i + 2 < n;
-    const int2 nl1 = i >= 1 ? P[i - 1] : q, nr1 = i + 1 < n ? P[i + 1] : q;
-    const int2 nl2 = l2 ? P[i - 2] : q, nr2 = r2 ? P[i + 2] : q;
-    bool drop = h1 && (cross3(nl1, nr1, q) >= 0 || (r2 && cross3(nl1, nr2, q) >= 0) ||
-                       (l2 && cross3(nl2, nr1, q) >= 0));
+    const bool alive = i < n;
+    const int2 q = alive ? P[i] : make_int2(0, 0);
+    const bool h1 = alive && i >= 1 && i + 1 < n, l2 = i >= 2, r2 = i + 2 < n;
+    const int2 nl1 = alive && i >= 1 ? P[i - 1] : q, nr1 = alive && i + 1 < n ? P[i + 1] : q;
+    const int2 nl2 = alive && l2 ? P[i - 2] : q, nr2 = alive && r2 ? P[i + 2] : q;
+    bool drop = !alive || (h1 && (cross3(nl1, nr1, q) >= 0 || (r2 && cross3(nl1, nr2, q) >= 0) ||
+                                  (l2 && cross3(nl2, nr1, q) >= 0)));
     constexpr int CH = 3;  // levels per batch; levels 1..RUN_LOG-1 have siblings
 #pragma unroll
-    for (int k0 = 1; k0 < RUN_LOG; k0 += CH) {
+    for (int k0 = SPARSE_EXIT ? 2 : 1; k0 < RUN_LOG; k0 += CH) {
+        if (SPARSE_EXIT && __all_sync(0xFFFFFFFFu, drop))
+            break;
         int la[CH], ra[CH];
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
             const int k = k0 + u, node = i >> k;
-            la[u] = node >= 1 ? M[tree_off(k) + node - 1] : -1;
-            ra[u] = (node + 1) < (RUN >> k) ? M[tree_off(k) + node + 1] : -1;
+            la[u] = k < RUN_LOG && node >= 1 ? M[tree_off(k) + node - 1] : -1;
+            ra[u] = k < RUN_LOG && (node + 1) < (RUN >> k) ? M[tree_off(k) + node + 1] : -1;
         }
         int2 A[CH], B[CH];
 #pragma unroll
@@ -85,9 +91,8 @@ __device__ __forceinline__ bool run_keeps(const int2 *P, const short *M, int n, 
             B[u] = ra[u] >= 0 ? P[ra[u]] : q;
         }
 #pragma unroll
-        for (int u = 0; u < CH; ++u) {
+        for (int u = 0; u < CH; ++u)
             drop |= la[u] >= 0 && ra[u] >= 0 && cross3(A[u], B[u], q) >= 0;
-        }
     }
     return !drop;
 }
