@@ -4,8 +4,10 @@
 Default workload (the configuration the headline metric is quoted on):
 p = 65536, n = 2^26 int32 points per instance, three seeded distributions
 (uniform square, inscribed disc, Gaussian sigma = p/8) run separately.  One
-step = one ch_convex_hull call per distribution (3 * 2^26 points).  Inputs
-(537 MB each) are resident in HBM and larger than L2, so no flush is needed.
+step = one ch_convex_hull call per distribution (3 * 2^26 points), each
+instance on its own CUDA stream and workspace (independent problems).
+Inputs (537 MB each) are resident in HBM and larger than L2, so no flush is
+needed.
 
 Prints ONE JSON line (rank 0).  `value` is device-timed whole-job throughput in
 Gpoints/s; `e2e` is the same metric through ch_convex_hull_host (host buffers,
@@ -13,8 +15,9 @@ copies inside the timed region); `roofline` is for the dominant kernel (the
 reduction), timed per launch with CUDA events recorded on its stream;
 `cpu_baseline` is the CPU oracle on the host cores.  `value` comes from a
 timed region without instrumentation; the roofline's launch times come from
-a second timed region of the same steps with events around each reduction
-launch (its step time is reported as roofline.ms_per_step_while_timed).
+a second timed region of the same steps, instances one after another on one
+stream, with events around each reduction launch (its step time is reported
+as roofline.ms_per_step_while_timed).
 
 --impl reference times the CPU oracle itself on the same workload (rank 0 only).
 
@@ -193,6 +196,7 @@ def workload_config(workload):
     p, n, dists = WORKLOADS[workload]
     return {"workload": workload, "p": p, "n_per_instance": n, "distributions": list(dists),
             "instances_per_step": len(dists),
+            "concurrency": "each instance on its own CUDA stream and workspace",
             "l2": "inputs 8n bytes per instance, larger than L2; no flush"}
 
 
@@ -278,14 +282,29 @@ def run_ours(args):
     p, n, inputs = gen_inputs(args.workload, rank)
     dev_in = [torch.from_numpy(P).cuda() for _, P in inputs]
     nws = ch.ch_convex_hull_workspace_size(n, p)
-    ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+    # the instances of a step are independent problems: each has its own
+    # stream and workspace, so that one instance's latency-bound chain and
+    # hull kernels overlap the others' streaming
+    wss = [torch.empty(nws, dtype=torch.uint8, device="cuda") for _ in inputs]
     hulls = [torch.empty((2 * p, 2), dtype=torch.int32, device="cuda") for _ in inputs]
     hcs = [torch.empty(1, dtype=torch.int32, device="cuda") for _ in inputs]
     stream = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream() for _ in inputs]
 
-    def step():
-        for d, h, c in zip(dev_in, hulls, hcs):
-            ch.ch_convex_hull(d, p, hull=h, hull_count=c, workspace=ws, stream=stream)
+    def step(concurrent=True):
+        if not concurrent:  # one after another on the main stream
+            for d, h, c, w in zip(dev_in, hulls, hcs, wss):
+                ch.ch_convex_hull(d, p, hull=h, hull_count=c, workspace=w, stream=stream)
+            return
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        for d, h, c, w, st in zip(dev_in, hulls, hcs, wss, streams):
+            st.wait_event(fork)
+            ch.ch_convex_hull(d, p, hull=h, hull_count=c, workspace=w, stream=st)
+        for st in streams:
+            join = torch.cuda.Event()
+            join.record(st)
+            stream.wait_event(join)
 
     for _ in range(args.warmup):
         step()
@@ -294,11 +313,11 @@ def run_ours(args):
     if rc != ch.CH_OK:
         raise RuntimeError(f"warm-up failed: {ch.strerror(rc)}")
 
-    # value: the timed steps as a user runs them; then the same steps again
-    # with CUDA events recorded around every launch of the reduction kernel
-    # on its stream (the roofline); the events sit between dependent
-    # launches, so that second region is a little slower and is reported
-    # beside the first
+    # value: the timed steps as a user runs them (instances concurrent); then
+    # the same steps again with the instances one after another on one stream
+    # and CUDA events recorded around every launch of the reduction kernel
+    # (the roofline: each launch alone on the GPU); that second region's step
+    # time is reported beside the first
     nl = args.steps * len(inputs)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nl)]
     for a, b in evs:
@@ -310,8 +329,10 @@ def run_ours(args):
     sampler.start()
     time.sleep(0.3)
     ms = _timed(torch, dist, world, step, args.steps, stream)
+    for _ in range(2):
+        step(False)
     ch.ch_trace_set(evs)
-    ms_traced = _timed(torch, dist, world, step, args.steps, stream)
+    ms_traced = _timed(torch, dist, world, lambda: step(False), args.steps, stream)
     ch.ch_trace_set([])
     clocks = sampler.stop()
     rc = ch.ch_sync_status()
@@ -328,7 +349,7 @@ def run_ours(args):
     e2e_steps = max(1, min(args.steps, 5))
     host_in = [torch.from_numpy(P).pin_memory() for _, P in inputs]
     nws_h = ch.ch_convex_hull_host_workspace_size(n, p)
-    del ws
+    del wss
     ws_h = torch.empty(nws_h, dtype=torch.uint8, device="cuda")
     hh = torch.empty((2 * p, 2), dtype=torch.int32).pin_memory()
     hsz = []
