@@ -5,7 +5,8 @@ benchmark's CPU-baseline / reference leg may import this package.  It shares no
 code with the CUDA library and never imports it.
 
 ``oracle.c`` holds the integer part (Algorithm 1, the Lemma 1 chains and
-polyline, Andrew's monotone-chain hull, an O(m^3) brute-force hull, the
+polyline, Andrew's monotone-chain hull, Melkman's hull of a simple polyline,
+Steps 1-2 for points anywhere in int32, an O(m^3) brute-force hull, the
 culling-polygon start array).  ``learned.py`` holds the floating-point part of
 the learned culling (histogram, MLP forward/backward in float64, extreme
 points).  Every function cites the passage of the paper it follows; arrays are
@@ -56,6 +57,8 @@ def _load():
                 "oracle_chain": (i64, [P, i32, P, P]),
                 "oracle_mask": (None, [P, i32, P]),
                 "oracle_polyline": (i64, [P, i32, P]),
+                "oracle_melkman": (i64, [P, i64, P]),
+                "oracle_hull_box": (i64, [P, i64, P]),
                 "oracle_hull_points": (i64, [P, i64, P]),
                 "oracle_hull_chain": (i64, [P, i32, P]),
                 "oracle_hull_brute": (i64, [P, i64, P]),
@@ -159,6 +162,35 @@ def hull_chain(L) -> np.ndarray:
     p = L.shape[0]
     out = np.empty((2 * p + 2, 2), dtype=np.int32)
     h = _load().oracle_hull_chain(_ptr(L), p, _ptr(out))
+    return out[:h].copy()
+
+
+def melkman(poly) -> np.ndarray:
+    """Melkman's on-line hull of a simple polyline (the hull algorithm of
+    Section 3, Fig. 10), strict vertices CCW from the lexicographic minimum.
+    The vertices must be distinct and the polyline simple; the Lemma 1
+    polyline is."""
+    poly = _pts(poly)
+    m = poly.shape[0]
+    out = np.empty((max(m, 1) + 1, 2), dtype=np.int32)
+    h = _load().oracle_melkman(_ptr(poly), m, _ptr(out))
+    return out[:h].copy()
+
+
+def hull_box(pts) -> np.ndarray:
+    """Steps 1-2 of the general procedure (Section 2): bounding box,
+    translation into it, Algorithm 1 with the columns along the shorter side,
+    the hull of the reduced set, mapped back.  Points anywhere in int32."""
+    pts = _pts(pts)
+    n = pts.shape[0]
+    if n == 0:
+        return np.empty((0, 2), dtype=np.int32)
+    side = int(min(int(pts[:, 0].max()) - int(pts[:, 0].min()),
+                   int(pts[:, 1].max()) - int(pts[:, 1].min()))) + 1
+    out = np.empty((2 * side + 2, 2), dtype=np.int32)
+    h = _load().oracle_hull_box(_ptr(pts), n, _ptr(out))
+    if h < 0:
+        raise ValueError("oracle_hull_box: a side of the box exceeds 2^30")
     return out[:h].copy()
 
 

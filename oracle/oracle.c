@@ -548,3 +548,173 @@ int oracle_label_batch(const int32_t *pts, const int64_t *off, const int32_t *ps
     free(Hb);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Melkman's on-line hull of a simple polyline, the hull algorithm the     */
+/* paper applies to its reduced set in Section 3 (Fig. 10): a deque holds  */
+/* the hull of the vertices seen so far, counter-clockwise from its bottom */
+/* to its top, with the last vertex at both ends.  A new vertex u that is  */
+/* on or inside the hull (left of or on both edges at the deque's ends) is */
+/* skipped; otherwise vertices are popped from the top while u is not      */
+/* strictly left of the top edge and from the bottom while the bottom edge */
+/* is not strictly left-turning into u, and u is pushed at both ends.      */
+/* Popping on "not strictly left" and skipping on "left or on" drop        */
+/* collinear points, so the hull lists strict vertices.  The input must be */
+/* a simple polyline with distinct vertices, as the Lemma 1 polyline is.   */
+/* A collinear prefix becomes the segment between its lexicographic        */
+/* extremes before the first vertex off its line starts the deque.         */
+/* Output as every hull here: counter-clockwise from the lexicographic     */
+/* minimum.                                                                */
+/* ------------------------------------------------------------------------ */
+static void put_rotated(const int32_t *ring, int64_t h, int32_t *out)
+{
+    int64_t s = 0;
+    for (int64_t i = 1; i < h; ++i)
+        if (cmp_xy(&ring[2 * i], &ring[2 * s]) < 0)
+            s = i;
+    for (int64_t i = 0; i < h; ++i) {
+        out[2 * i] = ring[2 * ((s + i) % h)];
+        out[2 * i + 1] = ring[2 * ((s + i) % h) + 1];
+    }
+}
+
+int64_t oracle_melkman(const int32_t *v, int64_t m, int32_t *out)
+{
+    if (m <= 0)
+        return 0;
+    /* the collinear prefix v[0..k-1] and its extremes a (min), b (max) */
+    int64_t a = 0, b = 0, k = 1;
+    for (; k < m; ++k) {
+        if (k >= 2 && cross3(&v[2 * a], &v[2 * b], &v[2 * k]) != 0)
+            break;
+        if (cmp_xy(&v[2 * k], &v[2 * a]) < 0)
+            a = k;
+        if (cmp_xy(&v[2 * k], &v[2 * b]) > 0)
+            b = k;
+    }
+    if (k == m) { /* every vertex on one line (or a single vertex) */
+        out[0] = v[2 * a];
+        out[1] = v[2 * a + 1];
+        if (a == b)
+            return 1;
+        out[2] = v[2 * b];
+        out[3] = v[2 * b + 1];
+        return 2;
+    }
+    /* deque as a plain array indexed bot..top, room for m pushes each way */
+    int64_t cap = 2 * m + 8, mid = m + 4;
+    int32_t *D = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)cap);
+#define DQ(i) (&D[2 * (i)])
+#define SETDQ(i, p)              \
+    do {                         \
+        D[2 * (i)] = (p)[0];     \
+        D[2 * (i) + 1] = (p)[1]; \
+    } while (0)
+    int64_t bot = mid, top = mid + 3;
+    const int32_t *vk = &v[2 * k];
+    SETDQ(bot, vk);
+    SETDQ(top, vk);
+    if (cross3(&v[2 * a], &v[2 * b], vk) > 0) {
+        SETDQ(bot + 1, &v[2 * a]);
+        SETDQ(bot + 2, &v[2 * b]);
+    } else {
+        SETDQ(bot + 1, &v[2 * b]);
+        SETDQ(bot + 2, &v[2 * a]);
+    }
+    for (int64_t i = k + 1; i < m; ++i) {
+        const int32_t *u = &v[2 * i];
+        if (cross3(DQ(top - 1), DQ(top), u) >= 0 && cross3(DQ(bot), DQ(bot + 1), u) >= 0)
+            continue; /* on or inside the current hull */
+        while (top - bot > 1 && cross3(DQ(top - 1), DQ(top), u) <= 0)
+            --top;
+        ++top;
+        SETDQ(top, u);
+        while (top - bot > 1 && cross3(u, DQ(bot), DQ(bot + 1)) <= 0)
+            ++bot;
+        --bot;
+        SETDQ(bot, u);
+    }
+#undef DQ
+#undef SETDQ
+    /* D[bot..top-1] is the hull, counter-clockwise */
+    int64_t h = top - bot;
+    put_rotated(&D[2 * bot], h, out);
+    free(D);
+    return h;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Steps 1 and 2 of the paper's general procedure (Section 2,              */
+/* "Implementation of the proposed heuristic") for int32 points anywhere:  */
+/* the bounding box [xmin, xmax] x [ymin, ymax]; the translation           */
+/* x' = x - xmin + 1, y' = y - ymin + 1 into a p x q box (the printed     */
+/* formula is garbled; this is the reading that maps the box onto          */
+/* [1, p] x [1, q]); Algorithm 1 with the columns along the shorter side   */
+/* (when q < p the roles of x and y swap, the sweep along min(p, q));     */
+/* the hull of the reduced set on its Lemma 1 polyline; the vertices       */
+/* mapped back.  Swapping x and y reverses the orientation, so the list is */
+/* then reversed before it is rotated to start at the lexicographic min.   */
+/* Sides above 2^30 are rejected (ORC_ERR_ARG), as for p.                  */
+/* ------------------------------------------------------------------------ */
+int64_t oracle_hull_box(const int32_t *pts, int64_t n, int32_t *out)
+{
+    if (n <= 0)
+        return 0;
+    int64_t xmin = pts[0], xmax = pts[0], ymin = pts[1], ymax = pts[1];
+    for (int64_t i = 1; i < n; ++i) {
+        if (pts[2 * i] < xmin) xmin = pts[2 * i];
+        if (pts[2 * i] > xmax) xmax = pts[2 * i];
+        if (pts[2 * i + 1] < ymin) ymin = pts[2 * i + 1];
+        if (pts[2 * i + 1] > ymax) ymax = pts[2 * i + 1];
+    }
+    const int64_t p = xmax - xmin + 1, q = ymax - ymin + 1;
+    if (p > (1 << 30) || q > (1 << 30))
+        return ORC_ERR_ARG;
+    const int tr = q < p;
+    const int64_t nc = tr ? q : p, nr = tr ? p : q;
+    /* Algorithm 1 on the translated (and, if tr, swapped) points; the     */
+    /* empty entry is (nr + 1, -1), the sentinel of the longer side        */
+    int32_t *L = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)nc);
+    for (int64_t i = 0; i < nc; ++i) {
+        L[2 * i] = (int32_t)(nr + 1);
+        L[2 * i + 1] = -1;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t x = pts[2 * i] - xmin + 1, y = pts[2 * i + 1] - ymin + 1;
+        const int64_t c = tr ? y : x, r = tr ? x : y;
+        if (r < L[2 * (c - 1)]) L[2 * (c - 1)] = (int32_t)r;
+        if (r > L[2 * (c - 1) + 1]) L[2 * (c - 1) + 1] = (int32_t)r;
+    }
+    /* Lemma 1 polyline (a column is valid when ly <= hy), then Andrew */
+    int32_t *poly = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(2 * nc + 1));
+    int64_t s = 0;
+    for (int64_t i = 0; i < nc; ++i) {
+        if (L[2 * i] > L[2 * i + 1])
+            continue;
+        poly[2 * s] = (int32_t)(i + 1);
+        poly[2 * s + 1] = L[2 * i];
+        ++s;
+        if (L[2 * i + 1] != L[2 * i]) {
+            poly[2 * s] = (int32_t)(i + 1);
+            poly[2 * s + 1] = L[2 * i + 1];
+            ++s;
+        }
+    }
+    int32_t *hf = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(2 * nc + 2));
+    const int64_t h = andrew_sorted(poly, s, hf);
+    /* back to the input's coordinates (reversed when swapped) */
+    int32_t *ring = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(h + 1));
+    for (int64_t i = 0; i < h; ++i) {
+        const int64_t j = tr ? h - 1 - i : i;
+        const int64_t c = hf[2 * j], r = hf[2 * j + 1];
+        const int64_t x = (tr ? r : c) + xmin - 1, y = (tr ? c : r) + ymin - 1;
+        ring[2 * i] = (int32_t)x;
+        ring[2 * i + 1] = (int32_t)y;
+    }
+    put_rotated(ring, h, out);
+    free(ring);
+    free(hf);
+    free(poly);
+    free(L);
+    return h;
+}
