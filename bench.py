@@ -22,6 +22,16 @@ as roofline.ms_per_step_while_timed).
 --impl reference times the CPU oracle itself on the same workload (rank 0 only).
 
 Other workloads (--workload):
+  box       Steps 1-2 for int32 points anywhere: three instances of 2^26
+            points (uniform in a 65536 x 65536 box at (-1.5e9, 7e8), disc in a
+            120000 x 40000 box at (1e9, -2e9), Gaussian in a 30000 x 90000
+            box at (-123456789, 987654321)); a step is ch_bbox on each, one
+            read of the three boxes, then ch_convex_hull_box on each (columns
+            along the shorter side), each instance on its own stream.
+  melkman   the paper's Melkman experiment (Section 3, Fig. 10) on the
+            projected-shells stand-in (p = 4096, 10^7 points): Algorithm 1,
+            the Lemma 1 polyline and Melkman's hull (ch_convex_hull_melkman)
+            against the plain path on the same input, hulls checked equal.
   learned   p = 65536, n = 2^27 per instance, one instance each of uniform,
             disc, Gaussian and thin annulus (r in [0.45p, 0.5p]); the path
             with the trained culling network (ch_hull_learned) against the
@@ -72,8 +82,7 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_OF_FORM = ("k_reduce_private", "k_reduce_filtered", "k_reduce_global",
-                  "k_reduce_filtered_bulk")
+KERNEL_OF_FORM = ("k_reduce_private", "k_reduce_filtered", "k_reduce_global")
 
 
 def _kernel_sha(src_path, name):
@@ -189,6 +198,18 @@ def workload_config(workload):
         return {"workload": "learned", "p": p, "n_per_instance": n, "distributions": list(dists),
                 "instances_per_step": len(dists),
                 "l2": "inputs 8n bytes per instance, larger than L2; no flush"}
+    if workload == "box":
+        return {"workload": "box", "n_per_instance": BOX_N,
+                "boxes": [{"distribution": d, "width": sx, "height": sy, "x0": x0, "y0": y0}
+                          for d, sx, sy, x0, y0 in BOX],
+                "instances_per_step": len(BOX),
+                "concurrency": "each instance on its own CUDA stream and workspace",
+                "l2": "inputs 8n bytes per instance, larger than L2; no flush"}
+    if workload == "melkman":
+        p, n, dists = WORKLOADS[MELKMAN]
+        return {"workload": "melkman", "p": p, "n_per_instance": n, "distributions": list(dists),
+                "instances_per_step": 1,
+                "l2": "80 MB of points, below L2 (129 MB): an L2 flush precedes every step"}
     if workload == "batched":
         return {"workload": "batched", "sets": BATCH_SETS, "ps": [256, 1024, 4096, 16384],
                 "n_range": [100, 1_000_000], "distributions": ["uniform", "disc", "gaussian"],
@@ -209,22 +230,37 @@ def _reference_units(workload):
     if workload == "batched":
         pts, off, ps, _ = synth.batched(BATCH_SETS, seed=4)
         return [(int(ps[s]), f"set{s}", pts[off[s]:off[s + 1]]) for s in range(len(ps))]
-    p, n, inputs = gen_inputs(workload, 0)
+    if workload == "box":
+        return [(None, d, P) for d, P in box_inputs(0)]
+    p, n, inputs = gen_inputs(MELKMAN if workload == "melkman" else workload, 0)
     return [(p, d, P) for d, P in inputs]
+
+
+def oracle_solver(workload):
+    """The oracle's form of one problem of the workload: Algorithm 1 + the
+    hull of the reduced set; Steps 1-2 first for `box`; Melkman's hull of the
+    Lemma 1 polyline for `melkman`."""
+    import oracle
+    if workload == "box":
+        return lambda p, P: oracle.hull_box(P)
+    if workload == "melkman":
+        return lambda p, P: oracle.melkman(oracle.polyline(oracle.reduce(P, p)))
+    return lambda p, P: oracle.hull_chain(oracle.reduce(P, p))
 
 
 def run_reference(args):
     """The CPU oracle as it stands (Algorithm 1 + the hull of the reduced set,
     single thread) on the same workload.  A step is a bounded sample of it:
     the whole step for the plain workloads, one instance per step (in turn)
-    for `learned`, the next sets up to 1e8 points for `batched`."""
+    for `learned` and `box`, the next sets up to 1e8 points for `batched`."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     oracle.build()
     units = _reference_units(args.workload)
-    per_step = {"learned": 1}.get(args.workload)
+    per_step = {"learned": 1, "box": 1}.get(args.workload)
+    solve = oracle_solver(args.workload)
     cursor = [0]
 
     def step():
@@ -233,13 +269,13 @@ def run_reference(args):
             while done < 100_000_000:
                 p, _, P = units[cursor[0] % len(units)]
                 cursor[0] += 1
-                oracle.hull_chain(oracle.reduce(P, p))
+                solve(p, P)
                 done += P.shape[0]
             return done
         todo = units if per_step is None else [units[cursor[0] % len(units)]]
         cursor[0] += 1
         for p, _, P in todo:
-            oracle.hull_chain(oracle.reduce(P, p))
+            solve(p, P)
             done += P.shape[0]
         return done
 
@@ -250,6 +286,7 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     v = pts / dt / 1e9
     sample = {"learned": "one n = 2^27 instance per step, in turn",
+              "box": "one n = 2^26 instance per step, in turn",
               "batched": "consecutive sets up to 1e8 points per step"}.get(
                   args.workload, f"the whole step ({len(units)} instances)")
     line = {
@@ -415,6 +452,18 @@ def run_ours(args):
 
 
 LEARNED = (65536, 1 << 27, ("uniform", "disc", "gaussian", "annulus"))
+# Steps 1-2: (distribution, box width, box height, x0, y0) per instance
+BOX_N = 1 << 26
+BOX = (("uniform", 65536, 65536, -1_500_000_000, 700_000_000),
+       ("disc", 120_000, 40_000, 1_000_000_000, -2_000_000_000),
+       ("gaussian", 30_000, 90_000, -123_456_789, 987_654_321))
+MELKMAN = "projected_shells"
+
+
+def box_inputs(rank):
+    from paper_1505_00914_gb300 import synth
+    return [(d, synth.boxed(d, BOX_N, sx, sy, x0, y0, seed=31 + 1000 * rank + i))
+            for i, (d, sx, sy, x0, y0) in enumerate(BOX)]
 WEIGHTS = os.path.join(ROOT, "paper_1505_00914_gb300", "weights", "cull_mlp_k16.npz")
 BATCH_SETS = 10_000
 
@@ -747,13 +796,283 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+def run_box(args):
+    """Steps 1-2 (bounding box, translation fused into Algorithm 1, columns
+    along the shorter side) on int32 points anywhere."""
+    torch, dist, world, rank = _setup_dist()
+    from paper_1505_00914_gb300 import ch
+    ch.lib()
+    inputs = box_inputs(rank)
+    n = BOX_N
+    dev_in = [torch.from_numpy(P).cuda() for _, P in inputs]
+    stream = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream() for _ in inputs]
+    boxes_d = [torch.empty(4, dtype=torch.int32, device="cuda") for _ in inputs]
+    boxes_h = torch.empty((len(inputs), 4), dtype=torch.int32).pin_memory()
+    bws = [torch.empty(max(ch._size(ch.lib().ch_bbox_workspace_size), 1), dtype=torch.uint8,
+                       device="cuda") for _ in inputs]
+    # the boxes are known from the data; size the workspaces once
+    truth = [np.array([P[:, 0].min(), P[:, 0].max(), P[:, 1].min(), P[:, 1].max()], np.int32)
+             for _, P in inputs]
+    side = [int(min(b[1] - b[0], b[3] - b[2])) + 1 for b in truth]
+    wss = [torch.empty(ch.ch_convex_hull_box_workspace_size(n, b), dtype=torch.uint8, device="cuda")
+           for b in truth]
+    hulls = [torch.empty((2 * s + 2, 2), dtype=torch.int32, device="cuda") for s in side]
+    hcs = [torch.empty(1, dtype=torch.int32, device="cuda") for _ in inputs]
+
+    def step(concurrent=True):
+        sts = streams if concurrent else [stream] * len(inputs)
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        for i, st in enumerate(sts):
+            st.wait_event(fork)
+            ch.ch_bbox(dev_in[i], box=boxes_d[i], workspace=bws[i], stream=st)
+            with torch.cuda.stream(st):
+                boxes_h[i].copy_(boxes_d[i], non_blocking=True)
+        for st in set(sts):
+            st.synchronize()  # the one host read of the boxes
+        for i, st in enumerate(sts):
+            ch.ch_convex_hull_box(dev_in[i], boxes_h[i].numpy(), hull=hulls[i], hull_count=hcs[i],
+                                  workspace=wss[i], stream=st)
+        for st in set(sts):
+            if st is not stream:
+                join = torch.cuda.Event()
+                join.record(st)
+                stream.wait_event(join)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    rc = ch.ch_sync_status()
+    if rc != ch.CH_OK:
+        raise RuntimeError(f"warm-up failed: {ch.strerror(rc)}")
+    for i in range(len(inputs)):
+        if not np.array_equal(boxes_h[i].numpy(), truth[i]):
+            raise RuntimeError("bounding box mismatch")
+    nl = args.steps * len(inputs)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nl)]
+    for a, b in evs:
+        a.record(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    ms = _timed(torch, dist, world, step, args.steps, stream)
+    for _ in range(2):
+        step(False)
+    ch.ch_trace_set(evs)
+    ms_traced = _timed(torch, dist, world, lambda: step(False), args.steps, stream)
+    ch.ch_trace_set([])
+    clocks = sampler.stop()
+    rc = ch.ch_sync_status()
+    if rc != ch.CH_OK:
+        raise RuntimeError(f"timed run failed: {ch.strerror(rc)}")
+    # launches follow the instances in order: the reduction of instance i
+    # is evs[k] with k % 3 == i
+    red = [a.elapsed_time(b) for a, b in evs]
+    pts_step = n * len(inputs)
+    value = world * pts_step * args.steps / (ms / 1e3) / 1e9
+    hv = [int(c.item()) for c in hcs]
+
+    # e2e: pinned host points -> device, the same step, hulls back to the host
+    e2e_steps = max(1, min(args.steps, 3))
+    host_in = [torch.from_numpy(P).pin_memory() for _, P in inputs]
+    hh = [torch.empty(tuple(h.shape), dtype=torch.int32).pin_memory() for h in hulls]
+    d2h = 0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for i, hp in enumerate(host_in):
+            dev_in[i].copy_(hp, non_blocking=True)
+        step()
+        torch.cuda.synchronize()
+        for i in range(len(inputs)):
+            k = int(hcs[i].item())
+            hh[i][:k].copy_(hulls[i][:k])
+            d2h += 4 + 8 * k
+    e2e_s = _max_over_ranks(torch, dist, world, time.perf_counter() - w0)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = _peaks()
+    # dominant kernel: the main reduction of the largest frame (instance 0,
+    # 65536 columns); per launch it reads the points and writes L
+    red0 = [red[k] for k in range(0, len(red), len(inputs))]
+    red0_avg = sum(red0) / len(red0)
+    kernel_bytes = 8 * n + 8 * side[0]
+    achieved = kernel_bytes / (red0_avg / 1e3) / 1e9
+    cpu_v, cpu_dt, cpu_passes = _cpu_rate(oracle_solver("box"), [(None, P) for _, P in inputs[:1]],
+                                          args.cpu_budget)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gpoints/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": workload_config("box"),
+        "hbm_frac_step": (pts_step * 16 / (ms / args.steps / 1e3) / 1e9) / peak,
+        "box": {"columns": side, "transposed": [bool(b[3] - b[2] < b[1] - b[0]) for b in truth],
+                "reduction_ms_per_instance": [sum(red[i::len(inputs)]) / args.steps
+                                              for i in range(len(inputs))],
+                "hull_vertices": hv,
+                "note": "two passes over the points per instance (bounding box, then the "
+                        "reduction) and one 16-byte host read of the boxes per step"},
+        "roofline": {"bound": "hbm", "kernel": KERNEL_OF_FORM[ch.ch_plan_info(n, side[0])[0]],
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "algorithmic_bytes_per_launch": kernel_bytes,
+                     "avg_launch_ms": red0_avg, "ms_per_step_while_timed": ms_traced / args.steps,
+                     "traffic": None},
+        "e2e": {"value": world * pts_step * e2e_steps / e2e_s / 1e9, "unit": "Gpoints/s",
+                "h2d_bytes_per_step": pts_step * 8, "d2h_bytes_per_step": d2h // e2e_steps,
+                "steps": e2e_steps},
+        "cpu_baseline": {"value": cpu_v, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{cpu_passes} pass(es) over the uniform instance "
+                                   f"({cpu_dt:.1f} s, single thread, Steps 1-2 + Algorithm 1 "
+                                   f"+ hull)"},
+        "gpu_launches": args.steps * len(inputs) * (2 + ch.ch_plan_info(n, side[0])[1] + 1),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _cpu_rate(solve, problems, budget_s):
+    """Points per second of the oracle over (p, points) problems, repeated
+    until about budget_s elapsed."""
+    done, passes, t0 = 0, 0, time.perf_counter()
+    while True:
+        for p, P in problems:
+            solve(p, P)
+            done += P.shape[0]
+        passes += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt / 1e9, dt, passes
+
+
+def run_melkman(args):
+    """Algorithm 1 -> Lemma 1 polyline -> Melkman's hull, against the plain
+    path, on the projected-shells stand-in for the paper's scans."""
+    torch, dist, world, rank = _setup_dist()
+    from paper_1505_00914_gb300 import ch
+    ch.lib()
+    p, n, inputs = gen_inputs(MELKMAN, rank)
+    P = inputs[0][1]
+    d = torch.from_numpy(P).cuda()
+    stream = torch.cuda.current_stream()
+    ws_m = torch.empty(ch.ch_convex_hull_melkman_workspace_size(n, p), dtype=torch.uint8, device="cuda")
+    ws_p = torch.empty(ch.ch_convex_hull_workspace_size(n, p), dtype=torch.uint8, device="cuda")
+    poly = torch.empty((2 * p, 2), dtype=torch.int32, device="cuda")
+    pc = torch.empty(1, dtype=torch.int32, device="cuda")
+    hm, hcm = torch.empty((2 * p, 2), dtype=torch.int32, device="cuda"), torch.empty(1, dtype=torch.int32, device="cuda")
+    hp, hcp = torch.empty((2 * p, 2), dtype=torch.int32, device="cuda"), torch.empty(1, dtype=torch.int32, device="cuda")
+    # the input (80 MB) fits in L2: each step starts after a 256 MB write
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(arm):
+        flush.zero_()
+        if arm == "melkman":
+            ch.ch_convex_hull_melkman(d, p, poly=poly, poly_count=pc, hull=hm, hull_count=hcm,
+                                      workspace=ws_m, stream=stream)
+        else:
+            ch.ch_convex_hull(d, p, hull=hp, hull_count=hcp, workspace=ws_p, stream=stream)
+
+    for arm in ("melkman", "plain"):
+        for _ in range(args.warmup):
+            step(arm)
+    torch.cuda.synchronize()
+    rc = ch.ch_sync_status()
+    if rc != ch.CH_OK:
+        raise RuntimeError(f"warm-up failed: {ch.strerror(rc)}")
+    same = bool(torch.equal(hm[: int(hcm.item())].cpu(), hp[: int(hcp.item())].cpu()))
+    fl = _timed(torch, dist, world, lambda: flush.zero_(), args.steps, stream)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for a, b in evs:
+        a.record(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    ms = {arm: _timed(torch, dist, world, lambda arm=arm: step(arm), args.steps, stream) - fl
+          for arm in ("melkman", "plain")}
+    ch.ch_trace_set(evs)
+    ms_traced = _timed(torch, dist, world, lambda: step("melkman"), args.steps, stream) - fl
+    ch.ch_trace_set([])
+    clocks = sampler.stop()
+    rc = ch.ch_sync_status()
+    if rc != ch.CH_OK:
+        raise RuntimeError(f"timed run failed: {ch.strerror(rc)}")
+    red_avg = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+    rate = {arm: world * n * args.steps / (t / 1e3) / 1e9 for arm, t in ms.items()}
+
+    e2e_steps = max(1, min(args.steps, 5))
+    host_in = torch.from_numpy(P).pin_memory()
+    hh = torch.empty((2 * p, 2), dtype=torch.int32).pin_memory()
+    d2h = 0
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        d.copy_(host_in, non_blocking=True)
+        ch.ch_convex_hull_melkman(d, p, poly=poly, poly_count=pc, hull=hm, hull_count=hcm,
+                                  workspace=ws_m, stream=stream)
+        k = int(hcm.item())
+        hh[:k].copy_(hm[:k])
+        d2h += 4 + 8 * k
+    e2e_s = _max_over_ranks(torch, dist, world, time.perf_counter() - w0)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = _peaks()
+    kname = KERNEL_OF_FORM[ch.ch_plan_info(n, p)[0]]
+    kernel_bytes = 8 * n + 8 * p
+    achieved = kernel_bytes / (red_avg / 1e3) / 1e9
+    cpu_v, cpu_dt, cpu_passes = _cpu_rate(oracle_solver("melkman"), [(p, P)], args.cpu_budget)
+    nk = ch.ch_plan_info(n, p)[1] - 2 + 2  # reduce kernels + polyline + Melkman
+    line = {
+        "metric": METRIC, "value": rate["melkman"], "unit": "Gpoints/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms["melkman"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": workload_config("melkman"),
+        "melkman": {"plain_gpoints_s": rate["plain"],
+                    "ms_per_step": {a: t / args.steps for a, t in ms.items()},
+                    "reduction_ms": red_avg,
+                    "after_reduction_ms": ms_traced / args.steps - red_avg,
+                    "polyline_vertices": int(pc.item()), "hull_vertices": int(hcm.item()),
+                    "hulls_identical": same,
+                    "l2_flush_ms_subtracted": fl / args.steps},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "algorithmic_bytes_per_launch": kernel_bytes, "avg_launch_ms": red_avg,
+                     "ms_per_step_while_timed": ms_traced / args.steps, "traffic": None},
+        "e2e": {"value": world * n * e2e_steps / e2e_s / 1e9, "unit": "Gpoints/s",
+                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": d2h // e2e_steps,
+                "steps": e2e_steps},
+        "cpu_baseline": {"value": cpu_v, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{cpu_passes} pass(es) over the instance ({cpu_dt:.1f} s, "
+                                   f"single thread, Algorithm 1 + polyline + Melkman)"},
+        "gpu_launches": args.steps * nk,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["learned", "batched"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["learned", "batched", "box",
+                                                                "melkman"],
                     default="plain_at_scale")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
@@ -765,6 +1084,10 @@ def main():
         run_learned(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "box":
+        run_box(args)
+    elif args.workload == "melkman":
+        run_melkman(args)
     else:
         run_ours(args)
 

@@ -164,6 +164,47 @@ int ch_convex_hull_host(const int32_t *host_pts, int64_t n, int32_t p,
                         void *workspace, size_t ws_bytes, ch_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
+/* Lemma 1's polyline and Melkman's hull of it (Section 2.1; Section 3,    */
+/* Fig. 10: the reduced set is a simple polyline, so Melkman's linear      */
+/* algorithm for simple polylines applies without a sort).                 */
+/* ---------------------------------------------------------------------- */
+
+int ch_polyline_workspace_size(int32_t p, size_t *bytes);
+
+/* From L (int32[p][2], as written by ch_reduce): for each valid column in
+ * increasing x, the vertex (x, ly) and then (x, hy) when hy != ly, written to
+ * poly (capacity 2p pairs); *count (device int32) = the number of vertices.
+ * Joining consecutive vertices gives the simple chain of Lemma 1. */
+int ch_polyline(const int32_t *L, int32_t p, int32_t *poly, int32_t *count,
+                void *workspace, size_t ws_bytes, ch_stream_t stream);
+
+/* Bytes of the deque ch_hull_melkman keeps in global memory: 0 (workspace
+ * may be NULL) unless the largest convex lattice polygon in [1,p]^2 has more
+ * than 16382 vertices (p above about 2^17). */
+int ch_hull_melkman_workspace_size(int32_t p, size_t *bytes);
+
+/* Melkman's algorithm on the polyline poly[0 .. *count) (count: DEVICE
+ * int32), which must be simple with distinct vertices in [1,p]^2 - the Lemma 1
+ * polyline is.  Writes the strict hull vertices counter-clockwise from the
+ * lexicographic minimum to hull (capacity min(2p, *count) pairs) and their
+ * number to *hull_count (device int32).  A vertex outside [1,p]^2 records
+ * CH_ERR_RANGE (hull_count 0).  For a polyline that is not simple the result
+ * is unspecified, but nothing is written beyond min(2p, *count) pairs (a
+ * longer vertex list records CH_ERR_CAPACITY instead).  One warp: the
+ * algorithm is sequential. */
+int ch_hull_melkman(const int32_t *poly, const int32_t *count, int32_t p, int32_t *hull,
+                    int32_t *hull_count, void *workspace, size_t ws_bytes, ch_stream_t stream);
+
+int ch_convex_hull_melkman_workspace_size(int64_t n, int32_t p, size_t *bytes);
+
+/* ch_reduce, ch_polyline and ch_hull_melkman in one call; L, poly and
+ * poly_count may each be NULL (the workspace holds them).  Same hull as
+ * ch_convex_hull. */
+int ch_convex_hull_melkman(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t *poly,
+                           int32_t *poly_count, int32_t *hull, int32_t *hull_count,
+                           void *workspace, size_t ws_bytes, ch_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
 /* Many independent sets in one persistent launch (the three steps per     */
 /* set, Section 2.1).                                                      */
 /* ---------------------------------------------------------------------- */

@@ -75,6 +75,12 @@ def _declare(lib):
         "ch_hull_learned_workspace_size": (ctypes.c_int, [i64, i32, szp]),
         "ch_hull_learned_kernel_count": (ctypes.c_int, [i64, i32, i32, ctypes.POINTER(i32)]),
         "ch_hull_learned": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P, P, P, sz, P]),
+        "ch_polyline_workspace_size": (ctypes.c_int, [i32, szp]),
+        "ch_polyline": (ctypes.c_int, [P, i32, P, P, P, sz, P]),
+        "ch_hull_melkman_workspace_size": (ctypes.c_int, [i32, szp]),
+        "ch_hull_melkman": (ctypes.c_int, [P, P, i32, P, P, P, sz, P]),
+        "ch_convex_hull_melkman_workspace_size": (ctypes.c_int, [i64, i32, szp]),
+        "ch_convex_hull_melkman": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, sz, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -287,6 +293,66 @@ def ch_convex_hull_host(host_pts, p: int, workspace, stream=None, host_hull=None
 
 
 # ------------------------------------------------------------------ batched
+
+
+def ch_polyline_workspace_size(p: int) -> int:
+    return _size(lib().ch_polyline_workspace_size, int(p))
+
+
+def ch_polyline(L, p: int | None = None, poly=None, count=None, workspace=None, stream=None):
+    """Lemma 1 polyline of L: returns (poly, count); poly has capacity 2p
+    rows, the first count[0] of which are the vertices."""
+    dev = _dev(L)
+    p = int(L.shape[0] if p is None else p)
+    if poly is None:
+        poly = torch.empty((2 * p, 2), dtype=torch.int32, device=dev)
+    if count is None:
+        count = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = _ws(ch_polyline_workspace_size(p), dev, workspace)
+    _check(lib().ch_polyline(_ptr(L), p, _ptr(poly), _ptr(count), _ptr(ws), ws.numel(),
+                             _stream(stream)), "ch_polyline")
+    return poly, count
+
+
+def ch_hull_melkman_workspace_size(p: int) -> int:
+    return _size(lib().ch_hull_melkman_workspace_size, int(p))
+
+
+def ch_hull_melkman(poly, count, p: int, hull=None, hull_count=None, workspace=None, stream=None):
+    """Melkman's hull of the simple polyline poly[:count[0]] (count: device
+    int32 tensor); returns (hull, hull_count)."""
+    dev = _dev(poly)
+    if hull is None:
+        hull = torch.empty((max(2 * int(p), 2), 2), dtype=torch.int32, device=dev)
+    if hull_count is None:
+        hull_count = torch.empty(1, dtype=torch.int32, device=dev)
+    need = ch_hull_melkman_workspace_size(p)
+    ws = _ws(need, dev, workspace) if need or workspace is not None else None
+    _check(lib().ch_hull_melkman(_ptr(poly), _ptr(count), int(p), _ptr(hull), _ptr(hull_count),
+                                 _ptr(ws), 0 if ws is None else ws.numel(), _stream(stream)),
+           "ch_hull_melkman")
+    return hull, hull_count
+
+
+def ch_convex_hull_melkman_workspace_size(n: int, p: int) -> int:
+    return _size(lib().ch_convex_hull_melkman_workspace_size, int(n), int(p))
+
+
+def ch_convex_hull_melkman(pts, p: int, L=None, poly=None, poly_count=None, hull=None,
+                           hull_count=None, workspace=None, stream=None):
+    """Algorithm 1, the Lemma 1 polyline and Melkman's hull in one call;
+    returns (hull, hull_count)."""
+    pts = _pts(pts)
+    dev = _dev(pts)
+    if hull is None:
+        hull = torch.empty((2 * p, 2), dtype=torch.int32, device=dev)
+    if hull_count is None:
+        hull_count = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = _ws(ch_convex_hull_melkman_workspace_size(pts.shape[0], p), dev, workspace)
+    _check(lib().ch_convex_hull_melkman(_ptr(pts), pts.shape[0], int(p), _ptr(L), _ptr(poly),
+                                        _ptr(poly_count), _ptr(hull), _ptr(hull_count), _ptr(ws),
+                                        ws.numel(), _stream(stream)), "ch_convex_hull_melkman")
+    return hull, hull_count
 
 
 def _host_sizes(offsets, ps):

@@ -811,4 +811,125 @@ int ch_convex_hull_host(const int32_t *host_pts, int64_t n, int32_t p, int32_t *
     return ch_sync_status(stream);
 }
 
+// ---- Lemma 1 polyline and Melkman's hull ----
+
+int ch_polyline_workspace_size(int32_t p, size_t *bytes)
+{
+    if (!bytes || p < 1 || p > CH_MAX_P)
+        return CH_ERR_ARG;
+    *bytes = polyline_state_bytes(p);
+    return CH_OK;
+}
+
+int ch_polyline(const int32_t *L, int32_t p, int32_t *poly, int32_t *count, void *workspace,
+                size_t ws_bytes, ch_stream_t stream)
+{
+    if (p < 1 || p > CH_MAX_P || !L || !poly || !count || !aligned8(L) || !aligned8(poly))
+        return CH_ERR_ARG;
+    if (ws_bytes < polyline_state_bytes(p) || !workspace)
+        return CH_ERR_WORKSPACE;
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    return cuda_rc(polyline_launch(L, p, p, poly, count, workspace, false, st,
+                                   reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int ch_hull_melkman_workspace_size(int32_t p, size_t *bytes)
+{
+    if (!bytes || p < 1 || p > CH_MAX_P)
+        return CH_ERR_ARG;
+    *bytes = melkman_ws_bytes(p);
+    return CH_OK;
+}
+
+int ch_hull_melkman(const int32_t *poly, const int32_t *count, int32_t p, int32_t *hull,
+                    int32_t *hull_count, void *workspace, size_t ws_bytes, ch_stream_t stream)
+{
+    if (p < 1 || p > CH_MAX_P || !poly || !count || !hull || !hull_count || !aligned8(poly) ||
+        !aligned8(hull))
+        return CH_ERR_ARG;
+    const size_t need = melkman_ws_bytes(p);
+    if (ws_bytes < need || (need && !workspace))
+        return CH_ERR_WORKSPACE;
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    return cuda_rc(melkman_launch(poly, count, p, hull, hull_count, workspace, st,
+                                  reinterpret_cast<cudaStream_t>(stream)));
+}
+
+namespace {
+struct MelkmanWs {
+    ReducePlan plan;
+    size_t state, part, L, poly, count, dq, end;
+};
+int melkman_layout(int64_t n, int p, MelkmanWs *w)
+{
+    int rc = reduce_plan(n, p, &w->plan);
+    if (rc != CH_OK)
+        return rc;
+    WsLayout l;
+    w->state = l.take(polyline_state_bytes(p));
+    w->part = l.take(reduce_partials_bytes(w->plan, p));
+    w->L = l.take((size_t)p * 8);
+    w->poly = l.take((size_t)p * 16);
+    w->count = l.take(8);
+    w->dq = l.take(melkman_ws_bytes(p));
+    w->end = l.off;
+    return CH_OK;
+}
+}  // namespace
+
+int ch_convex_hull_melkman_workspace_size(int64_t n, int32_t p, size_t *bytes)
+{
+    if (!bytes || check_np(n, p) != CH_OK)
+        return CH_ERR_ARG;
+    MelkmanWs w;
+    const int rc = melkman_layout(n, p, &w);
+    if (rc != CH_OK)
+        return rc;
+    *bytes = w.end;
+    return CH_OK;
+}
+
+int ch_convex_hull_melkman(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t *poly,
+                           int32_t *poly_count, int32_t *hull, int32_t *hull_count,
+                           void *workspace, size_t ws_bytes, ch_stream_t stream)
+{
+    if (check_np(n, p) != CH_OK || (n > 0 && !pts) || !hull || !hull_count || !aligned8(pts) ||
+        !aligned8(L) || !aligned8(poly) || !aligned8(hull))
+        return CH_ERR_ARG;
+    MelkmanWs w;
+    int rc = melkman_layout(n, p, &w);
+    if (rc != CH_OK)
+        return rc;
+    if (ws_bytes < w.end || !workspace)
+        return CH_ERR_WORKSPACE;
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *b = reinterpret_cast<char *>(workspace);
+    if (!L)
+        L = reinterpret_cast<int32_t *>(b + w.L);
+    if (!poly)
+        poly = reinterpret_cast<int32_t *>(b + w.poly);
+    if (!poly_count)
+        poly_count = reinterpret_cast<int32_t *>(b + w.count);
+    cudaEvent_t ev0, ev1;
+    next_trace(&ev0, &ev1);
+    unsigned long long *zero = reinterpret_cast<unsigned long long *>(b + w.state);
+    const int nzero = (int)(polyline_state_bytes(p) / 8);
+    cudaError_t e = reduce_launch(w.plan, pts, n, square_frame(p), b + w.part, L, st, s,
+                                  w.plan.mode == 0 ? nullptr : zero, nzero, ev0, ev1);
+    if (e == cudaSuccess && w.plan.mode == 0)
+        e = reduce_merge_launch(b + w.part, w.plan.copies, p, p, L, s, zero, nzero);
+    if (e == cudaSuccess)
+        e = polyline_launch(L, p, p, poly, poly_count, zero, true, st, s);
+    if (e == cudaSuccess)
+        e = melkman_launch(poly, poly_count, p, hull, hull_count, b + w.dq, st, s);
+    return cuda_rc(e);
+}
+
 }  // extern "C"

@@ -220,6 +220,18 @@ cudaError_t bbox_launch(const int32_t *pts, int64_t n, int32_t *box, void *ws, c
 cudaError_t unframe_launch(const int32_t *hull_in, const int32_t *count_in, const Frame &f,
                            int32_t *hull_out, int32_t *count_out, cudaStream_t s);
 
+// ---- Lemma 1 polyline and Melkman's hull (polyline.cu) ----
+size_t polyline_state_bytes(int p);
+// poly: the Lemma 1 polyline of L (columns of nr rows; 0 means p), *count
+// its vertices.  state: polyline_state_bytes(p), zeroed here unless
+// state_zeroed.
+cudaError_t polyline_launch(const int32_t *L, int p, int nr, int32_t *poly, int32_t *count,
+                            void *state, bool state_zeroed, unsigned *status, cudaStream_t s);
+long long lattice_hull_bound(int p);
+size_t melkman_ws_bytes(int p);  // 0 when the deque fits in shared memory
+cudaError_t melkman_launch(const int32_t *poly, const int32_t *count, int p, int32_t *hull,
+                           int32_t *hull_count, void *ws, unsigned *status, cudaStream_t s);
+
 // ---- api.cu ----
 unsigned *device_status_ptr();  // this device's status word (nullptr on failure)
 int sm_count();

@@ -166,6 +166,17 @@ def points(dist: str, n: int, p: int, seed: int = 0) -> np.ndarray:
     return _GEN[dist](n, p, seed)
 
 
+def boxed(dist: str, n: int, sx: int, sy: int, x0: int, y0: int, seed: int = 0) -> np.ndarray:
+    """n points of a distribution drawn on the 65536 x 65536 square, scaled
+    (integer arithmetic) to an sx by sy box and shifted to start at (x0, y0):
+    int32 points anywhere, the input of the bounding-box steps.  The box must
+    fit in int32."""
+    base = points(dist, n, 65536, seed=seed).astype(np.int64) - 1
+    x = x0 + (base[:, 0] * (sx - 1)) // 65535
+    y = y0 + (base[:, 1] * (sy - 1)) // 65535
+    return np.ascontiguousarray(np.stack([x, y], 1).astype(np.int32))
+
+
 def batched_spec(B: int, seed: int = 0, n_lo: float = 1e2, n_hi: float = 1e6,
                  ps=(256, 1024, 4096, 16384), dists=("uniform", "disc", "gaussian")):
     """Per-set sizes of the batched workload: n log-uniform in [n_lo, n_hi],
