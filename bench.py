@@ -28,6 +28,11 @@ Other workloads (--workload):
             box at (-123456789, 987654321)); a step is ch_bbox on each, one
             read of the three boxes, then ch_convex_hull_box on each (columns
             along the shorter side), each instance on its own stream.
+  sparse    the sparse regime p > n (Section 4): p = 2^24, n = 2^20 per
+            instance, uniform / disc / Gaussian, through the tree of bit words
+            (ch_convex_hull_sparse) against the plain path (an array L of p
+            entries) on the same inputs; plus, as in Fig. 11, both paths at
+            column densities s/p of 5 % to 85 % (uniform x).
   melkman   the paper's Melkman experiment (Section 3, Fig. 10) on the
             projected-shells stand-in (p = 4096, 10^7 points): Algorithm 1,
             the Lemma 1 polyline and Melkman's hull (ch_convex_hull_melkman)
@@ -205,6 +210,13 @@ def workload_config(workload):
                 "instances_per_step": len(BOX),
                 "concurrency": "each instance on its own CUDA stream and workspace",
                 "l2": "inputs 8n bytes per instance, larger than L2; no flush"}
+    if workload == "sparse":
+        p, n, dists = SPARSE
+        return {"workload": "sparse", "p": p, "n_per_instance": n, "distributions": list(dists),
+                "instances_per_step": len(dists),
+                "concurrency": "each instance on its own CUDA stream and workspace",
+                "l2": "points 8 MB per instance, below L2: a 256 MB write precedes every step "
+                      "and its time is subtracted"}
     if workload == "melkman":
         p, n, dists = WORKLOADS[MELKMAN]
         return {"workload": "melkman", "p": p, "n_per_instance": n, "distributions": list(dists),
@@ -232,6 +244,9 @@ def _reference_units(workload):
         return [(int(ps[s]), f"set{s}", pts[off[s]:off[s + 1]]) for s in range(len(ps))]
     if workload == "box":
         return [(None, d, P) for d, P in box_inputs(0)]
+    if workload == "sparse":
+        p, n, dists = SPARSE
+        return [(p, d, synth.points(d, n, p, seed=51 + i)) for i, d in enumerate(dists)]
     p, n, inputs = gen_inputs(MELKMAN if workload == "melkman" else workload, 0)
     return [(p, d, P) for d, P in inputs]
 
@@ -245,6 +260,11 @@ def oracle_solver(workload):
         return lambda p, P: oracle.hull_box(P)
     if workload == "melkman":
         return lambda p, P: oracle.melkman(oracle.polyline(oracle.reduce(P, p)))
+    if workload == "sparse":  # the chains from the points (no array of p), then the hull
+        def solve(p, P):
+            oracle.chain_points(P)
+            return oracle.hull_points(P)
+        return solve
     return lambda p, P: oracle.hull_chain(oracle.reduce(P, p))
 
 
@@ -458,6 +478,9 @@ BOX = (("uniform", 65536, 65536, -1_500_000_000, 700_000_000),
        ("disc", 120_000, 40_000, 1_000_000_000, -2_000_000_000),
        ("gaussian", 30_000, 90_000, -123_456_789, 987_654_321))
 MELKMAN = "projected_shells"
+# sparse regime p > n: side, points per instance, distributions
+SPARSE = (1 << 24, 1 << 20, ("uniform", "disc", "gaussian"))
+SPARSE_DENSITIES = (0.05, 0.25, 0.45, 0.65, 0.85)
 
 
 def box_inputs(rank):
@@ -1065,6 +1088,163 @@ def run_melkman(args):
         dist.destroy_process_group()
 
 
+def run_sparse(args):
+    """The tree of bit words against the array L of p entries, p > n."""
+    torch, dist, world, rank = _setup_dist()
+    from paper_1505_00914_gb300 import ch, synth
+    ch.lib()
+    p, n, dists = SPARSE
+    inputs = [(d, synth.points(d, n, p, seed=51 + 1000 * rank + i)) for i, d in enumerate(dists)]
+    dev_in = [torch.from_numpy(P).cuda() for _, P in inputs]
+    stream = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream() for _ in inputs]
+    ws_s = [ch.ch_sparse_workspace(n, p) for _ in inputs]
+    ws_p = [torch.empty(ch.ch_convex_hull_workspace_size(n, p), dtype=torch.uint8, device="cuda")
+            for _ in inputs]
+    cap = min(p, n)
+    out = {a: [(torch.empty((2 * cap, 2), dtype=torch.int32, device="cuda"),
+                torch.empty(1, dtype=torch.int32, device="cuda")) for _ in inputs]
+           for a in ("sparse", "plain")}
+    cnts = [torch.empty(2, dtype=torch.int32, device="cuda") for _ in inputs]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def run(arm, i, st):
+        h, hc = out[arm][i]
+        if arm == "sparse":
+            ch.ch_convex_hull_sparse(dev_in[i], p, ws_s[i], counts=cnts[i], hull=h, hull_count=hc,
+                                     stream=st)
+        else:
+            ch.ch_convex_hull(dev_in[i], p, hull=h, hull_count=hc, workspace=ws_p[i], stream=st)
+
+    def step(arm, concurrent=True):
+        flush.zero_()
+        if not concurrent:
+            for i in range(len(inputs)):
+                run(arm, i, stream)
+            return
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        for i, st in enumerate(streams):
+            st.wait_event(fork)
+            run(arm, i, st)
+        for st in streams:
+            join = torch.cuda.Event()
+            join.record(st)
+            stream.wait_event(join)
+
+    for arm in ("sparse", "plain"):
+        for _ in range(args.warmup):
+            step(arm)
+    torch.cuda.synchronize()
+    rc = ch.ch_sync_status()
+    if rc != ch.CH_OK:
+        raise RuntimeError(f"warm-up failed: {ch.strerror(rc)}")
+    same = all(torch.equal(out["sparse"][i][0][: int(out["sparse"][i][1].item())].cpu(),
+                           out["plain"][i][0][: int(out["plain"][i][1].item())].cpu())
+               for i in range(len(inputs)))
+    cols = [int(c[0].item()) for c in cnts]
+    fl = _timed(torch, dist, world, lambda: flush.zero_(), args.steps, stream)
+    nl = args.steps * len(inputs)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nl)]
+    for a, b in evs:
+        a.record(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    ms = {arm: _timed(torch, dist, world, lambda arm=arm: step(arm), args.steps, stream) - fl
+          for arm in ("sparse", "plain")}
+    ch.ch_trace_set(evs)
+    ms_traced = _timed(torch, dist, world, lambda: step("sparse", False), args.steps, stream) - fl
+    ch.ch_trace_set([])
+    # Fig. 11: both paths at column densities s/p (uniform x), one instance each
+    sweep = []
+    for dens in SPARSE_DENSITIES:
+        nd = int(round(-p * np.log1p(-dens)))
+        Q = torch.from_numpy(synth.points("uniform", nd, p, seed=61)).cuda()
+        wsd = ch.ch_sparse_workspace(nd, p)
+        wpd = torch.empty(ch.ch_convex_hull_workspace_size(nd, p), dtype=torch.uint8, device="cuda")
+        hd = torch.empty((2 * min(p, nd), 2), dtype=torch.int32, device="cuda")
+        hcd = torch.empty(1, dtype=torch.int32, device="cuda")
+        cd = torch.empty(2, dtype=torch.int32, device="cuda")
+        fns = {"sparse": lambda: ch.ch_convex_hull_sparse(Q, p, wsd, counts=cd, hull=hd,
+                                                          hull_count=hcd, stream=stream),
+               "array": lambda: ch.ch_convex_hull(Q, p, hull=hd, hull_count=hcd, workspace=wpd,
+                                                  stream=stream)}
+        row = {"density_target": dens, "n": nd}
+        for k, fn in fns.items():
+            for _ in range(3):
+                fn()
+            reps = 5
+            t = _timed(torch, dist, world, lambda fn=fn: (flush.zero_(), fn()), reps, stream)
+            row[k + "_ms"] = (t - fl / args.steps * reps) / reps
+        row["density"] = int(cd[0].item()) / p
+        sweep.append(row)
+        del wsd, wpd, Q
+    clocks = sampler.stop()
+    rc = ch.ch_sync_status()
+    if rc != ch.CH_OK:
+        raise RuntimeError(f"timed run failed: {ch.strerror(rc)}")
+    red_avg = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+    pts_step = n * len(inputs)
+    rate = {arm: world * pts_step * args.steps / (t / 1e3) / 1e9 for arm, t in ms.items()}
+
+    e2e_steps = max(1, min(args.steps, 5))
+    host_in = [torch.from_numpy(P).pin_memory() for _, P in inputs]
+    hh = torch.empty((2 * cap, 2), dtype=torch.int32).pin_memory()
+    d2h = 0
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for i, hp in enumerate(host_in):
+            dev_in[i].copy_(hp, non_blocking=True)
+            run("sparse", i, stream)
+            k = int(out["sparse"][i][1].item())
+            hh[:k].copy_(out["sparse"][i][0][:k])
+            d2h += 4 + 8 * k
+    e2e_s = _max_over_ranks(torch, dist, world, time.perf_counter() - w0)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = _peaks()
+    # the reduction kernel reads the points and reads and writes each touched
+    # entry of L (16 bytes per valid column)
+    s_avg = sum(cols) / len(cols)
+    kernel_bytes = 8 * n + 16 * s_avg
+    achieved = kernel_bytes / (red_avg / 1e3) / 1e9
+    cpu_v, cpu_dt, cpu_passes = _cpu_rate(oracle_solver("sparse"), [(p, P) for _, P in inputs],
+                                          args.cpu_budget)
+    line = {
+        "metric": METRIC, "value": rate["sparse"], "unit": "Gpoints/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms["sparse"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": workload_config("sparse"),
+        "sparse": {"plain_gpoints_s": rate["plain"], "speedup_vs_plain": rate["sparse"] / rate["plain"],
+                   "ms_per_step": {a: t / args.steps for a, t in ms.items()},
+                   "valid_columns": cols, "hulls_identical": same,
+                   "l2_flush_ms_subtracted": fl / args.steps, "density_sweep": sweep},
+        "roofline": {"bound": "hbm", "kernel": "k_sparse_reduce", "achieved": achieved,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "algorithmic_bytes_per_launch": kernel_bytes, "avg_launch_ms": red_avg,
+                     "ms_per_step_while_timed": ms_traced / args.steps, "traffic": None,
+                     "note": "scattered atomics on L and the tree, not a streaming pass"},
+        "e2e": {"value": world * pts_step * e2e_steps / e2e_s / 1e9, "unit": "Gpoints/s",
+                "h2d_bytes_per_step": pts_step * 8, "d2h_bytes_per_step": d2h // e2e_steps,
+                "steps": e2e_steps},
+        "cpu_baseline": {"value": cpu_v, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{cpu_passes} pass(es) over the step's instances "
+                                   f"({cpu_dt:.1f} s, single thread: chains from the points "
+                                   f"+ hull)"},
+        "gpu_launches": args.steps * len(inputs) * ch.ch_sparse_kernel_count(n, p),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1072,7 +1252,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["learned", "batched", "box",
-                                                                "melkman"],
+                                                                "melkman", "sparse"],
                     default="plain_at_scale")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
@@ -1088,6 +1268,8 @@ def main():
         run_box(args)
     elif args.workload == "melkman":
         run_melkman(args)
+    elif args.workload == "sparse":
+        run_sparse(args)
     else:
         run_ours(args)
 

@@ -197,12 +197,43 @@ int ch_hull_melkman(const int32_t *poly, const int32_t *count, int32_t p, int32_
 
 int ch_convex_hull_melkman_workspace_size(int64_t n, int32_t p, size_t *bytes);
 
-/* ch_reduce, ch_polyline and ch_hull_melkman in one call; L, poly and
+/* ch_reduce, the polyline and ch_hull_melkman in one call; L, poly and
  * poly_count may each be NULL (the workspace holds them).  Same hull as
- * ch_convex_hull. */
+ * ch_convex_hull.  The polyline written to poly (capacity 2p pairs) is
+ * ch_polyline's with the vertices that the exact in-tile pre-filter of the
+ * hull step rules out (on or above a segment between two other chain points)
+ * removed, column by column: the Lemma 1 polyline of a sub-array of L, so
+ * still simple, and holding every hull vertex. */
 int ch_convex_hull_melkman(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t *poly,
                            int32_t *poly_count, int32_t *hull, int32_t *hull_count,
                            void *workspace, size_t ws_bytes, ch_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* The sparse regime p > n (Section 4, "Extraction using a tree structure" */
+/* and "For all practical purposes"): the bit array M becomes a w-ary tree */
+/* of 32-bit words (one bit per non-empty word of the level below), L is   */
+/* kept in a form whose empty entry is all-zero, and each call clears what */
+/* it touched, so that a call costs O(n + s) and never O(p).               */
+/* ---------------------------------------------------------------------- */
+
+/* *bytes: workspace for n points of side p; *persistent_bytes (optional):
+ * its leading part, which must be zero-filled (cudaMemsetAsync) before the
+ * first call and which every call that records no error leaves zero-filled
+ * again (it depends on p only, so one workspace sized for the largest n
+ * serves any smaller n of the same p).  After a recorded error, zero it
+ * again. */
+int ch_sparse_workspace_size(int64_t n, int32_t p, size_t *bytes, size_t *persistent_bytes);
+
+/* Number of kernels one ch_convex_hull_sparse call launches. */
+int ch_sparse_kernel_count(int64_t n, int32_t p, int32_t *kernels);
+
+/* Same results as ch_convex_hull (chains and hull; L is not materialised):
+ * lower, upper (capacity min(p, n) pairs each) and counts may be NULL, in
+ * which case the workspace holds them.  Points outside [1,p]^2 are skipped
+ * and recorded as CH_ERR_RANGE. */
+int ch_convex_hull_sparse(const int32_t *pts, int64_t n, int32_t p, int32_t *lower,
+                          int32_t *upper, int32_t *counts, int32_t *hull, int32_t *hull_count,
+                          void *workspace, size_t ws_bytes, ch_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
 /* Many independent sets in one persistent launch (the three steps per     */

@@ -126,6 +126,27 @@ def chain(L) -> tuple[np.ndarray, np.ndarray]:
     return lo[:s].copy(), up[:s].copy()
 
 
+def chain_points(pts) -> tuple[np.ndarray, np.ndarray]:
+    """The Lemma 1 chains straight from the points, for sides too large for
+    an array L of p entries: for each distinct x in increasing order,
+    (x, min y) and (x, max y) of the points with that x.  The same result as
+    chain(reduce(pts, p)) without the O(p) array."""
+    pts = _pts(pts)
+    if pts.shape[0] == 0:
+        e = np.zeros((0, 2), dtype=np.int32)
+        return e, e.copy()
+    x, y = pts[:, 0].astype(np.int64), pts[:, 1].astype(np.int64)
+    o = np.lexsort((y, x))
+    x, y = x[o], y[o]
+    first = np.ones(x.shape[0], dtype=bool)
+    first[1:] = x[1:] != x[:-1]
+    last = np.ones(x.shape[0], dtype=bool)
+    last[:-1] = x[1:] != x[:-1]
+    lo = np.stack([x[first], y[first]], 1).astype(np.int32)
+    up = np.stack([x[last], y[last]], 1).astype(np.int32)
+    return lo, up
+
+
 def mask(L) -> np.ndarray:
     """Bit array M ("Extraction using an array of bits"): uint32 words,
     column i at bit (i-1)&31 of word (i-1)>>5."""

@@ -81,6 +81,9 @@ def _declare(lib):
         "ch_hull_melkman": (ctypes.c_int, [P, P, i32, P, P, P, sz, P]),
         "ch_convex_hull_melkman_workspace_size": (ctypes.c_int, [i64, i32, szp]),
         "ch_convex_hull_melkman": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, sz, P]),
+        "ch_sparse_workspace_size": (ctypes.c_int, [i64, i32, szp, szp]),
+        "ch_sparse_kernel_count": (ctypes.c_int, [i64, i32, ctypes.POINTER(i32)]),
+        "ch_convex_hull_sparse": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, sz, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -352,6 +355,49 @@ def ch_convex_hull_melkman(pts, p: int, L=None, poly=None, poly_count=None, hull
     _check(lib().ch_convex_hull_melkman(_ptr(pts), pts.shape[0], int(p), _ptr(L), _ptr(poly),
                                         _ptr(poly_count), _ptr(hull), _ptr(hull_count), _ptr(ws),
                                         ws.numel(), _stream(stream)), "ch_convex_hull_melkman")
+    return hull, hull_count
+
+
+def ch_sparse_workspace_size(n: int, p: int):
+    """(bytes, persistent_bytes) of the sparse path's workspace: the leading
+    persistent_bytes must be zero before the first call and stay zero after
+    each call that records no error."""
+    a, b = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    _check(lib().ch_sparse_workspace_size(int(n), int(p), ctypes.byref(a), ctypes.byref(b)),
+           "ch_sparse_workspace_size")
+    return int(a.value), int(b.value)
+
+
+def ch_sparse_kernel_count(n: int, p: int) -> int:
+    k = ctypes.c_int32(0)
+    _check(lib().ch_sparse_kernel_count(int(n), int(p), ctypes.byref(k)), "ch_sparse_kernel_count")
+    return int(k.value)
+
+
+def ch_sparse_workspace(n: int, p: int, device="cuda"):
+    """A zero-filled workspace for ch_convex_hull_sparse."""
+    nbytes, _ = ch_sparse_workspace_size(n, p)
+    return torch.zeros(max(nbytes, 1), dtype=torch.uint8, device=device)
+
+
+def ch_convex_hull_sparse(pts, p: int, workspace, lower=None, upper=None, counts=None, hull=None,
+                          hull_count=None, stream=None):
+    """The path through the tree of bit words (sparse regime p > n); the
+    workspace comes from ch_sparse_workspace and is reused across calls.
+    Returns (hull, hull_count)."""
+    pts = _pts(pts)
+    dev = _dev(pts)
+    n = pts.shape[0]
+    if hull is None:
+        hull = torch.empty((max(2 * min(p, max(n, 1)), 2), 2), dtype=torch.int32, device=dev)
+    if hull_count is None:
+        hull_count = torch.empty(1, dtype=torch.int32, device=dev)
+    need, _ = ch_sparse_workspace_size(n, p)
+    if workspace.numel() * workspace.element_size() < need:
+        raise ChError(CH_ERR_WORKSPACE, "ch_convex_hull_sparse")
+    _check(lib().ch_convex_hull_sparse(_ptr(pts), n, int(p), _ptr(lower), _ptr(upper), _ptr(counts),
+                                       _ptr(hull), _ptr(hull_count), _ptr(workspace),
+                                       workspace.numel(), _stream(stream)), "ch_convex_hull_sparse")
     return hull, hull_count
 
 

@@ -926,10 +926,57 @@ int ch_convex_hull_melkman(const int32_t *pts, int64_t n, int32_t p, int32_t *L,
     if (e == cudaSuccess && w.plan.mode == 0)
         e = reduce_merge_launch(b + w.part, w.plan.copies, p, p, L, s, zero, nzero);
     if (e == cudaSuccess)
-        e = polyline_launch(L, p, p, poly, poly_count, zero, true, st, s);
+        e = polyline_launch(L, p, p, poly, poly_count, zero, true, st, s, true);
     if (e == cudaSuccess)
         e = melkman_launch(poly, poly_count, p, hull, hull_count, b + w.dq, st, s);
     return cuda_rc(e);
+}
+
+// ---- sparse regime (p > n): the w-ary tree of bit words ----
+
+int ch_sparse_workspace_size(int64_t n, int32_t p, size_t *bytes, size_t *persistent_bytes)
+{
+    if (!bytes || check_np(n, p) != CH_OK)
+        return CH_ERR_ARG;
+    const SparseLayout L = sparse_layout(n, p);
+    *bytes = L.end;
+    if (persistent_bytes)
+        *persistent_bytes = L.persistent_end;
+    return CH_OK;
+}
+
+int ch_sparse_kernel_count(int64_t n, int32_t p, int32_t *kernels)
+{
+    if (!kernels || check_np(n, p) != CH_OK)
+        return CH_ERR_ARG;
+    *kernels = sparse_kernel_count(sparse_layout(n, p));
+    return CH_OK;
+}
+
+int ch_convex_hull_sparse(const int32_t *pts, int64_t n, int32_t p, int32_t *lower,
+                          int32_t *upper, int32_t *counts, int32_t *hull, int32_t *hull_count,
+                          void *workspace, size_t ws_bytes, ch_stream_t stream)
+{
+    if (check_np(n, p) != CH_OK || (n > 0 && !pts) || !hull || !hull_count || !aligned8(pts) ||
+        !aligned8(lower) || !aligned8(upper) || !aligned8(hull))
+        return CH_ERR_ARG;
+    const SparseLayout L = sparse_layout(n, p);
+    if (ws_bytes < L.end || !workspace)
+        return CH_ERR_WORKSPACE;
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    char *b = reinterpret_cast<char *>(workspace);
+    if (!lower)
+        lower = reinterpret_cast<int32_t *>(b + L.lower);
+    if (!upper)
+        upper = reinterpret_cast<int32_t *>(b + L.upper);
+    if (!counts)
+        counts = reinterpret_cast<int32_t *>(b + L.counts);
+    cudaEvent_t ev0, ev1;
+    next_trace(&ev0, &ev1);
+    return cuda_rc(sparse_launch(L, pts, n, p, workspace, lower, upper, counts, hull, hull_count,
+                                 st, reinterpret_cast<cudaStream_t>(stream), ev0, ev1));
 }
 
 }  // extern "C"

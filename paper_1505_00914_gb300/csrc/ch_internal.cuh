@@ -224,13 +224,37 @@ cudaError_t unframe_launch(const int32_t *hull_in, const int32_t *count_in, cons
 size_t polyline_state_bytes(int p);
 // poly: the Lemma 1 polyline of L (columns of nr rows; 0 means p), *count
 // its vertices.  state: polyline_state_bytes(p), zeroed here unless
-// state_zeroed.
+// state_zeroed.  filter: drop the vertices the in-tile hull pre-filter rules
+// out (still a simple polyline with every hull vertex).
 cudaError_t polyline_launch(const int32_t *L, int p, int nr, int32_t *poly, int32_t *count,
-                            void *state, bool state_zeroed, unsigned *status, cudaStream_t s);
+                            void *state, bool state_zeroed, unsigned *status, cudaStream_t s,
+                            bool filter = false);
 long long lattice_hull_bound(int p);
 size_t melkman_ws_bytes(int p);  // 0 when the deque fits in shared memory
 cudaError_t melkman_launch(const int32_t *poly, const int32_t *count, int p, int32_t *hull,
                            int32_t *hull_count, void *ws, unsigned *status, cudaStream_t s);
+
+// ---- sparse regime: w-ary tree of bit words (sparse.cu) ----
+constexpr int TREE_MAX_LEVELS = 7;  // 32^6 >= 2^30
+struct TreeLevels {
+    int levels;
+    uint32_t *M[TREE_MAX_LEVELS];
+};
+struct SparseLayout {
+    int levels, chain_cap, state_words;
+    size_t words[TREE_MAX_LEVELS], list_cap[TREE_MAX_LEVELS];
+    int state_off[TREE_MAX_LEVELS];
+    size_t Lz, M[TREE_MAX_LEVELS], persistent_end;  // zero-filled between calls
+    size_t list[2], cnt, state, lower, upper, counts, hull, end;
+};
+// Levels of the tree for side p (words[k] = words of level k, optional).
+int tree_levels(int p, size_t *words);
+SparseLayout sparse_layout(int64_t n, int p);
+cudaError_t sparse_launch(const SparseLayout &L, const int32_t *pts, int64_t n, int p, void *ws,
+                          int32_t *lower, int32_t *upper, int32_t *counts, int32_t *hull,
+                          int32_t *hull_count, unsigned *status, cudaStream_t s, cudaEvent_t ev0,
+                          cudaEvent_t ev1);
+int sparse_kernel_count(const SparseLayout &L);
 
 // ---- api.cu ----
 unsigned *device_status_ptr();  // this device's status word (nullptr on failure)

@@ -6,7 +6,9 @@
 //             then (x, hy) when the two differ: a compaction with weights
 //             0, 1 or 2 per column in one pass over 1024-column tiles
 //             (decoupled look-back).  Joining consecutive vertices gives the
-//             simple chain of Lemma 1.
+//             simple chain of Lemma 1.  The filtered form drops, tile by
+//             tile, the vertices the exact pre-filter of the hull step rules
+//             out, which leaves a shorter simple polyline for Melkman.
 // k_melkman   one warp runs Melkman's algorithm.  A deque holds the hull of
 //             the vertices seen so far, counter-clockwise from its bottom to
 //             its top, with the newest vertex at both ends; only the two
@@ -22,8 +24,10 @@
 //             drop collinear points: the hull lists strict vertices,
 //             counter-clockwise from the lexicographic minimum.
 #include <climits>
+#include <type_traits>
 
 #include "ch_internal.cuh"
+#include "hull_filter.cuh"
 #include "lookback.cuh"
 
 namespace ch {
@@ -32,6 +36,18 @@ namespace {
 constexpr int PL_TILE = 1024;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
+struct PolyFilterSmem {
+    int2 P[2][PL_TILE];  // the tile's lower chain and mirrored upper chain
+    short M[2][2 * PL_TILE];
+};
+
+// FILTER: a column's ly (hy) vertex is kept only when the exact in-tile
+// pre-filter of hull_filter.cuh keeps it on the tile's lower (upper) chain;
+// a column with ly == hy keeps its one vertex when either chain keeps it.
+// The result is the Lemma 1 polyline of a sub-array of L (each column
+// holding a subset of its two points), so it is still simple, and it keeps
+// every hull vertex.
+template <bool FILTER>
 __global__ void __launch_bounds__(PL_TILE)
     k_polyline(const int2 *__restrict__ L, int p, int nr, int2 *poly, int *count,
                unsigned long long *state, int ntiles, unsigned *status)
@@ -39,17 +55,60 @@ __global__ void __launch_bounds__(PL_TILE)
     pdl_wait();
     pdl_trigger();
     __shared__ int s_tile, s_tot;
-    __shared__ int s_wsum[PL_TILE / 32];
+    __shared__ int s_wsum[PL_TILE / 32 + 1];
     __shared__ long long s_prefix;
+    __shared__ typename std::conditional<FILTER, PolyFilterSmem, int>::type fs;
     if (threadIdx.x == 0)
         s_tile = (int)atomicAdd(state, 1ull);
     __syncthreads();
     const int tile = s_tile;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int c = tile * PL_TILE + threadIdx.x;  // 0-based column
-    const int2 e = c < p ? L[c] : make_int2(nr + 1, -1);
-    const bool valid = c < p && !(e.x == nr + 1 && e.y == -1);
-    const int wt = valid ? (e.x != e.y ? 2 : 1) : 0;
+    int c = tile * PL_TILE + threadIdx.x;  // 0-based column
+    int2 e = c < p ? L[c] : make_int2(nr + 1, -1);
+    bool valid = c < p && !(e.x == nr + 1 && e.y == -1);
+    int wt;
+    bool emit_lo = valid, emit_hi = valid && e.x != e.y;
+    if constexpr (FILTER) {
+        // rank the valid columns, filter their two chains in shared memory;
+        // from here on thread r speaks for the tile's r-th valid column
+        const unsigned bal = __ballot_sync(FULL, valid);
+        if (lane == 0)
+            s_wsum[w] = __popc(bal);
+        __syncthreads();
+        if (w == 0) {
+            const int v = s_wsum[lane];
+            int inc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULL, inc, o);
+                if (lane >= o)
+                    inc += t;
+            }
+            s_wsum[lane] = inc - v;
+            if (lane == 31)
+                s_wsum[PL_TILE / 32] = inc;
+        }
+        __syncthreads();
+        const int cnt = s_wsum[PL_TILE / 32];
+        if (valid) {
+            const int r = s_wsum[w] + __popc(bal & ((1u << lane) - 1u));
+            fs.P[0][r] = make_int2(c + 1, e.x);
+            fs.P[1][r] = make_int2(c + 1, -e.y);
+        }
+        __syncthreads();
+        build_min_trees(fs.P[0], fs.M[0], cnt, fs.P[1], fs.M[1], cnt);
+        const bool k0 = run_keeps(fs.P[0], fs.M[0], cnt, threadIdx.x);
+        const bool k1 = run_keeps(fs.P[1], fs.M[1], cnt, threadIdx.x);
+        valid = (int)threadIdx.x < cnt;
+        if (valid) {
+            c = fs.P[0][threadIdx.x].x - 1;
+            e = make_int2(fs.P[0][threadIdx.x].y, -fs.P[1][threadIdx.x].y);
+        }
+        emit_lo = valid && (e.x != e.y ? k0 : (k0 || k1));
+        emit_hi = valid && e.x != e.y && k1;
+        __syncthreads();  // s_wsum is reused below
+    }
+    wt = (int)emit_lo + (int)emit_hi;
     int incl = wt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -87,11 +146,11 @@ __global__ void __launch_bounds__(PL_TILE)
         }
     }
     __syncthreads();
-    const long long pos = s_prefix + excl;
-    if (wt >= 1)
-        poly[pos] = make_int2(c + 1, e.x);
-    if (wt == 2)
-        poly[pos + 1] = make_int2(c + 1, e.y);
+    long long pos = s_prefix + excl;
+    if (emit_lo)
+        poly[pos++] = make_int2(c + 1, e.x);
+    if (emit_hi)
+        poly[pos] = make_int2(c + 1, e.y);
 }
 
 constexpr int MK_STAGE = 1024;  // polyline vertices staged per round
@@ -109,8 +168,10 @@ __device__ __forceinline__ unsigned long long lex_key(int2 q)
 }
 
 // poly: *count vertices of a simple polyline, distinct, in [1, p]^2.
-// dq_global: the deque when it does not fit in shared memory, else nullptr;
-// dq_cap: its capacity (a power of two above the largest hull plus one).
+// GDQ: the deque is dq_global (it does not fit in shared memory), else it
+// follows the staging buffer in shared memory; dq_cap: its capacity (a power
+// of two above the largest hull plus one).
+template <bool GDQ>
 __global__ void __launch_bounds__(32)
     k_melkman(const int2 *__restrict__ poly, const int *count, int p, int2 *dq_global,
               unsigned dq_cap, int2 *hull, int *hull_count, unsigned *status)
@@ -119,7 +180,7 @@ __global__ void __launch_bounds__(32)
     pdl_trigger();
     extern __shared__ int2 sm[];
     int2 *stage = sm;
-    int2 *dq = dq_global ? dq_global : sm + MK_STAGE;
+    int2 *dq = GDQ ? dq_global : sm + MK_STAGE;
     const unsigned mask = dq_cap - 1;
     const int lane = threadIdx.x;
     const int m = *count;
@@ -291,7 +352,7 @@ cudaError_t set_melkman_smem()
         return cudaErrorInvalidDevice;
     if (!done[dev]) {
         const cudaError_t e = cudaFuncSetAttribute(
-            k_melkman, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            k_melkman<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
             (int)((MK_STAGE + MK_SMEM_MAX_DQ) * sizeof(int2)));
         if (e != cudaSuccess)
             return e;
@@ -337,7 +398,8 @@ size_t melkman_ws_bytes(int p)
 size_t polyline_state_bytes(int p) { return chain_state_bytes(p); }
 
 cudaError_t polyline_launch(const int32_t *L, int p, int nr, int32_t *poly, int32_t *count,
-                            void *state, bool state_zeroed, unsigned *status, cudaStream_t s)
+                            void *state, bool state_zeroed, unsigned *status, cudaStream_t s,
+                            bool filter)
 {
     const int nt = (p + PL_TILE - 1) / PL_TILE;
     if (!state_zeroed) {
@@ -345,9 +407,9 @@ cudaError_t polyline_launch(const int32_t *L, int p, int nr, int32_t *poly, int3
         if (e != cudaSuccess)
             return e;
     }
-    launch(k_polyline, nt, PL_TILE, 0, s, reinterpret_cast<const int2 *>(L), p, nr > 0 ? nr : p,
-           reinterpret_cast<int2 *>(poly), count, reinterpret_cast<unsigned long long *>(state), nt,
-           status);
+    launch(filter ? k_polyline<true> : k_polyline<false>, nt, PL_TILE, 0, s,
+           reinterpret_cast<const int2 *>(L), p, nr > 0 ? nr : p, reinterpret_cast<int2 *>(poly),
+           count, reinterpret_cast<unsigned long long *>(state), nt, status);
     return cudaGetLastError();
 }
 
@@ -360,7 +422,8 @@ cudaError_t melkman_launch(const int32_t *poly, const int32_t *count, int p, int
     const size_t cap = melkman_deque_cap(p);
     const bool in_smem = cap <= MK_SMEM_MAX_DQ;
     const size_t smem = (MK_STAGE + (in_smem ? cap : 0)) * sizeof(int2);
-    launch(k_melkman, 1, 32, smem, s, reinterpret_cast<const int2 *>(poly), count, p,
+    launch(in_smem ? k_melkman<false> : k_melkman<true>, 1, 32, smem, s,
+           reinterpret_cast<const int2 *>(poly), count, p,
            in_smem ? nullptr : reinterpret_cast<int2 *>(ws), (unsigned)cap,
            reinterpret_cast<int2 *>(hull), hull_count, status);
     return cudaGetLastError();

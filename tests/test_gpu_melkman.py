@@ -69,8 +69,31 @@ def test_polyline_and_melkman_match_the_oracle(dist, p, n):
     H = oracle.hull_points(P)
     np.testing.assert_array_equal(oracle.melkman(poly), H)
     np.testing.assert_array_equal(gpu_melkman(poly, p), H)
-    h, hc = ch.ch_convex_hull_melkman(dev(P).reshape(-1, 2), p)
+    fused_matches(P, p, poly, H)
+
+
+def fused_matches(P, p, poly_full, H):
+    """ch_convex_hull_melkman: the hull is exact; its polyline is the Lemma 1
+    polyline with some non-vertices removed (a subsequence holding every hull
+    vertex), and Melkman on it alone gives the hull again."""
+    d = dev(P).reshape(-1, 2) if P.shape[0] else torch.empty((0, 2), dtype=torch.int32,
+                                                             device="cuda")
+    poly = torch.empty((2 * p, 2), dtype=torch.int32, device="cuda")
+    pc = torch.empty(1, dtype=torch.int32, device="cuda")
+    h, hc = ch.ch_convex_hull_melkman(d, p, poly=poly, poly_count=pc)
     np.testing.assert_array_equal(host(h)[: int(host(hc)[0])], H)
+    sub = host(poly)[: int(host(pc)[0])]
+    assert sub.shape[0] <= poly_full.shape[0]
+    # subsequence of the full polyline
+    key = lambda a: a[:, 0].astype(np.int64) * (1 << 32) + a[:, 1]
+    kf, ks = key(poly_full), key(sub)
+    pos = np.searchsorted(kf, ks)  # the Lemma 1 polyline is sorted by (x, y)
+    assert np.all(pos < kf.shape[0]) and np.all(kf[np.minimum(pos, kf.shape[0] - 1)] == ks)
+    assert np.all(np.diff(pos) > 0)
+    # every hull vertex kept, and Melkman on the shorter polyline agrees
+    assert set(map(tuple, H)) <= set(map(tuple, sub))
+    np.testing.assert_array_equal(oracle.melkman(sub), H)
+    return sub
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 5, 33, 1025])
@@ -82,9 +105,33 @@ def test_small_and_degenerate(p, n):
     poly = gpu_polyline(L, p)
     np.testing.assert_array_equal(poly, oracle.polyline(L))
     np.testing.assert_array_equal(gpu_melkman(poly, p), oracle.hull_points(P))
-    h, hc = ch.ch_convex_hull_melkman(dev(P).reshape(-1, 2) if n else
-                                      torch.empty((0, 2), dtype=torch.int32, device="cuda"), p)
-    np.testing.assert_array_equal(host(h)[: int(host(hc)[0])], oracle.hull_points(P))
+    fused_matches(P, p, poly, oracle.hull_points(P))
+
+
+def _segments_meet(a, b, c, d):
+    def orient(o, u, v):
+        return int(np.sign((int(u[0]) - o[0]) * (int(v[1]) - o[1]) - (int(u[1]) - o[1]) * (int(v[0]) - o[0])))
+
+    def on(o, u, v):
+        return min(o[0], u[0]) <= v[0] <= max(o[0], u[0]) and min(o[1], u[1]) <= v[1] <= max(o[1], u[1])
+    o1, o2, o3, o4 = orient(a, b, c), orient(a, b, d), orient(c, d, a), orient(c, d, b)
+    if o1 * o2 < 0 and o3 * o4 < 0:
+        return True
+    return ((o1 == 0 and on(a, b, c)) or (o2 == 0 and on(a, b, d)) or
+            (o3 == 0 and on(c, d, a)) or (o4 == 0 and on(c, d, b)))
+
+
+@pytest.mark.parametrize("dist", DISTS)
+def test_filtered_polyline_is_simple(dist):
+    """The polyline the fused path hands to Melkman is still simple."""
+    p, n = 40, 3000
+    P = synth.points(dist, n, p, seed=77)
+    L = oracle.reduce(P, p)
+    sub = fused_matches(P, p, oracle.polyline(L), oracle.hull_points(P))
+    e = [(sub[i], sub[i + 1]) for i in range(sub.shape[0] - 1)]
+    for i in range(len(e)):
+        for j in range(i + 2, len(e)):
+            assert not _segments_meet(e[i][0], e[i][1], e[j][0], e[j][1]), (i, j)
 
 
 def test_collinear_and_walk_back_polylines():

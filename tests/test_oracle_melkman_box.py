@@ -155,3 +155,19 @@ def test_hull_box_at_the_ends_of_int32_and_on_the_plain_square():
     np.testing.assert_array_equal(oracle.hull_box(S), oracle.hull(S, p))
     with pytest.raises(ValueError):
         oracle.hull_box(np.asarray([[0, 0], [2 ** 30, 5]], np.int32))
+
+
+def test_chain_points_equals_the_scan_of_L():
+    """The chains taken from the points directly (for sides too large for L)
+    equal the Lemma 1 scan of Algorithm 1's array."""
+    for P, p in _tiny_sets(3000, seed=17):
+        lo, up = oracle.chain_points(P)
+        lo2, up2 = oracle.chain(oracle.reduce(P, p))
+        np.testing.assert_array_equal(lo, lo2)
+        np.testing.assert_array_equal(up, up2)
+    for dist in ("uniform", "gaussian", "shells"):
+        P = synth.points(dist, 200_000, 70_000, seed=4)
+        lo, up = oracle.chain_points(P)
+        lo2, up2 = oracle.chain(oracle.reduce(P, 70_000))
+        np.testing.assert_array_equal(lo, lo2)
+        np.testing.assert_array_equal(up, up2)
