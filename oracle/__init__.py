@@ -59,6 +59,7 @@ def _load():
                 "oracle_polyline": (i64, [P, i32, P]),
                 "oracle_melkman": (i64, [P, i64, P]),
                 "oracle_hull_box": (i64, [P, i64, P]),
+                "oracle_reduce_rows": (None, [P, i32, P]),
                 "oracle_hull_points": (i64, [P, i64, P]),
                 "oracle_hull_chain": (i64, [P, i32, P]),
                 "oracle_hull_brute": (i64, [P, i64, P]),
@@ -145,6 +146,30 @@ def chain_points(pts) -> tuple[np.ndarray, np.ndarray]:
     lo = np.stack([x[first], y[first]], 1).astype(np.int32)
     up = np.stack([x[last], y[last]], 1).astype(np.int32)
     return lo, up
+
+
+def reduce_rows(L) -> np.ndarray:
+    """The second scan along y (Section 2, Fig. 4): Algorithm 1 over the rx
+    points of L (its valid (x, ly) and (x, hy)) with x and y exchanged; row
+    y-1 of the result = (min x, max x), else (p+1, -1)."""
+    L = np.ascontiguousarray(np.asarray(L, dtype=np.int32).reshape(-1, 2))
+    p = L.shape[0]
+    R = np.empty((p, 2), dtype=np.int32)
+    _load().oracle_reduce_rows(_ptr(L), p, _ptr(R))
+    return R
+
+
+def rx_points(L) -> np.ndarray:
+    """The reduced set of the scan along x: the Lemma 1 polyline's vertices."""
+    return polyline(L)
+
+
+def rxy_points(R) -> np.ndarray:
+    """The reduced set after the second scan: (lo, y) then (hi, y) when they
+    differ, for each valid row y in increasing order."""
+    R = np.ascontiguousarray(np.asarray(R, dtype=np.int32).reshape(-1, 2))
+    q = polyline(R)  # rows play the part of columns
+    return np.ascontiguousarray(q[:, ::-1])
 
 
 def mask(L) -> np.ndarray:

@@ -718,3 +718,32 @@ int64_t oracle_hull_box(const int32_t *pts, int64_t n, int32_t *out)
     free(L);
     return h;
 }
+
+/* ------------------------------------------------------------------------ */
+/* The second scan along y (Section 2, Fig. 4: rx -> rxy): Algorithm 1 run */
+/* again over the rx points, the surviving (x, ly) and (x, hy) of L, with  */
+/* the roles of x and y exchanged.  R is indexed by y, 0-based; entry      */
+/* y - 1 becomes (min x, max x) over the rx points with that y, or stays   */
+/* (p + 1, -1) (the square of side p, so q = p).  The rxy points are the   */
+/* (lo, y) and (hi, y) of the valid rows: a subset of the rx points that   */
+/* keeps every point extreme in its row, hence every hull vertex.          */
+/* ------------------------------------------------------------------------ */
+void oracle_reduce_rows(const int32_t *L, int32_t p, int32_t *R)
+{
+    for (int64_t i = 0; i < p; ++i) {
+        R[2 * i] = p + 1;
+        R[2 * i + 1] = -1;
+    }
+    for (int64_t i = 0; i < p; ++i) {
+        if (!entry_valid(L, p, i))
+            continue;
+        const int32_t x = (int32_t)(i + 1);
+        for (int k = 0; k < 2; ++k) {
+            const int32_t y = L[2 * i + k];
+            if (x < R[2 * (y - 1)])
+                R[2 * (y - 1)] = x;
+            if (x > R[2 * (y - 1) + 1])
+                R[2 * (y - 1) + 1] = x;
+        }
+    }
+}

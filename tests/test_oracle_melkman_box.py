@@ -171,3 +171,42 @@ def test_chain_points_equals_the_scan_of_L():
         lo2, up2 = oracle.chain(oracle.reduce(P, 70_000))
         np.testing.assert_array_equal(lo, lo2)
         np.testing.assert_array_equal(up, up2)
+
+
+def test_second_scan_on_fig1():
+    """Fig. 1's L: the rx points are (1,1) (1,4) (2,2) (2,4) (3,2) (3,5)
+    (4,3) (5,2) (5,3); scanning them along y keeps, per row, the leftmost
+    and rightmost: row 1 (1,1); row 2 x in {2,3,5}; row 3 x in {4,5}; row 4
+    x in {1,2}; row 5 (3,5).  One point, (3,2), goes; the pentagon stays."""
+    L = oracle.reduce(_fig1_points(), 5)
+    R = oracle.reduce_rows(L)
+    np.testing.assert_array_equal(R, [[1, 1], [2, 5], [4, 5], [1, 2], [3, 3]])
+    rxy = oracle.rxy_points(R)
+    assert rxy.shape[0] == 8 and oracle.rx_points(L).shape[0] == 9
+    np.testing.assert_array_equal(oracle.hull_points(rxy), [[1, 1], [5, 2], [5, 3], [3, 5], [1, 4]])
+
+
+def test_second_scan_is_algorithm1_on_the_transposed_rx_points():
+    """The second scan is Algorithm 1 over the rx points with x and y
+    exchanged; the rxy set is a subset of rx, at most min(2q, |rx|) points,
+    and keeps the hull (brute force)."""
+    for P, p in _tiny_sets(3000, seed=23):
+        L = oracle.reduce(P, p)
+        rx = oracle.rx_points(L)
+        R = oracle.reduce_rows(L)
+        np.testing.assert_array_equal(R, oracle.reduce(rx[:, ::-1], p))
+        rxy = oracle.rxy_points(R)
+        assert rxy.shape[0] <= min(2 * p, rx.shape[0])
+        assert set(map(tuple, rxy)) <= set(map(tuple, rx))
+        np.testing.assert_array_equal(oracle.hull_brute(rxy), oracle.hull_brute(P))
+    # full lattice square: rx is the top and bottom of every column, rxy the corners
+    p = 9
+    P = np.asarray([(x, y) for x in range(1, p + 1) for y in range(1, p + 1)], np.int32)
+    rxy = oracle.rxy_points(oracle.reduce_rows(oracle.reduce(P, p)))
+    np.testing.assert_array_equal(rxy, [[1, 1], [p, 1], [1, p], [p, p]])
+    for dist in ("disc", "shells"):
+        P = synth.points(dist, 300_000, 4096, seed=5)
+        L = oracle.reduce(P, 4096)
+        rxy = oracle.rxy_points(oracle.reduce_rows(L))
+        assert rxy.shape[0] < oracle.rx_points(L).shape[0]
+        np.testing.assert_array_equal(oracle.hull_points(rxy), oracle.hull_points(P))
