@@ -33,6 +33,10 @@ Other workloads (--workload):
             (ch_convex_hull_sparse) against the plain path (an array L of p
             entries) on the same inputs; plus, as in Fig. 11, both paths at
             column densities s/p of 5 % to 85 % (uniform x).
+  rxy       Algorithm 1 along x, then the second scan along y (Section 2,
+            Figs. 4 and 7) and the hull of the rxy points
+            (ch_convex_hull_rxy), against the plain path, on the
+            projected-shells stand-in; reports the rx and rxy counts.
   melkman   the paper's Melkman experiment (Section 3, Fig. 10) on the
             projected-shells stand-in (p = 4096, 10^7 points): Algorithm 1,
             the Lemma 1 polyline and Melkman's hull (ch_convex_hull_melkman)
@@ -217,9 +221,9 @@ def workload_config(workload):
                 "concurrency": "each instance on its own CUDA stream and workspace",
                 "l2": "points 8 MB per instance, below L2: a 256 MB write precedes every step "
                       "and its time is subtracted"}
-    if workload == "melkman":
+    if workload in ("melkman", "rxy"):
         p, n, dists = WORKLOADS[MELKMAN]
-        return {"workload": "melkman", "p": p, "n_per_instance": n, "distributions": list(dists),
+        return {"workload": workload, "p": p, "n_per_instance": n, "distributions": list(dists),
                 "instances_per_step": 1,
                 "l2": "80 MB of points, below L2 (129 MB): an L2 flush precedes every step"}
     if workload == "batched":
@@ -247,7 +251,7 @@ def _reference_units(workload):
     if workload == "sparse":
         p, n, dists = SPARSE
         return [(p, d, synth.points(d, n, p, seed=51 + i)) for i, d in enumerate(dists)]
-    p, n, inputs = gen_inputs(MELKMAN if workload == "melkman" else workload, 0)
+    p, n, inputs = gen_inputs(MELKMAN if workload in ("melkman", "rxy") else workload, 0)
     return [(p, d, P) for d, P in inputs]
 
 
@@ -260,6 +264,9 @@ def oracle_solver(workload):
         return lambda p, P: oracle.hull_box(P)
     if workload == "melkman":
         return lambda p, P: oracle.melkman(oracle.polyline(oracle.reduce(P, p)))
+    if workload == "rxy":
+        return lambda p, P: oracle.hull_points(oracle.rxy_points(oracle.reduce_rows(
+            oracle.reduce(P, p))))
     if workload == "sparse":  # the chains from the points (no array of p), then the hull
         def solve(p, P):
             oracle.chain_points(P)
@@ -977,41 +984,80 @@ def _cpu_rate(solve, problems, budget_s):
     return done / dt / 1e9, dt, passes
 
 
-def run_melkman(args):
-    """Algorithm 1 -> Lemma 1 polyline -> Melkman's hull, against the plain
-    path, on the projected-shells stand-in for the paper's scans."""
+def run_alt(args):
+    """One alternative form of the path against the plain path, on the
+    projected-shells stand-in for the paper's scans (p = 4096, 10^7 points):
+    `melkman` - Algorithm 1, the Lemma 1 polyline and Melkman's hull
+    (Section 3, Fig. 10); `rxy` - Algorithm 1 along x, the second scan along y
+    and the hull of the rxy points (Section 2, Figs. 4 and 7)."""
     torch, dist, world, rank = _setup_dist()
     from paper_1505_00914_gb300 import ch
     ch.lib()
+    alt = args.workload
     p, n, inputs = gen_inputs(MELKMAN, rank)
     P = inputs[0][1]
     d = torch.from_numpy(P).cuda()
     stream = torch.cuda.current_stream()
-    ws_m = torch.empty(ch.ch_convex_hull_melkman_workspace_size(n, p), dtype=torch.uint8, device="cuda")
+    if alt == "melkman":
+        ws_a = torch.empty(ch.ch_convex_hull_melkman_workspace_size(n, p), dtype=torch.uint8,
+                           device="cuda")
+    else:
+        ws_a = torch.empty(ch.ch_convex_hull_rxy_workspace_size(n, p), dtype=torch.uint8,
+                           device="cuda")
     ws_p = torch.empty(ch.ch_convex_hull_workspace_size(n, p), dtype=torch.uint8, device="cuda")
     poly = torch.empty((2 * p, 2), dtype=torch.int32, device="cuda")
     pc = torch.empty(1, dtype=torch.int32, device="cuda")
-    hm, hcm = torch.empty((2 * p, 2), dtype=torch.int32, device="cuda"), torch.empty(1, dtype=torch.int32, device="cuda")
+    La = torch.empty((p, 2), dtype=torch.int32, device="cuda")
+    Ra = torch.empty((p, 2), dtype=torch.int32, device="cuda")
+    ha, hca = torch.empty((2 * p, 2), dtype=torch.int32, device="cuda"), torch.empty(1, dtype=torch.int32, device="cuda")
     hp, hcp = torch.empty((2 * p, 2), dtype=torch.int32, device="cuda"), torch.empty(1, dtype=torch.int32, device="cuda")
     # the input (80 MB) fits in L2: each step starts after a 256 MB write
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
+    def run_alt_once():
+        if alt == "melkman":
+            ch.ch_convex_hull_melkman(d, p, poly=poly, poly_count=pc, hull=ha, hull_count=hca,
+                                      workspace=ws_a, stream=stream)
+        else:
+            ch.ch_convex_hull_rxy(d, p, L=La, R=Ra, hull=ha, hull_count=hca, workspace=ws_a,
+                                  stream=stream)
+
     def step(arm):
         flush.zero_()
-        if arm == "melkman":
-            ch.ch_convex_hull_melkman(d, p, poly=poly, poly_count=pc, hull=hm, hull_count=hcm,
-                                      workspace=ws_m, stream=stream)
+        if arm == alt:
+            run_alt_once()
         else:
             ch.ch_convex_hull(d, p, hull=hp, hull_count=hcp, workspace=ws_p, stream=stream)
 
-    for arm in ("melkman", "plain"):
+    for arm in (alt, "plain"):
         for _ in range(args.warmup):
             step(arm)
     torch.cuda.synchronize()
     rc = ch.ch_sync_status()
     if rc != ch.CH_OK:
         raise RuntimeError(f"warm-up failed: {ch.strerror(rc)}")
-    same = bool(torch.equal(hm[: int(hcm.item())].cpu(), hp[: int(hcp.item())].cpu()))
+    same = bool(torch.equal(ha[: int(hca.item())].cpu(), hp[: int(hcp.item())].cpu()))
+    detail = {}
+    if alt == "melkman":
+        # the paper's exact pipeline as well: the full Lemma 1 polyline
+        # (ch_polyline) and Melkman on it (ch_hull_melkman)
+        L1 = ch.ch_reduce(d, p)
+        full, fc = ch.ch_polyline(L1, p)
+        ws_m = ch.ch_hull_melkman_workspace_size(p)
+        wsm = torch.empty(max(ws_m, 1), dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            ch.ch_hull_melkman(full, fc, p, workspace=wsm, stream=stream)
+        t = _timed(torch, dist, world, lambda: ch.ch_hull_melkman(full, fc, p, workspace=wsm,
+                                                                  stream=stream), 5, stream)
+        detail = {"polyline_vertices": int(fc.item()),
+                  "polyline_vertices_after_prefilter": int(pc.item()),
+                  "melkman_ms_on_full_polyline": t / 5}
+    else:
+        Lh, Rh = La.cpu().numpy(), Ra.cpu().numpy()
+        vl = ~((Lh[:, 0] == p + 1) & (Lh[:, 1] == -1))
+        vr = ~((Rh[:, 0] == p + 1) & (Rh[:, 1] == -1))
+        detail = {"rx": int(vl.sum() + (vl & (Lh[:, 0] != Lh[:, 1])).sum()),
+                  "rxy": int(vr.sum() + (vr & (Rh[:, 0] != Rh[:, 1])).sum())}
     fl = _timed(torch, dist, world, lambda: flush.zero_(), args.steps, stream)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
@@ -1023,9 +1069,9 @@ def run_melkman(args):
     sampler.start()
     time.sleep(0.3)
     ms = {arm: _timed(torch, dist, world, lambda arm=arm: step(arm), args.steps, stream) - fl
-          for arm in ("melkman", "plain")}
+          for arm in (alt, "plain")}
     ch.ch_trace_set(evs)
-    ms_traced = _timed(torch, dist, world, lambda: step("melkman"), args.steps, stream) - fl
+    ms_traced = _timed(torch, dist, world, lambda: step(alt), args.steps, stream) - fl
     ch.ch_trace_set([])
     clocks = sampler.stop()
     rc = ch.ch_sync_status()
@@ -1042,10 +1088,9 @@ def run_melkman(args):
     w0 = time.perf_counter()
     for _ in range(e2e_steps):
         d.copy_(host_in, non_blocking=True)
-        ch.ch_convex_hull_melkman(d, p, poly=poly, poly_count=pc, hull=hm, hull_count=hcm,
-                                  workspace=ws_m, stream=stream)
-        k = int(hcm.item())
-        hh[:k].copy_(hm[:k])
+        run_alt_once()
+        k = int(hca.item())
+        hh[:k].copy_(ha[:k])
         d2h += 4 + 8 * k
     e2e_s = _max_over_ranks(torch, dist, world, time.perf_counter() - w0)
     if rank != 0:
@@ -1056,20 +1101,22 @@ def run_melkman(args):
     kname = KERNEL_OF_FORM[ch.ch_plan_info(n, p)[0]]
     kernel_bytes = 8 * n + 8 * p
     achieved = kernel_bytes / (red_avg / 1e3) / 1e9
-    cpu_v, cpu_dt, cpu_passes = _cpu_rate(oracle_solver("melkman"), [(p, P)], args.cpu_budget)
-    nk = ch.ch_plan_info(n, p)[1] - 2 + 2  # reduce kernels + polyline + Melkman
+    cpu_v, cpu_dt, cpu_passes = _cpu_rate(oracle_solver(alt), [(p, P)], args.cpu_budget)
+    # reduce kernels + (polyline, Melkman) or (fill, row scan, chain, final, unframe)
+    nk = ch.ch_plan_info(n, p)[1] - 2 + (2 if alt == "melkman" else 5)
+    what = {"melkman": "Algorithm 1 + polyline + Melkman",
+            "rxy": "Algorithm 1 + second scan + hull"}[alt]
     line = {
-        "metric": METRIC, "value": rate["melkman"], "unit": "Gpoints/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms["melkman"] / args.steps,
+        "metric": METRIC, "value": rate[alt], "unit": "Gpoints/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms[alt] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "config": workload_config("melkman"),
-        "melkman": {"plain_gpoints_s": rate["plain"],
-                    "ms_per_step": {a: t / args.steps for a, t in ms.items()},
-                    "reduction_ms": red_avg,
-                    "after_reduction_ms": ms_traced / args.steps - red_avg,
-                    "polyline_vertices": int(pc.item()), "hull_vertices": int(hcm.item()),
-                    "hulls_identical": same,
-                    "l2_flush_ms_subtracted": fl / args.steps},
+        "data": "synthetic", "config": workload_config(alt),
+        alt: dict({"plain_gpoints_s": rate["plain"],
+                   "ms_per_step": {a: t / args.steps for a, t in ms.items()},
+                   "reduction_ms": red_avg,
+                   "after_reduction_ms": ms_traced / args.steps - red_avg,
+                   "hull_vertices": int(hca.item()), "hulls_identical": same,
+                   "l2_flush_ms_subtracted": fl / args.steps}, **detail),
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "algorithmic_bytes_per_launch": kernel_bytes, "avg_launch_ms": red_avg,
@@ -1079,7 +1126,7 @@ def run_melkman(args):
                 "steps": e2e_steps},
         "cpu_baseline": {"value": cpu_v, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
                          "sample": f"{cpu_passes} pass(es) over the instance ({cpu_dt:.1f} s, "
-                                   f"single thread, Algorithm 1 + polyline + Melkman)"},
+                                   f"single thread, {what})"},
         "gpu_launches": args.steps * nk,
         "clocks": clocks,
     }
@@ -1252,7 +1299,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["learned", "batched", "box",
-                                                                "melkman", "sparse"],
+                                                                "melkman", "rxy", "sparse"],
                     default="plain_at_scale")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
@@ -1266,8 +1313,8 @@ def main():
         run_batched(args)
     elif args.workload == "box":
         run_box(args)
-    elif args.workload == "melkman":
-        run_melkman(args)
+    elif args.workload in ("melkman", "rxy"):
+        run_alt(args)
     elif args.workload == "sparse":
         run_sparse(args)
     else:

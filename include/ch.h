@@ -236,6 +236,29 @@ int ch_convex_hull_sparse(const int32_t *pts, int64_t n, int32_t p, int32_t *low
                           void *workspace, size_t ws_bytes, ch_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
+/* The second scan along y (Section 2, Fig. 4: rx -> rxy).                 */
+/* ---------------------------------------------------------------------- */
+
+/* From L (int32[p][2], as written by ch_reduce): Algorithm 1 once more over
+ * its rx points - the valid (x, ly) and (x, hy) - with x and y exchanged.
+ * R: int32[p][2], written in full; row y (1-based) at R[2(y-1)] = min x,
+ * R[2(y-1)+1] = max x over the rx points with that y, (p+1, -1) for none.
+ * The rxy points are the (min x, y) and (max x, y) of the valid rows: a
+ * subset of rx that keeps every hull vertex.  An entry of L outside
+ * 1 <= ly <= hy <= p (other than the empty one) is skipped and recorded as
+ * CH_ERR_RANGE. */
+int ch_reduce_rows(const int32_t *L, int32_t p, int32_t *R, ch_stream_t stream);
+
+int ch_convex_hull_rxy_workspace_size(int64_t n, int32_t p, size_t *bytes);
+
+/* ch_reduce, ch_reduce_rows, then the chains and hull of the rxy points (the
+ * plain path's kernels in the transposed frame, the hull mapped back).  L and
+ * R may be NULL (the workspace holds them).  Same hull as ch_convex_hull. */
+int ch_convex_hull_rxy(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t *R,
+                       int32_t *hull, int32_t *hull_count, void *workspace, size_t ws_bytes,
+                       ch_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
 /* Many independent sets in one persistent launch (the three steps per     */
 /* set, Section 2.1).                                                      */
 /* ---------------------------------------------------------------------- */

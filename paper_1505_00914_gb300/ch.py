@@ -84,6 +84,9 @@ def _declare(lib):
         "ch_sparse_workspace_size": (ctypes.c_int, [i64, i32, szp, szp]),
         "ch_sparse_kernel_count": (ctypes.c_int, [i64, i32, ctypes.POINTER(i32)]),
         "ch_convex_hull_sparse": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, sz, P]),
+        "ch_reduce_rows": (ctypes.c_int, [P, i32, P, P]),
+        "ch_convex_hull_rxy_workspace_size": (ctypes.c_int, [i64, i32, szp]),
+        "ch_convex_hull_rxy": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, sz, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -398,6 +401,37 @@ def ch_convex_hull_sparse(pts, p: int, workspace, lower=None, upper=None, counts
     _check(lib().ch_convex_hull_sparse(_ptr(pts), n, int(p), _ptr(lower), _ptr(upper), _ptr(counts),
                                        _ptr(hull), _ptr(hull_count), _ptr(workspace),
                                        workspace.numel(), _stream(stream)), "ch_convex_hull_sparse")
+    return hull, hull_count
+
+
+def ch_reduce_rows(L, p: int | None = None, R=None, stream=None):
+    """The second scan along y over the rx points of L: R (p, 2)."""
+    dev = _dev(L)
+    p = int(L.shape[0] if p is None else p)
+    if R is None:
+        R = torch.empty((p, 2), dtype=torch.int32, device=dev)
+    _check(lib().ch_reduce_rows(_ptr(L), p, _ptr(R), _stream(stream)), "ch_reduce_rows")
+    return R
+
+
+def ch_convex_hull_rxy_workspace_size(n: int, p: int) -> int:
+    return _size(lib().ch_convex_hull_rxy_workspace_size, int(n), int(p))
+
+
+def ch_convex_hull_rxy(pts, p: int, L=None, R=None, hull=None, hull_count=None, workspace=None,
+                       stream=None):
+    """Algorithm 1 along x, the second scan along y, the hull of the rxy
+    points; returns (hull, hull_count)."""
+    pts = _pts(pts)
+    dev = _dev(pts)
+    if hull is None:
+        hull = torch.empty((2 * p, 2), dtype=torch.int32, device=dev)
+    if hull_count is None:
+        hull_count = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = _ws(ch_convex_hull_rxy_workspace_size(pts.shape[0], p), dev, workspace)
+    _check(lib().ch_convex_hull_rxy(_ptr(pts), pts.shape[0], int(p), _ptr(L), _ptr(R), _ptr(hull),
+                                    _ptr(hull_count), _ptr(ws), ws.numel(), _stream(stream)),
+           "ch_convex_hull_rxy")
     return hull, hull_count
 
 

@@ -979,4 +979,97 @@ int ch_convex_hull_sparse(const int32_t *pts, int64_t n, int32_t p, int32_t *low
                                  st, reinterpret_cast<cudaStream_t>(stream), ev0, ev1));
 }
 
+// ---- the second scan along y (rx -> rxy) ----
+
+int ch_reduce_rows(const int32_t *L, int32_t p, int32_t *R, ch_stream_t stream)
+{
+    if (p < 1 || p > CH_MAX_P || !L || !R || !aligned8(L) || !aligned8(R))
+        return CH_ERR_ARG;
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    return cuda_rc(rows_launch(L, p, R, st, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+namespace {
+struct RxyWs {
+    PathWs path;
+    size_t R, hull_t, count_t, end;
+};
+int rxy_layout(int64_t n, int p, RxyWs *w)
+{
+    int rc = path_layout(n, p, &w->path);
+    if (rc != CH_OK)
+        return rc;
+    WsLayout l;
+    l.off = w->path.end;
+    w->R = l.take((size_t)p * 8);
+    w->hull_t = l.take((size_t)p * 16);
+    w->count_t = l.take(8);
+    w->end = l.off;
+    return CH_OK;
+}
+}  // namespace
+
+int ch_convex_hull_rxy_workspace_size(int64_t n, int32_t p, size_t *bytes)
+{
+    if (!bytes || check_np(n, p) != CH_OK)
+        return CH_ERR_ARG;
+    RxyWs w;
+    const int rc = rxy_layout(n, p, &w);
+    if (rc != CH_OK)
+        return rc;
+    *bytes = w.end;
+    return CH_OK;
+}
+
+int ch_convex_hull_rxy(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t *R,
+                       int32_t *hull, int32_t *hull_count, void *workspace, size_t ws_bytes,
+                       ch_stream_t stream)
+{
+    if (check_np(n, p) != CH_OK || (n > 0 && !pts) || !hull || !hull_count || !aligned8(pts) ||
+        !aligned8(L) || !aligned8(R) || !aligned8(hull))
+        return CH_ERR_ARG;
+    RxyWs w;
+    int rc = rxy_layout(n, p, &w);
+    if (rc != CH_OK)
+        return rc;
+    if (ws_bytes < w.end || !workspace)
+        return CH_ERR_WORKSPACE;
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *b = reinterpret_cast<char *>(workspace);
+    const PathWs &pw = w.path;
+    if (!L)
+        L = reinterpret_cast<int32_t *>(b + pw.L);
+    if (!R)
+        R = reinterpret_cast<int32_t *>(b + w.R);
+    cudaEvent_t ev0, ev1;
+    next_trace(&ev0, &ev1);
+    cudaError_t e = reduce_launch(pw.plan, pts, n, square_frame(p), b + pw.part, L, st, s, nullptr,
+                                  0, ev0, ev1);
+    if (e == cudaSuccess && pw.plan.mode == 0)
+        e = reduce_merge_launch(b + pw.part, pw.plan.copies, p, p, L, s);
+    if (e == cudaSuccess)
+        e = rows_launch(L, p, R, st, s);
+    // the rxy points as chains along y: the transposed frame of the plain path
+    const HullLayout hl = hull_layout(p);
+    char *hw = b + pw.hull;
+    int32_t *hull_t = reinterpret_cast<int32_t *>(b + w.hull_t);
+    int32_t *count_t = reinterpret_cast<int32_t *>(b + w.count_t);
+    if (e == cudaSuccess)
+        e = chain_launch(R, p, reinterpret_cast<int32_t *>(b + pw.lower),
+                         reinterpret_cast<int32_t *>(b + pw.upper),
+                         reinterpret_cast<int32_t *>(b + pw.counts), nullptr, b + pw.state, false,
+                         reinterpret_cast<int2 *>(hw + hl.cand), reinterpret_cast<int *>(hw + hl.ccnt),
+                         st, s);
+    if (e == cudaSuccess)
+        e = hull_final_launch(hl, hw, hull_t, count_t, s);
+    if (e == cudaSuccess)
+        e = unframe_launch(hull_t, count_t, Frame{1, 1, p, p, 1}, hull, hull_count, s);
+    return cuda_rc(e);
+}
+
 }  // extern "C"

@@ -256,6 +256,11 @@ cudaError_t sparse_launch(const SparseLayout &L, const int32_t *pts, int64_t n, 
                           cudaEvent_t ev1);
 int sparse_kernel_count(const SparseLayout &L);
 
+// ---- second scan along y (rows.cu) ----
+// R (int32[p][2]) = Algorithm 1 along y over the rx points of L; an entry
+// of L that no in-range input can produce is skipped as CH_ERR_RANGE.
+cudaError_t rows_launch(const int32_t *L, int p, int32_t *R, unsigned *status, cudaStream_t s);
+
 // ---- api.cu ----
 unsigned *device_status_ptr();  // this device's status word (nullptr on failure)
 int sm_count();

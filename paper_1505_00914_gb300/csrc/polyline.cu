@@ -167,11 +167,23 @@ __device__ __forceinline__ unsigned long long lex_key(int2 q)
            (unsigned long long)((unsigned)q.y ^ 0x80000000u);
 }
 
+// Orientation of (o, a, b) in 32-bit arithmetic when every coordinate lies
+// in [1, 2^15]: each product is below 2^30 in magnitude and their difference
+// below 2^31, so the sign is exact; else in 64-bit arithmetic.
+template <bool SMALL>
+__device__ __forceinline__ long long orient(int2 o, int2 a, int2 b)
+{
+    if constexpr (SMALL)
+        return (a.x - o.x) * (b.y - o.y) - (a.y - o.y) * (b.x - o.x);
+    else
+        return cross3(o, a, b);
+}
+
 // poly: *count vertices of a simple polyline, distinct, in [1, p]^2.
 // GDQ: the deque is dq_global (it does not fit in shared memory), else it
 // follows the staging buffer in shared memory; dq_cap: its capacity (a power
 // of two above the largest hull plus one).
-template <bool GDQ>
+template <bool GDQ, bool SMALL>
 __global__ void __launch_bounds__(32)
     k_melkman(const int2 *__restrict__ poly, const int *count, int p, int2 *dq_global,
               unsigned dq_cap, int2 *hull, int *hull_count, unsigned *status)
@@ -215,7 +227,7 @@ __global__ void __launch_bounds__(32)
                     k = 1;
                     continue;
                 }
-                const long long o = cross3(a, b, u);
+                const long long o = orient<SMALL>(a, b, u);
                 if (k >= 2 && o != 0) {
                     // the first vertex off the prefix's line: the deque starts
                     // as the counter-clockwise triangle (u, a, b) or (u, b, a)
@@ -247,7 +259,7 @@ __global__ void __launch_bounds__(32)
                 bool out = false;
                 if (j < cnt) {
                     const int2 u = stage[j];
-                    out = !(cross3(t1, t0, u) >= 0 && cross3(b0, b1, u) >= 0);
+                    out = !(orient<SMALL>(t1, t0, u) >= 0 && orient<SMALL>(b0, b1, u) >= 0);
                 }
                 const unsigned ob = __ballot_sync(FULL, out);
                 if (!ob) {
@@ -258,7 +270,7 @@ __global__ void __launch_bounds__(32)
                 const int2 u = stage[i];
                 ++i;
                 // top: pop while u is not strictly left of the top edge
-                while (top - bot > 1 && cross3(t1, t0, u) <= 0) {
+                while (top - bot > 1 && orient<SMALL>(t1, t0, u) <= 0) {
                     --top;
                     t0 = t1;
                     t1 = dq[(unsigned)(top - 1) & mask];
@@ -272,7 +284,7 @@ __global__ void __launch_bounds__(32)
                 t1 = t0;
                 t0 = u;
                 // bottom: pop while (u, D[bot], D[bot+1]) is not a strict left turn
-                while (top - bot > 1 && cross3(u, b0, b1) <= 0) {
+                while (top - bot > 1 && orient<SMALL>(u, b0, b1) <= 0) {
                     ++bot;
                     b0 = b1;
                     b1 = dq[(unsigned)(bot + 1) & mask];
@@ -351,9 +363,12 @@ cudaError_t set_melkman_smem()
     if (dev < 0 || dev >= 64)
         return cudaErrorInvalidDevice;
     if (!done[dev]) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            k_melkman<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-            (int)((MK_STAGE + MK_SMEM_MAX_DQ) * sizeof(int2)));
+        const int bytes = (int)((MK_STAGE + MK_SMEM_MAX_DQ) * sizeof(int2));
+        cudaError_t e = cudaFuncSetAttribute(k_melkman<false, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_melkman<false, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess)
             return e;
         done[dev] = true;
@@ -422,7 +437,10 @@ cudaError_t melkman_launch(const int32_t *poly, const int32_t *count, int p, int
     const size_t cap = melkman_deque_cap(p);
     const bool in_smem = cap <= MK_SMEM_MAX_DQ;
     const size_t smem = (MK_STAGE + (in_smem ? cap : 0)) * sizeof(int2);
-    launch(in_smem ? k_melkman<false> : k_melkman<true>, 1, 32, smem, s,
+    const bool small = p <= (1 << 15);
+    launch(in_smem ? (small ? k_melkman<false, true> : k_melkman<false, false>)
+                   : k_melkman<true, false>,
+           1, 32, smem, s,
            reinterpret_cast<const int2 *>(poly), count, p,
            in_smem ? nullptr : reinterpret_cast<int2 *>(ws), (unsigned)cap,
            reinterpret_cast<int2 *>(hull), hull_count, status);

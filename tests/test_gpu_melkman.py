@@ -208,3 +208,21 @@ def test_melkman_path_full_size(dist):
     del P
     h, hc = ch.ch_convex_hull_melkman(d, p)
     np.testing.assert_array_equal(host(h)[: int(host(hc)[0])], H)
+
+
+@pytest.mark.parametrize("p", [32768, 32769])
+def test_full_scale_coordinates_at_the_32_bit_boundary(p):
+    """Up to p = 2^15 the orientation runs in 32-bit arithmetic; polylines
+    spanning the whole square, with near-collinear triples, at both sides of
+    that boundary."""
+    rng = np.random.default_rng(p)
+    for m in (50, 4000):
+        poly = star(rng, m, (p - 2) // 2, p)
+        np.testing.assert_array_equal(gpu_melkman(poly, p), oracle.hull_points(poly))
+    # long thin fans: every triple nearly collinear over the full width
+    xs = np.arange(1, p + 1, 97)
+    lo = np.stack([xs, 1 + (xs * 3) // p], 1)
+    hi = np.stack([xs[::-1], p - (xs[::-1] * 5) // p], 1)
+    poly = np.concatenate([lo, hi]).astype(np.int32)
+    np.testing.assert_array_equal(oracle.melkman(poly), oracle.hull_points(poly))
+    np.testing.assert_array_equal(gpu_melkman(poly, p), oracle.hull_points(poly))
