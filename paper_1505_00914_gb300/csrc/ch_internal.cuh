@@ -155,7 +155,8 @@ cudaError_t chain_launch(const int32_t *L, int p, int32_t *lower, int32_t *upper
 // ---- hull (hull.cu) ----
 struct HullLayout {
     int nblk;  // runs of 1024 chain points (or chain tiles) per chain
-    size_t cand, ccnt, gA, gB, gF, gix, end;
+    bool refilter;  // survivors filtered a second time before the final CTA
+    size_t cand, ccnt, gA, gB, gF, gix, ccnt2, counts2, state2, end;
 };
 HullLayout hull_layout(int p);
 size_t hull_ws_bytes(int p);

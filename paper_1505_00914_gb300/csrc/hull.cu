@@ -27,6 +27,7 @@
 #include "ch_internal.cuh"
 #include "hull_filter.cuh"
 #include "hull_merge.cuh"
+#include "lookback.cuh"
 
 namespace ch {
 namespace {
@@ -61,6 +62,67 @@ __global__ void __launch_bounds__(RUN)
     const int n = compact_run(P, keep, cand + (size_t)blockIdx.x * RUN, s_wc);
     if (threadIdx.x == 0)
         ccnt[blockIdx.x] = n;
+}
+
+// With many runs (long chains: large p or sparse data) the survivors are
+// filtered once more before the final CTA: they are packed per chain
+// (k_cand_compact: one warp per run, the runs' offsets by a look-back over
+// tiles of 32 runs, the upper chain un-mirrored) and go through
+// k_hull_filter again as chains of their own.  A point the second pass drops
+// lies on or above a segment between two other points, as in the first, so
+// every drop stays exact; the final CTA then sees a few survivors per 1024
+// instead of the local hulls of every run.
+constexpr int REFILTER_MIN_BLK = 128;  // runs per chain from which the second pass runs
+
+__global__ void __launch_bounds__(1024)
+    k_cand_compact(const int2 *__restrict__ cand, const int *__restrict__ ccnt, int nblk, int2 *out,
+                   int *counts2, unsigned long long *state, int ntile, unsigned *status)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int chain = blockIdx.y;
+    unsigned long long *st = state + (size_t)chain * (ntile + 1);
+    __shared__ int s_tile;
+    __shared__ int s_off[32];
+    __shared__ long long s_prefix;
+    if (threadIdx.x == 0)
+        s_tile = (int)atomicAdd(st, 1ull);
+    __syncthreads();
+    const int tile = s_tile, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        const int r = tile * 32 + lane;
+        const int v = r < nblk ? ccnt[(size_t)chain * nblk + r] : 0;
+        int inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o)
+                inc += x;
+        }
+        s_off[lane] = inc - v;
+        const int tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+        if (lane == 0)
+            publish_aggregate(st + 1, tile, tot);
+        const long long pre = warp_look_back(st + 1, tile, tot, lane, status);
+        if (lane == 0) {
+            s_prefix = pre;
+            if (tile == ntile - 1)
+                counts2[chain] = (int)(pre + tot);
+        }
+    }
+    __syncthreads();
+    const int run = tile * 32 + warp;
+    if (run >= nblk)
+        return;
+    const int len = ccnt[(size_t)chain * nblk + run];
+    const int2 *src = cand + ((size_t)chain * nblk + run) * RUN;
+    int2 *dst = out + (size_t)chain * nblk * RUN + s_prefix + s_off[warp];
+    for (int k = lane; k < len; k += 32) {
+        int2 q = src[k];
+        if (chain)
+            q.y = -q.y;
+        dst[k] = q;
+    }
 }
 
 // The final CTA: gathers the survivors of every run (chain 0 first) into A,
@@ -141,6 +203,12 @@ HullLayout hull_layout(int p)
     h.gB = w.take(cap * sizeof(int2));
     h.gF = w.take(cap * sizeof(int));
     h.gix = w.take((2 * nblk + 1 + 4 * (cap / HS + 2)) * sizeof(int));
+    // second pass (packed survivors in gA, its survivors in gB)
+    h.refilter = nblk >= (size_t)REFILTER_MIN_BLK;
+    const size_t ntile = (nblk + 31) / 32;
+    h.ccnt2 = w.take(h.refilter ? 2 * nblk * sizeof(int) : 0);
+    h.counts2 = w.take(h.refilter ? 8 : 0);
+    h.state2 = w.take(h.refilter ? 2 * (ntile + 1) * 8 : 0);
     h.end = w.off;
     return h;
 }
@@ -175,8 +243,31 @@ cudaError_t hull_final_launch(const HullLayout &h, void *ws, int32_t *hull, int3
     if (e != cudaSuccess)
         return e;
     char *b = reinterpret_cast<char *>(ws);
+    size_t cand = h.cand, ccnt = h.ccnt;
+    if (h.refilter) {
+        unsigned *status = device_status_ptr();
+        if (!status)
+            return cudaErrorUnknown;
+        const int ntile = (h.nblk + 31) / 32;
+        e = cudaMemsetAsync(b + h.state2, 0, (size_t)2 * (ntile + 1) * 8, s);
+        if (e != cudaSuccess)
+            return e;
+        int2 *packed = reinterpret_cast<int2 *>(b + h.gA);
+        int *counts2 = reinterpret_cast<int *>(b + h.counts2);
+        launch(k_cand_compact, dim3(ntile, 2), 1024, 0, s, reinterpret_cast<const int2 *>(b + h.cand),
+               reinterpret_cast<const int *>(b + h.ccnt), h.nblk, packed, counts2,
+               reinterpret_cast<unsigned long long *>(b + h.state2), ntile, status);
+        const size_t half = (size_t)h.nblk * RUN;
+        launch(k_hull_filter, 2 * h.nblk, RUN, 0, s, (const int2 *)packed, (const int2 *)(packed + half),
+               (const int *)counts2, (int)half, h.nblk, reinterpret_cast<int2 *>(b + h.gB),
+               reinterpret_cast<int *>(b + h.ccnt2));
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+        cand = h.gB;  // gathered by the final CTA before it reuses gB
+        ccnt = h.ccnt2;
+    }
     launch(k_hull_final, 1, FT, FINAL_SMEM, s,
-        reinterpret_cast<const int2 *>(b + h.cand), reinterpret_cast<const int *>(b + h.ccnt), h.nblk,
+        reinterpret_cast<const int2 *>(b + cand), reinterpret_cast<const int *>(b + ccnt), h.nblk,
         reinterpret_cast<int2 *>(b + h.gA), reinterpret_cast<int2 *>(b + h.gB),
         reinterpret_cast<int *>(b + h.gF), reinterpret_cast<int *>(b + h.gix),
         reinterpret_cast<int2 *>(hull), hull_count);

@@ -226,3 +226,27 @@ def test_projected_shells_full_size():
     p = 4096
     P = synth.shells(10_000_000, p, seed=3)
     check_against_oracle(P, p)
+
+
+@pytest.mark.parametrize("p", [131071, 131072, 262145, 1 << 20, 1 << 22])
+def test_long_chains_second_filter_pass(p):
+    """From 128 runs of 1024 columns per chain on, the survivors of the
+    in-tile filter are packed and filtered again before the final CTA: sparse
+    and dense uniform sets, a disc, and a circle whose every column holds a
+    hull vertex region."""
+    rng = np.random.default_rng(p)
+    sets = [rng.integers(1, p + 1, size=(200_000, 2)),
+            synth.points("uniform", 3_000_000, p, seed=1),
+            synth.points("disc", 2_000_000, p, seed=2)]
+    t = np.linspace(0, 2 * np.pi, 400_000, endpoint=False)
+    r = (p - 3) / 2
+    circ = np.stack([(p + 1) / 2 + r * np.cos(t), (p + 1) / 2 + r * np.sin(t)], 1)
+    sets.append(np.clip(np.rint(circ), 1, p))
+    for P in sets:
+        P = np.ascontiguousarray(P, dtype=np.int32)
+        H = oracle.hull_points(P)
+        h, hc = ch.ch_convex_hull(dev(P).reshape(-1, 2), p)
+        np.testing.assert_array_equal(host(h)[: int(host(hc)[0])], H)
+        lo, up, cnt = ch.ch_chain(ch.ch_reduce(dev(P).reshape(-1, 2), p), p)
+        h2, hc2 = ch.ch_hull(lo, up, cnt, p)
+        np.testing.assert_array_equal(host(h2)[: int(host(hc2)[0])], H)
