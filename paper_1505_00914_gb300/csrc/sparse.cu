@@ -19,8 +19,9 @@
 //                  from zero to non-zero.
 // k_tree_expand    level k -> level k - 1, top down: the list of non-empty
 //                  words of level k (increasing index) becomes the list of
-//                  non-empty words of level k - 1, each word's set bits taken
-//                  in order by the ctz walk of Table I; a compaction with one
+//                  non-empty words of level k - 1, each word's set bits in
+//                  increasing order (the positions the ctz walk of Table I
+//                  visits, ranked by 32 lanes at once); a compaction with one
 //                  look-back pass.  The words it read are cleared.
 //                  Its leaf form takes the non-empty words of level 0 to
 //                  the lower and upper chains in increasing x (Lemma 1),
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(SP_RED_T)
         atomicOr(status, ST_RANGE);
 }
 
-// Block-wide exclusive scan of v over SP_T threads; returns the block total
+// Block-wide exclusive scan of v over the SP_T threads of a CTA; returns the block total
 // in *tot (all threads).
 __device__ __forceinline__ int block_excl_scan(int v, int *s_w, int *tot)
 {
@@ -124,15 +125,22 @@ __device__ __forceinline__ int block_excl_scan(int v, int *s_w, int *tot)
     return s_w[w] + incl - v;
 }
 
+constexpr int XW = 8;             // list words per warp
+constexpr int XT = 32 * XW;       // list words per tile (a CTA of 32 warps)
+
 // LEAF = false: in = non-empty words of level k (top: the single word 0),
 // out = non-empty words of level k - 1.  LEAF = true: in = non-empty words of
-// level 0, out = the chains.
+// level 0, out = the chains.  A warp takes XW consecutive words of the list;
+// lane b speaks for bit b of each, so the children of a word are ranked by
+// popc of the lower bits (the ctz walk of Table I, done by 32 lanes at once)
+// and a leaf word's 32 entries of Lz are read and cleared as one coalesced
+// 256-byte access.
 // in_cap, out_cap: capacities of the two lists (out: of the chains for LEAF);
 // child_limit: words of level k - 1 (LEAF: p).  With a workspace that was
 // zero-filled as required none of them is ever reached; otherwise the
 // excess is dropped and recorded as CH_ERR_CAPACITY instead of written.
 template <bool LEAF>
-__global__ void __launch_bounds__(SP_T)
+__global__ void __launch_bounds__(1024)
     k_tree_expand(uint32_t *Mk, const int *__restrict__ in, const int *in_cnt, int top, int *out,
                   int *out_cnt, int2 *Lz, int2 *lower, int2 *upper, int *counts,
                   unsigned long long *state, int in_cap, int out_cap, int child_limit,
@@ -148,18 +156,42 @@ __global__ void __launch_bounds__(SP_T)
     __syncthreads();
     const int tile = s_tile;
     const int cnt = top ? 1 : min(*in_cnt, in_cap);
-    const int ntiles = (cnt + SP_T - 1) / SP_T;
+    const int ntiles = (cnt + XT - 1) / XT;
     if (tile >= max(ntiles, 1))
         return;  // a later ticket: nothing waits on it
-    const int i = tile * SP_T + threadIdx.x;
-    const int idx = i < cnt ? (top ? 0 : in[i]) : -1;
-    uint32_t word = 0;
-    if (idx >= 0) {
-        word = Mk[idx];
-        Mk[idx] = 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w0 = tile * XT + warp * XW;  // this warp's first list position
+    int my_idx = -1;
+    uint32_t my_word = 0;
+    if (lane < XW && w0 + lane < cnt) {
+        my_idx = top ? 0 : in[w0 + lane];
+        my_word = Mk[my_idx];
+        Mk[my_idx] = 0;
+    }
+    int idx[XW];
+    uint32_t word[XW];
+    int wtot = 0;
+#pragma unroll
+    for (int k = 0; k < XW; ++k) {
+        idx[k] = __shfl_sync(FULL, my_idx, k);
+        word[k] = __shfl_sync(FULL, my_word, k);
+        wtot += __popc(word[k]);
+    }
+    int2 e[XW];
+    if constexpr (LEAF) {
+#pragma unroll
+        for (int k = 0; k < XW; ++k) {
+            const int child = idx[k] * 32 + lane;
+            e[k] = make_int2(0, 0);
+            if (((word[k] >> lane) & 1u) && child < child_limit) {
+                e[k] = Lz[child];
+                Lz[child] = make_int2(0, 0);
+            }
+        }
     }
     int tot;
-    const int excl = block_excl_scan(__popc(word), s_w, &tot);
+    const int wexcl = block_excl_scan(lane == 0 ? wtot : 0, s_w, &tot);
+    const int woff = __shfl_sync(FULL, wexcl, 0);
     if (threadIdx.x == 0)
         publish_aggregate(state + 1, tile, tot);
     if (threadIdx.x < 32) {
@@ -180,28 +212,26 @@ __global__ void __launch_bounds__(SP_T)
         }
     }
     __syncthreads();
-    long long pos = s_prefix + excl;
-    // the set bits of the word in increasing order: pos = ctz(x); x ^= 1 << pos
+    long long run = s_prefix + woff;
+    const unsigned below = (1u << lane) - 1u;
     bool over = false;
-    while (word) {
-        const int b = __ffs(word) - 1;
-        word ^= 1u << b;
-        const int child = idx * 32 + b;
-        if (pos >= out_cap || child >= child_limit) {
-            over = true;
-            break;
+#pragma unroll
+    for (int k = 0; k < XW; ++k) {
+        if ((word[k] >> lane) & 1u) {
+            const long long pos = run + __popc(word[k] & below);
+            const int child = idx[k] * 32 + lane;
+            if (pos >= out_cap || child >= child_limit) {
+                over = true;
+            } else if (LEAF) {
+                lower[pos] = make_int2(child + 1, INT_MAX - e[k].x);
+                upper[pos] = make_int2(child + 1, e[k].y);
+            } else {
+                out[pos] = child;
+            }
         }
-        if (LEAF) {
-            const int2 e = Lz[child];
-            Lz[child] = make_int2(0, 0);
-            lower[pos] = make_int2(child + 1, INT_MAX - e.x);
-            upper[pos] = make_int2(child + 1, e.y);
-        } else {
-            out[pos] = child;
-        }
-        ++pos;
+        run += __popc(word[k]);
     }
-    if (over)
+    if (__any_sync(FULL, over) && lane == 0)
         atomicOr(status, ST_CAPACITY);
 }
 
@@ -248,7 +278,7 @@ SparseLayout sparse_layout(int64_t n, int p)
     for (int k = 0; k < L.levels; ++k) {
         L.state_off[k] = L.state_words;
         // tiles of the expansion from level k (its input list)
-        L.state_words += (int)((L.list_cap[k] + SP_T - 1) / SP_T) + 1;
+        L.state_words += (int)((L.list_cap[k] + XT - 1) / XT) + 1;
     }
     L.state = w.take((size_t)L.state_words * 8);
     L.lower = w.take((size_t)cap_chain * 8);
@@ -296,8 +326,8 @@ cudaError_t sparse_launch(const SparseLayout &L, const int32_t *pts, int64_t n, 
     int cur = 0;
     for (int k = L.levels - 1; k >= 1; --k) {
         const bool top = k == L.levels - 1;
-        const int grid = (int)((L.list_cap[k] + SP_T - 1) / SP_T);
-        launch(k_tree_expand<false>, std::max(grid, 1), SP_T, 0, s, t.M[k], list[cur], cnt + cur,
+        const int grid = (int)((L.list_cap[k] + XT - 1) / XT);
+        launch(k_tree_expand<false>, std::max(grid, 1), 1024, 0, s, t.M[k], list[cur], cnt + cur,
                (int)top, list[cur ^ 1], cnt + (cur ^ 1), Lz, nullptr, nullptr, nullptr,
                st + L.state_off[k], (int)L.list_cap[k], (int)L.list_cap[k - 1],
                (int)L.words[k - 1], status);
@@ -305,8 +335,8 @@ cudaError_t sparse_launch(const SparseLayout &L, const int32_t *pts, int64_t n, 
             return e;
         cur ^= 1;
     }
-    const int grid0 = (int)((L.list_cap[0] + SP_T - 1) / SP_T);
-    launch(k_tree_expand<true>, std::max(grid0, 1), SP_T, 0, s, t.M[0], list[cur], cnt + cur,
+    const int grid0 = (int)((L.list_cap[0] + XT - 1) / XT);
+    launch(k_tree_expand<true>, std::max(grid0, 1), 1024, 0, s, t.M[0], list[cur], cnt + cur,
            (int)(L.levels == 1), nullptr, nullptr, Lz, reinterpret_cast<int2 *>(lower),
            reinterpret_cast<int2 *>(upper), counts, st + L.state_off[0], (int)L.list_cap[0],
            L.chain_cap, p, status);
