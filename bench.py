@@ -1037,8 +1037,8 @@ def run_alt(args):
     if rc != ch.CH_OK:
         raise RuntimeError(f"warm-up failed: {ch.strerror(rc)}")
     same = bool(torch.equal(ha[: int(hca.item())].cpu(), hp[: int(hcp.item())].cpu()))
-    detail = {}
-    if alt == "melkman":
+    detail = {"polyline_vertices_after_prefilter": int(pc.item())} if alt == "melkman" else {}
+    if alt == "melkman" and not args.no_aux:
         # the paper's exact pipeline as well: the full Lemma 1 polyline
         # (ch_polyline) and Melkman on it (ch_hull_melkman)
         L1 = ch.ch_reduce(d, p)
@@ -1207,7 +1207,7 @@ def run_sparse(args):
     ch.ch_trace_set([])
     # Fig. 11: both paths at column densities s/p (uniform x), one instance each
     sweep = []
-    for dens in SPARSE_DENSITIES:
+    for dens in (() if args.no_aux else SPARSE_DENSITIES):
         nd = int(round(-p * np.log1p(-dens)))
         Q = torch.from_numpy(synth.points("uniform", nd, p, seed=61)).cuda()
         wsd = ch.ch_sparse_workspace(nd, p)
@@ -1302,6 +1302,9 @@ def main():
                                                                 "melkman", "rxy", "sparse"],
                     default="plain_at_scale")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-aux", action="store_true",
+                    help="skip the side measurements (density sweep, Melkman on the full "
+                         "polyline): for profiling runs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -166,7 +166,6 @@ __global__ void __launch_bounds__(1024)
     if (lane < XW && w0 + lane < cnt) {
         my_idx = top ? 0 : in[w0 + lane];
         my_word = Mk[my_idx];
-        Mk[my_idx] = 0;
     }
     int idx[XW];
     uint32_t word[XW];
@@ -183,10 +182,8 @@ __global__ void __launch_bounds__(1024)
         for (int k = 0; k < XW; ++k) {
             const int child = idx[k] * 32 + lane;
             e[k] = make_int2(0, 0);
-            if (((word[k] >> lane) & 1u) && child < child_limit) {
+            if (((word[k] >> lane) & 1u) && child < child_limit)
                 e[k] = Lz[child];
-                Lz[child] = make_int2(0, 0);
-            }
         }
     }
     int tot;
@@ -212,6 +209,11 @@ __global__ void __launch_bounds__(1024)
         }
     }
     __syncthreads();
+    // the clears come after the look-back: a release or acquire of the
+    // look-back waits for this thread's earlier stores, which would put their
+    // latency on the path between consecutive tiles
+    if (my_idx >= 0)
+        Mk[my_idx] = 0;
     long long run = s_prefix + woff;
     const unsigned below = (1u << lane) - 1u;
     bool over = false;
@@ -225,6 +227,7 @@ __global__ void __launch_bounds__(1024)
             } else if (LEAF) {
                 lower[pos] = make_int2(child + 1, INT_MAX - e[k].x);
                 upper[pos] = make_int2(child + 1, e[k].y);
+                Lz[child] = make_int2(0, 0);
             } else {
                 out[pos] = child;
             }
