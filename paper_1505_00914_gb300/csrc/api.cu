@@ -199,8 +199,9 @@ int ch_plan_info(int64_t n, int32_t p, int32_t *form, int32_t *kernels)
         return rc;
     if (form)
         *form = pl.mode;
-    if (kernels)  // reduction (+ merge of private copies), chain, final hull
-        *kernels = reduce_kernel_count(pl) + (pl.mode == 0 ? 1 : 0) + 2;
+    if (kernels)  // reduction (+ merge of private copies), chain, (second filter pass), final hull
+        *kernels = reduce_kernel_count(pl) + (pl.mode == 0 ? 1 : 0) + 2 +
+                   (hull_layout(p).refilter ? 2 : 0);
     return CH_OK;
 }
 
@@ -585,9 +586,9 @@ int ch_hull_learned_kernel_count(int64_t n, int32_t p, int32_t with_net, int32_t
     if (rc != CH_OK)
         return rc;
     // warm-up (filtered forms), culling step, the reduction (+ merge of
-    // private copies), chain, final hull
+    // private copies), chain, (second filter pass), final hull
     *kernels = reduce_kernel_count(pl) + cull_kernel_count(with_net != 0) +
-               (pl.mode == 0 ? 1 : 0) + 2;
+               (pl.mode == 0 ? 1 : 0) + 2 + (hull_layout(p).refilter ? 2 : 0);
     return CH_OK;
 }
 

@@ -348,6 +348,11 @@ cudaError_t sparse_launch(const SparseLayout &L, const int32_t *pts, int64_t n, 
     return hull_launch(lower, upper, counts, L.chain_cap, hull, hull_count, b + L.hull, status, s);
 }
 
-int sparse_kernel_count(const SparseLayout &L) { return 1 + L.levels + 2; }
+// the reduction, one expansion per level, the hull filter and final CTA (and
+// the second filter pass for long chains)
+int sparse_kernel_count(const SparseLayout &L)
+{
+    return 1 + L.levels + 2 + (hull_layout(L.chain_cap).refilter ? 2 : 0);
+}
 
 }  // namespace ch
