@@ -22,6 +22,8 @@ as roofline.ms_per_step_while_timed).
 --impl reference times the CPU oracle itself on the same workload (rank 0 only).
 
 Other workloads (--workload):
+  plain_at_scale_u16  the default workload with the points stored as packed
+            16-bit pairs (ch_convex_hull_u16: 4 bytes per point instead of 8).
   box       Steps 1-2 for int32 points anywhere: three instances of 2^26
             points (uniform in a 65536 x 65536 box at (-1.5e9, 7e8), disc in a
             120000 x 40000 box at (1e9, -2e9), Gaussian in a 30000 x 90000
@@ -75,10 +77,13 @@ METRIC = "Gpoints/s reduce+chain+hull, % of HBM roofline; batched/learned vs pla
 WORKLOADS = {
     # name: (p, n, distributions)
     "plain_at_scale": (65536, 1 << 26, ("uniform", "disc", "gaussian")),
+    # the same sets as packed 16-bit points (x - 1) | (y - 1) << 16, 4 bytes each
+    "plain_at_scale_u16": (65536, 1 << 26, ("uniform", "disc", "gaussian")),
     "plain_small": (1024, 100_000, ("uniform",)),
     "projected_shells": (4096, 10_000_000, ("shells",)),
-    # profiling case of the filtered reduction: 268 MB of points, above L2
+    # profiling cases of the filtered reduction: 268 MB (134 MB) of points, above L2
     "profile_reduce": (65536, 1 << 25, ("uniform",)),
+    "profile_reduce_u16": (65536, 1 << 25, ("uniform",)),
 }
 
 
@@ -105,13 +110,14 @@ def _kernel_sha(src_path, name):
     return hashlib.sha256("\n".join(lines[start:end + 1]).encode()).hexdigest()[:16]
 
 
-def _traffic(kernel, n, p):
+def _traffic(kernel, n, p, u16=False):
     """DRAM bytes per launch of the reduction kernel from the committed ncu
-    counters, scaled from the captured n to this n (the kernel streams each
-    point once); None when the kernel's source changed since the capture or
-    the capture was at another p."""
+    counters (int32 or packed 16-bit points), scaled from the captured n to
+    this n (the kernel streams each point once); None when the kernel's source
+    changed since the capture or the capture was at another p."""
     try:
-        with open(os.path.join(ROOT, "profiles", "reduce_traffic.json")) as f:
+        name = "reduce_traffic_u16.json" if u16 else "reduce_traffic.json"
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             rec = json.load(f)
         src = os.path.join(ROOT, "paper_1505_00914_gb300", "csrc", "reduce.cu")
         if rec.get("kernel") != kernel or rec.get("p") != p:
@@ -183,6 +189,12 @@ def gen_inputs(workload, rank):
     return p, n, [(d, synth.points(d, n, p, seed=1 + 1000 * rank)) for d in dists]
 
 
+def pack_u16(P):
+    """Host int32 (n, 2) points -> int32 (n,) words (x - 1) | (y - 1) << 16."""
+    P = np.asarray(P, dtype=np.int64)
+    return np.ascontiguousarray((((P[:, 1] - 1) << 16) | (P[:, 0] - 1)).astype(np.uint32).view(np.int32))
+
+
 def cpu_oracle_rate(p, inputs, budget_s):
     """The CPU oracle as it stands (single thread): Algorithm 1 + hull of the
     reduced set, over the workload's instances until ~budget_s elapsed."""
@@ -232,6 +244,8 @@ def workload_config(workload):
                 "l2": "about 8.5 GB of points per step, larger than L2; no flush"}
     p, n, dists = WORKLOADS[workload]
     return {"workload": workload, "p": p, "n_per_instance": n, "distributions": list(dists),
+            "point_format": ("packed uint16 pairs (x - 1, y - 1), 4 bytes per point"
+                             if workload.endswith("_u16") else "int32 pairs, 8 bytes per point"),
             "instances_per_step": len(dists),
             "concurrency": "each instance on its own CUDA stream and workspace",
             "l2": "inputs 8n bytes per instance, larger than L2; no flush"}
@@ -344,7 +358,11 @@ def run_ours(args):
     ch.lib()
 
     p, n, inputs = gen_inputs(args.workload, rank)
-    dev_in = [torch.from_numpy(P).cuda() for _, P in inputs]
+    u16 = args.workload.endswith("_u16")
+    bpp = 4 if u16 else 8  # bytes per point
+    host_fmt = [pack_u16(P) if u16 else P for _, P in inputs]
+    dev_in = [torch.from_numpy(Q).cuda() for Q in host_fmt]
+    hull_fn = ch.ch_convex_hull_u16 if u16 else ch.ch_convex_hull
     nws = ch.ch_convex_hull_workspace_size(n, p)
     # the instances of a step are independent problems: each has its own
     # stream and workspace, so that one instance's latency-bound chain and
@@ -358,13 +376,13 @@ def run_ours(args):
     def step(concurrent=True):
         if not concurrent:  # one after another on the main stream
             for d, h, c, w in zip(dev_in, hulls, hcs, wss):
-                ch.ch_convex_hull(d, p, hull=h, hull_count=c, workspace=w, stream=stream)
+                hull_fn(d, p, hull=h, hull_count=c, workspace=w, stream=stream)
             return
         fork = torch.cuda.Event()
         fork.record(stream)
         for d, h, c, w, st in zip(dev_in, hulls, hcs, wss, streams):
             st.wait_event(fork)
-            ch.ch_convex_hull(d, p, hull=h, hull_count=c, workspace=w, stream=st)
+            hull_fn(d, p, hull=h, hull_count=c, workspace=w, stream=st)
         for st in streams:
             join = torch.cuda.Event()
             join.record(st)
@@ -409,24 +427,36 @@ def run_ours(args):
     value = world * pts_step * args.steps / (ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
 
-    # e2e through the host-buffer entry point (pinned host memory)
+    # e2e through the host-buffer entry point (pinned host memory); the
+    # packed format has no host entry point, so its copies are made here
     e2e_steps = max(1, min(args.steps, 5))
-    host_in = [torch.from_numpy(P).pin_memory() for _, P in inputs]
-    nws_h = ch.ch_convex_hull_host_workspace_size(n, p)
-    del wss
-    ws_h = torch.empty(nws_h, dtype=torch.uint8, device="cuda")
+    host_in = [torch.from_numpy(Q).pin_memory() for Q in host_fmt]
     hh = torch.empty((2 * p, 2), dtype=torch.int32).pin_memory()
+    if u16:
+        def e2e_one(i, hp):
+            dev_in[i].copy_(hp, non_blocking=True)
+            hull_fn(dev_in[i], p, hull=hulls[i], hull_count=hcs[i], workspace=wss[i], stream=stream)
+            k = int(hcs[i].item())
+            hh[:k].copy_(hulls[i][:k])
+            return k
+    else:
+        nws_h = ch.ch_convex_hull_host_workspace_size(n, p)
+        del wss
+        ws_h = torch.empty(nws_h, dtype=torch.uint8, device="cuda")
+
+        def e2e_one(i, hp):
+            return ch.ch_convex_hull_host(hp, p, ws_h, stream=stream, host_hull=hh).shape[0]
     hsz = []
-    for hp in host_in:  # warm-up
-        hsz.append(ch.ch_convex_hull_host(hp, p, ws_h, stream=stream, host_hull=hh).shape[0])
+    for i, hp in enumerate(host_in):  # warm-up
+        hsz.append(e2e_one(i, hp))
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     w0 = time.perf_counter()
     d2h = 0
     for _ in range(e2e_steps):
-        for hp in host_in:
-            d2h += ch.ch_convex_hull_host(hp, p, ws_h, stream=stream, host_hull=hh).shape[0] * 8 + 4
+        for i, hp in enumerate(host_in):
+            d2h += e2e_one(i, hp) * 8 + 4
     e2e_s = time.perf_counter() - w0
     if world > 1:
         t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
@@ -439,7 +469,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    kernel_bytes = 8 * n + 8 * p  # points read + L produced, per launch
+    kernel_bytes = bpp * n + 8 * p  # points read + L produced, per launch
     achieved = kernel_bytes / (red_avg / 1e3) / 1e9
     kname = KERNEL_OF_FORM[ch.ch_plan_info(n, p)[0]]
     cpu_v, cpu_dt, cpu_passes = cpu_oracle_rate(p, inputs, args.cpu_budget)
@@ -457,14 +487,14 @@ def run_ours(args):
         "dtype": "int32",
         "data": "synthetic",
         "config": workload_config(args.workload),
-        "hbm_frac_step": (pts_step * 8 / (ms / args.steps / 1e3) / 1e9) / peak,
+        "hbm_frac_step": (pts_step * bpp / (ms / args.steps / 1e3) / 1e9) / peak,
         "roofline": {"bound": "hbm", "kernel": kname,
                      "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "algorithmic_bytes_per_launch": kernel_bytes, "avg_launch_ms": red_avg,
                      "ms_per_step_while_timed": ms_traced / args.steps,
-                     "traffic": _traffic(kname, n, p)},
-        "e2e": {"value": e2e_val, "unit": "Gpoints/s", "h2d_bytes_per_step": pts_step * 8,
+                     "traffic": _traffic(kname, n, p, u16)},
+        "e2e": {"value": e2e_val, "unit": "Gpoints/s", "h2d_bytes_per_step": pts_step * bpp,
                 "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps},
         "cpu_baseline": {"value": cpu_v, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
                          "sample": f"{cpu_passes} pass(es) over the step's {len(inputs)} instances "

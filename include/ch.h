@@ -152,6 +152,19 @@ int ch_convex_hull(const int32_t *pts, int64_t n, int32_t p, int32_t *L,
                    int32_t *hull, int32_t *hull_count,
                    void *workspace, size_t ws_bytes, ch_stream_t stream);
 
+/* The same two calls for points stored as packed 16-bit pairs (the int16x2
+ * point format): pts is uint32[n], point k = (x, y) with x - 1 in the low
+ * and y - 1 in the high 16 bits of pts[k] (little-endian uint16 pairs
+ * (x - 1, y - 1)), 4-byte aligned; p <= 65536 (else CH_ERR_ARG).  Half the
+ * bytes of int32 pairs per point.  Workspaces: ch_reduce_workspace_size and
+ * ch_convex_hull_workspace_size for the same n and p.  Outputs and errors
+ * as for ch_reduce and ch_convex_hull. */
+int ch_reduce_u16(const uint32_t *pts, int64_t n, int32_t p, int32_t *L, void *workspace,
+                  size_t ws_bytes, ch_stream_t stream);
+int ch_convex_hull_u16(const uint32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t *lower,
+                       int32_t *upper, int32_t *counts, int32_t *hull, int32_t *hull_count,
+                       void *workspace, size_t ws_bytes, ch_stream_t stream);
+
 int ch_convex_hull_host_workspace_size(int64_t n, int32_t p, size_t *bytes);
 
 /* End to end from HOST memory: copies host_pts (int32[n][2]; pinned memory

@@ -85,6 +85,8 @@ def _declare(lib):
         "ch_sparse_kernel_count": (ctypes.c_int, [i64, i32, ctypes.POINTER(i32)]),
         "ch_convex_hull_sparse": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, sz, P]),
         "ch_reduce_rows": (ctypes.c_int, [P, i32, P, P]),
+        "ch_reduce_u16": (ctypes.c_int, [P, i64, i32, P, P, sz, P]),
+        "ch_convex_hull_u16": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P, sz, P]),
         "ch_convex_hull_rxy_workspace_size": (ctypes.c_int, [i64, i32, szp]),
         "ch_convex_hull_rxy": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, sz, P]),
     }
@@ -276,6 +278,49 @@ def ch_convex_hull(pts, p: int, L=None, lower=None, upper=None, counts=None, hul
     _check(lib().ch_convex_hull(_ptr(pts), n, int(p), _ptr(L), _ptr(lower), _ptr(upper),
                                 _ptr(counts), _ptr(hull), _ptr(hull_count), _ptr(ws), ws.numel(),
                                 _stream(stream)), "ch_convex_hull")
+    return hull, hull_count
+
+
+def pack_u16(pts):
+    """int32 (n, 2) points in [1, 65536]^2 -> the packed 16-bit format of
+    ch_convex_hull_u16: one int32 word (x - 1) | (y - 1) << 16 per point
+    (a view of little-endian uint16 pairs (x - 1, y - 1))."""
+    x = (pts[:, 0] - 1).to(torch.int32)
+    y = (pts[:, 1] - 1).to(torch.int32)
+    return ((y << 16) | (x & 0xFFFF)).contiguous()
+
+
+def _pts16(pts):
+    if pts.dtype != torch.int32 or pts.dim() != 1 or not pts.is_contiguous():
+        raise ValueError("packed points must be a contiguous int32 tensor of shape (n,)")
+    return pts
+
+
+def ch_reduce_u16(pts, p: int, L=None, workspace=None, stream=None):
+    """Algorithm 1 on packed 16-bit points (see pack_u16): L (p, 2)."""
+    pts = _pts16(pts)
+    dev = _dev(pts)
+    if L is None:
+        L = torch.empty((p, 2), dtype=torch.int32, device=dev)
+    ws = _ws(ch_reduce_workspace_size(pts.shape[0], p), dev, workspace)
+    _check(lib().ch_reduce_u16(_ptr(pts), pts.shape[0], int(p), _ptr(L), _ptr(ws), ws.numel(),
+                               _stream(stream)), "ch_reduce_u16")
+    return L
+
+
+def ch_convex_hull_u16(pts, p: int, L=None, lower=None, upper=None, counts=None, hull=None,
+                       hull_count=None, workspace=None, stream=None):
+    """The fused path on packed 16-bit points; returns (hull, hull_count)."""
+    pts = _pts16(pts)
+    dev = _dev(pts)
+    if hull is None:
+        hull = torch.empty((2 * p, 2), dtype=torch.int32, device=dev)
+    if hull_count is None:
+        hull_count = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = _ws(ch_convex_hull_workspace_size(pts.shape[0], p), dev, workspace)
+    _check(lib().ch_convex_hull_u16(_ptr(pts), pts.shape[0], int(p), _ptr(L), _ptr(lower),
+                                    _ptr(upper), _ptr(counts), _ptr(hull), _ptr(hull_count),
+                                    _ptr(ws), ws.numel(), _stream(stream)), "ch_convex_hull_u16")
     return hull, hull_count
 
 

@@ -107,6 +107,7 @@ int box_frame(const int32_t *box, Frame *f)
     if (p < 1 || q < 1 || p > CH_MAX_P || q > CH_MAX_P)
         return CH_ERR_ARG;
     f->tr = q < p;
+    f->pk = 0;
     f->c0 = f->tr ? box[2] : box[0];
     f->r0 = f->tr ? box[0] : box[2];
     f->nc = (int)std::min(p, q);
@@ -307,12 +308,19 @@ int ch_convex_hull_workspace_size(int64_t n, int32_t p, size_t *bytes)
     return CH_OK;
 }
 
-int ch_convex_hull(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t *lower,
-                   int32_t *upper, int32_t *counts, int32_t *hull, int32_t *hull_count,
-                   void *workspace, size_t ws_bytes, ch_stream_t stream)
+}  // extern "C"
+
+namespace ch {
+namespace {
+// The fused path over the square of side p; frame = square_frame(p) for
+// int32 points, square_frame_u16(p) for packed 16-bit points.
+int convex_hull_square(const int32_t *pts, int64_t n, int32_t p, const Frame &frame, int32_t *L,
+                       int32_t *lower, int32_t *upper, int32_t *counts, int32_t *hull,
+                       int32_t *hull_count, void *workspace, size_t ws_bytes, ch_stream_t stream)
 {
-    if (check_np(n, p) != CH_OK || (n > 0 && !pts) || !hull || !hull_count || !aligned8(pts) ||
-        !aligned8(L) || !aligned8(lower) || !aligned8(upper) || !aligned8(hull))
+    // the caller checks the alignment of pts for its point format
+    if (check_np(n, p) != CH_OK || (n > 0 && !pts) || !hull || !hull_count || !aligned8(L) ||
+        !aligned8(lower) || !aligned8(upper) || !aligned8(hull))
         return CH_ERR_ARG;
     PathWs w;
     int rc = path_layout(n, p, &w);
@@ -339,7 +347,7 @@ int ch_convex_hull(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t
     unsigned long long *zero = reinterpret_cast<unsigned long long *>(b + w.state);
     const int nzero = (int)(chain_state_bytes(p) / 8);
     // the look-back state is cleared by the last kernel before the chain step
-    cudaError_t e = reduce_launch(w.plan, pts, n, square_frame(p), part, L, st, s,
+    cudaError_t e = reduce_launch(w.plan, pts, n, frame, part, L, st, s,
                                   w.plan.mode == 0 ? nullptr : zero, nzero, ev0, ev1);
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
@@ -358,6 +366,56 @@ int ch_convex_hull(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
     return cuda_rc(hull_final_launch(hl, hw, hull, hull_count, s));
+}
+}  // namespace
+}  // namespace ch
+
+extern "C" {
+
+int ch_convex_hull(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t *lower,
+                   int32_t *upper, int32_t *counts, int32_t *hull, int32_t *hull_count,
+                   void *workspace, size_t ws_bytes, ch_stream_t stream)
+{
+    if (!aligned8(pts))
+        return CH_ERR_ARG;
+    return convex_hull_square(pts, n, p, square_frame(p), L, lower, upper, counts, hull,
+                              hull_count, workspace, ws_bytes, stream);
+}
+
+int ch_convex_hull_u16(const uint32_t *pts, int64_t n, int32_t p, int32_t *L, int32_t *lower,
+                       int32_t *upper, int32_t *counts, int32_t *hull, int32_t *hull_count,
+                       void *workspace, size_t ws_bytes, ch_stream_t stream)
+{
+    if (p > 65536 || ((uintptr_t)pts & 3))
+        return CH_ERR_ARG;
+    return convex_hull_square(reinterpret_cast<const int32_t *>(pts), n, p, square_frame_u16(p), L,
+                              lower, upper, counts, hull, hull_count, workspace, ws_bytes, stream);
+}
+
+int ch_reduce_u16(const uint32_t *pts, int64_t n, int32_t p, int32_t *L, void *workspace,
+                  size_t ws_bytes, ch_stream_t stream)
+{
+    if (check_np(n, p) != CH_OK || p > 65536 || !L || (n > 0 && !pts) || ((uintptr_t)pts & 3) ||
+        !aligned8(L))
+        return CH_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ReducePlan pl;
+    int rc = reduce_plan(n, p, &pl);
+    if (rc != CH_OK)
+        return rc;
+    const size_t need = reduce_partials_bytes(pl, p);
+    if (ws_bytes < need || (need > 0 && !workspace))
+        return CH_ERR_WORKSPACE;
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    cudaEvent_t ev0, ev1;
+    next_trace(&ev0, &ev1);
+    cudaError_t e = reduce_launch(pl, reinterpret_cast<const int32_t *>(pts), n,
+                                  square_frame_u16(p), workspace, L, st, s, nullptr, 0, ev0, ev1);
+    if (e == cudaSuccess && pl.mode == 0)
+        e = reduce_merge_launch(workspace, pl.copies, p, p, L, s);
+    return cuda_rc(e);
 }
 
 namespace {

@@ -75,25 +75,32 @@ struct WsLayout {
 // the shorter side of the bounding box); a point (x, y) with u = tr ? y : x,
 // v = tr ? x : y lands in column u - c0 (0-based, < nc) at row v - r0 + 1
 // (1-based, <= nr).  The square of side p of Section 2.1 is {1, 1, p, p, 0}.
+// pk = 1: the points are packed 16-bit pairs, one 32-bit word per point,
+// (x - 1) | (y - 1) << 16, in the square of side p <= 65536.
 struct Frame {
     int c0, r0;
     int nc, nr;
     int tr;
+    int pk;
 };
-inline Frame square_frame(int p) { return Frame{1, 1, p, p, 0}; }
+inline Frame square_frame(int p) { return Frame{1, 1, p, p, 0, 0}; }
+inline Frame square_frame_u16(int p) { return Frame{1, 1, p, p, 0, 1}; }
 
 // Column c (0-based) and row index rr = row - 1 of point (x, y); unsigned
 // arithmetic, so that any out-of-frame point gives c >= nc or rr >= nr.
 // FM: 0 the square (offsets 1, known at compile time), 1 a translated frame,
-// 2 a translated and transposed frame.
+// 2 a translated and transposed frame, 3 the square with packed 16-bit points.
 template <int FM>
 __device__ __forceinline__ void frame_map(const Frame &f, int x, int y, uint32_t &c, uint32_t &rr)
 {
     const int u = FM == 2 ? y : x, v = FM == 2 ? x : y;
-    c = (uint32_t)u - (uint32_t)(FM == 0 ? 1 : f.c0);
-    rr = (uint32_t)v - (uint32_t)(FM == 0 ? 1 : f.r0);
+    c = (uint32_t)u - (uint32_t)(FM == 0 || FM == 3 ? 1 : f.c0);
+    rr = (uint32_t)v - (uint32_t)(FM == 0 || FM == 3 ? 1 : f.r0);
 }
-inline int frame_mode(const Frame &f) { return f.tr ? 2 : (f.c0 == 1 && f.r0 == 1 ? 0 : 1); }
+inline int frame_mode(const Frame &f)
+{
+    return f.pk ? 3 : f.tr ? 2 : (f.c0 == 1 && f.r0 == 1 ? 0 : 1);
+}
 
 // ---- reduction (reduce.cu) ----
 struct ReducePlan {

@@ -42,30 +42,88 @@ namespace {
 
 constexpr int RU = 4;            // 16-byte loads in flight per thread per iteration
 
-// The point array is read as 16-byte pairs of points starting at the first
-// 16-byte boundary; an 8-byte aligned array has its first point handled on its
-// own, and an odd tail likewise.
-struct PairView {
+// The point array is read as 16-byte vectors from the first 16-byte
+// boundary: two int32 (x, y) points per vector, or four packed 16-bit points
+// (FM 3, one 32-bit word (x - 1) | (y - 1) << 16 per point).  The points
+// before the boundary (head) and after the last whole vector (tail) are
+// taken one by one.
+template <int FM>
+constexpr int WPP = FM == 3 ? 1 : 2;  // 32-bit words per point
+template <int FM>
+constexpr int PPV = 4 / WPP<FM>;  // points per 16-byte vector
+
+struct VecView {
     const int4 *p4;
-    int64_t npairs;
-    int64_t head;  // 0 or 1 leading point outside the pairs
-    bool tail;     // one trailing point outside the pairs
+    int64_t nvec;
+    int head;  // points before the first vector (0 .. PPV - 1)
+    int tail;  // points after the last vector (0 .. PPV - 1)
 };
 
-__device__ __forceinline__ PairView pair_view(const int32_t *pts, int64_t n)
+template <int FM>
+__device__ __forceinline__ VecView vec_view(const int32_t *pts, int64_t n)
 {
-    PairView v;
-    v.head = (((uintptr_t)pts & 15) != 0 && n > 0) ? 1 : 0;
-    v.npairs = (n - v.head) >> 1;
-    v.tail = ((n - v.head) & 1) != 0;
-    v.p4 = reinterpret_cast<const int4 *>(pts + 2 * v.head);
+    VecView v;
+    const int64_t h = (int64_t)(((16 - ((uintptr_t)pts & 15)) & 15) / (4 * WPP<FM>));
+    v.head = (int)min(h, n);
+    v.nvec = (n - v.head) / PPV<FM>;
+    v.tail = (int)(n - v.head - v.nvec * PPV<FM>);
+    v.p4 = reinterpret_cast<const int4 *>(pts + WPP<FM> * v.head);
     return v;
 }
 
-// Streams the 16-byte pairs [s0, e0) of a CTA's slice: each thread keeps RU
-// loads in flight and issues its next RU before folding the current ones
+// Point k of the array.
+template <int FM>
+__device__ __forceinline__ void point_at(const int32_t *pts, int64_t k, int &x, int &y)
+{
+    if constexpr (FM == 3) {
+        const uint32_t w = (uint32_t)pts[k];
+        x = (int)(w & 0xFFFFu) + 1;
+        y = (int)(w >> 16) + 1;
+    } else {
+        x = pts[2 * k];
+        y = pts[2 * k + 1];
+    }
+}
+
+// fold(x, y) for every point of one vector.
+template <int FM, typename Fold>
+__device__ __forceinline__ void each_point(const int4 &v, Fold &&fold)
+{
+    if constexpr (FM == 3) {
+        const uint32_t w[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            fold((int)(w[k] & 0xFFFFu) + 1, (int)(w[k] >> 16) + 1);
+    } else {
+        fold(v.x, v.y);
+        fold(v.z, v.w);
+    }
+}
+
+// The head points (first CTA) and tail points (last CTA), one thread each.
+template <int FM, typename Fold>
+__device__ __forceinline__ void fold_edges(const int32_t *pts, int64_t n, const VecView &v,
+                                           Fold &&fold)
+{
+    if (threadIdx.x != 0)
+        return;
+    int x, y;
+    if (blockIdx.x == 0)
+        for (int k = 0; k < v.head; ++k) {
+            point_at<FM>(pts, k, x, y);
+            fold(x, y);
+        }
+    if (blockIdx.x == gridDim.x - 1)
+        for (int k = 0; k < v.tail; ++k) {
+            point_at<FM>(pts, n - v.tail + k, x, y);
+            fold(x, y);
+        }
+}
+
+// Streams the 16-byte vectors [s0, e0) of a CTA's slice: each thread keeps
+// RU loads in flight and issues its next RU before folding the current ones
 // (register double buffering), so the loads never wait for the folding.
-// fold(v) takes one pair of points.  KEEP: load through L2 with the
+// fold(v) takes one vector of points.  KEEP: load through L2 with the
 // normal policy (the data is read again soon) instead of evict-first.
 template <int RT, bool KEEP = false, typename Fold>
 __device__ __forceinline__ void stream_pairs(const int4 *__restrict__ p4, int64_t s0, int64_t e0,
@@ -122,18 +180,12 @@ __global__ void __launch_bounds__(RT)
         atomicMin(slo + c, (int)rr + 1);
         atomicMax(shi + c, (int)rr + 1);
     };
-    const PairView pv = pair_view(pts, n);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && pv.head)
-        fold(pts[0], pts[1]);
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0 && pv.tail)
-        fold(pts[2 * (n - 1)], pts[2 * (n - 1) + 1]);
-    const int64_t per = (pv.npairs + gridDim.x - 1) / gridDim.x;
+    const VecView pv = vec_view<FM>(pts, n);
+    fold_edges<FM>(pts, n, pv, fold);
+    const int64_t per = (pv.nvec + gridDim.x - 1) / gridDim.x;
     const int64_t s0 = (int64_t)blockIdx.x * per;
-    const int64_t e0 = min(pv.npairs, s0 + per);
-    stream_pairs<RT>(pv.p4, s0, e0, [&](const int4 &v) {
-        fold(v.x, v.y);
-        fold(v.z, v.w);
-    });
+    const int64_t e0 = min(pv.nvec, s0 + per);
+    stream_pairs<RT>(pv.p4, s0, e0, [&](const int4 &v) { each_point<FM>(v, fold); });
     __syncthreads();
     uint32_t *out = part + (size_t)blockIdx.x * nc;
     for (int i = threadIdx.x; i < nc; i += RT)  // rows <= 65536 in this form
@@ -179,20 +231,13 @@ __global__ void __launch_bounds__(256)
 {
     pdl_wait();
     pdl_trigger();
-    const PairView pv = pair_view(pts, n);
+    const VecView pv = vec_view<FM>(pts, n);
     bool bad = false;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < pv.npairs;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int4 v = __ldcs(pv.p4 + j);
-        bad |= !fold_global<FM>(L, f, v.x, v.y);
-        bad |= !fold_global<FM>(L, f, v.z, v.w);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (pv.head)
-            bad |= !fold_global<FM>(L, f, pts[0], pts[1]);
-        if (pv.tail)
-            bad |= !fold_global<FM>(L, f, pts[2 * (n - 1)], pts[2 * (n - 1) + 1]);
-    }
+    auto fold = [&](int x, int y) { bad |= !fold_global<FM>(L, f, x, y); };
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < pv.nvec;
+         j += (int64_t)gridDim.x * blockDim.x)
+        each_point<FM>(__ldcs(pv.p4 + j), fold);
+    fold_edges<FM>(pts, n, pv, fold);
     if (__syncthreads_or(bad) && threadIdx.x == 0)
         atomicOr(status, ST_RANGE);
 }
@@ -200,12 +245,12 @@ __global__ void __launch_bounds__(256)
 
 constexpr int WARM_DIV = 16;  // the warm-up reads the first 1/WARM_DIV of each slice
 
-// Slice of point pairs [s0, e0) reduced by CTA `b` of `grid`.
-__device__ __forceinline__ void slice_of(int64_t npairs, int b, int grid, int64_t &s0, int64_t &e0)
+// Slice of point vectors [s0, e0) reduced by CTA `b` of `grid`.
+__device__ __forceinline__ void slice_of(int64_t nvec, int b, int grid, int64_t &s0, int64_t &e0)
 {
-    const int64_t per = (npairs + grid - 1) / grid;
+    const int64_t per = (nvec + grid - 1) / grid;
     s0 = (int64_t)b * per;
-    e0 = min(npairs, s0 + per);
+    e0 = min(nvec, s0 + per);
 }
 
 // Filter words are (lo bin << 8) | hi bin; "tighter of" two packed words is
@@ -245,14 +290,11 @@ __global__ void __launch_bounds__(RT)
         if (b > (f & 0xFFu))
             fb[2 * c] = (unsigned char)b;
     };
-    const PairView pv = pair_view(pts, n);
+    const VecView pv = vec_view<FM>(pts, n);
     int64_t s0, e0;
-    slice_of(pv.npairs, blockIdx.x, grid, s0, e0);
+    slice_of(pv.nvec, blockIdx.x, grid, s0, e0);
     const int64_t warm = s0 + (e0 - s0) / WARM_DIV;
-    stream_pairs<RT, true>(pv.p4, s0, warm, [&](const int4 &v) {
-        learn(v.x, v.y);
-        learn(v.z, v.w);
-    });
+    stream_pairs<RT, true>(pv.p4, s0, warm, [&](const int4 &v) { each_point<FM>(v, learn); });
     __syncthreads();
     uint4 *out = reinterpret_cast<uint4 *>(slots) + (size_t)blockIdx.x * words;
     for (int i = threadIdx.x; i < words; i += RT)
@@ -354,17 +396,11 @@ __global__ void __launch_bounds__(RT)
                 fb[2 * c] = (unsigned char)b;
         }
     };
-    const PairView pv = pair_view(pts, n);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && pv.head)
-        fold(pts[0], pts[1]);
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0 && pv.tail)
-        fold(pts[2 * (n - 1)], pts[2 * (n - 1) + 1]);
+    const VecView pv = vec_view<FM>(pts, n);
+    fold_edges<FM>(pts, n, pv, fold);
     int64_t s0, e0;
-    slice_of(pv.npairs, blockIdx.x, gridDim.x, s0, e0);
-    stream_pairs<RT>(pv.p4, s0, e0, [&](const int4 &v) {
-        fold(v.x, v.y);
-        fold(v.z, v.w);
-    });
+    slice_of(pv.nvec, blockIdx.x, gridDim.x, s0, e0);
+    stream_pairs<RT>(pv.p4, s0, e0, [&](const int4 &v) { each_point<FM>(v, fold); });
     if (__syncthreads_or(bad) && threadIdx.x == 0)
         atomicOr(status, ST_RANGE);
 }
@@ -455,6 +491,9 @@ int dev_setup(int *dev_out)
         cudaFuncSetAttribute(k_filter_warm<1024, 0>, a, d.optin);
         cudaFuncSetAttribute(k_filter_warm<1024, 1>, a, d.optin);
         cudaFuncSetAttribute(k_filter_warm<1024, 2>, a, d.optin);
+        cudaFuncSetAttribute(k_reduce_private<1024, 3>, a, d.optin);
+        cudaFuncSetAttribute(k_reduce_filtered<1024, 3>, a, d.optin);
+        cudaFuncSetAttribute(k_filter_warm<1024, 3>, a, d.optin);
         d.ready = true;
     }
     return d.optin;
@@ -582,11 +621,15 @@ cudaError_t reduce_launch(const ReducePlan &pl, const int32_t *pts, int64_t n, c
         launch_fill(f, L2, s, zero, nzero);
     const int fm = frame_mode(f);
     if (!prefilled && pl.mode == 1)
-        (fm == 0 ? launch_warm<0> : fm == 1 ? launch_warm<1> : launch_warm<2>)(pl, pts, n, f, part, L2,
-                                                                             s, zero, nzero);
+        (fm == 0   ? launch_warm<0>
+         : fm == 1 ? launch_warm<1>
+         : fm == 2 ? launch_warm<2>
+                   : launch_warm<3>)(pl, pts, n, f, part, L2, s, zero, nzero);
     mark(ev0);
-    (fm == 0 ? launch_main<0> : fm == 1 ? launch_main<1> : launch_main<2>)(pl, pts, n, f, part, L2,
-                                                                         status, s);
+    (fm == 0   ? launch_main<0>
+     : fm == 1 ? launch_main<1>
+     : fm == 2 ? launch_main<2>
+               : launch_main<3>)(pl, pts, n, f, part, L2, status, s);
     mark(ev1);
     return cudaGetLastError();
 }
@@ -600,8 +643,10 @@ cudaError_t reduce_warm_launch(const ReducePlan &pl, const int32_t *pts, int64_t
         launch_fill(f, L2, s, zero, nzero);
     else if (pl.mode == 1) {
         const int fm = frame_mode(f);
-        (fm == 0 ? launch_warm<0> : fm == 1 ? launch_warm<1> : launch_warm<2>)(pl, pts, n, f, part, L2,
-                                                                             s, zero, nzero);
+        (fm == 0   ? launch_warm<0>
+         : fm == 1 ? launch_warm<1>
+         : fm == 2 ? launch_warm<2>
+                   : launch_warm<3>)(pl, pts, n, f, part, L2, s, zero, nzero);
     }
     return cudaGetLastError();
 }
