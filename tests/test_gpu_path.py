@@ -190,13 +190,26 @@ def test_argument_errors():
 
 
 def test_host_entry_point_matches():
+    """Page-locked points are read in place, pageable ones copied first; a
+    page-locked array starting 8 bytes into its buffer (not 16-byte aligned)
+    and odd lengths take the edge paths of the in-place read."""
     p = 4096
-    P = synth.shells(300_000, p, seed=2)
+    P = synth.shells(300_001, p, seed=2)
     nbytes = ch.ch_convex_hull_host_workspace_size(P.shape[0], p)
     ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     hp = torch.from_numpy(P).pin_memory()
-    h = ch.ch_convex_hull_host(hp, p, ws).numpy()
-    np.testing.assert_array_equal(h, oracle.hull_points(P))
+    np.testing.assert_array_equal(ch.ch_convex_hull_host(hp, p, ws).numpy(), oracle.hull_points(P))
+    pageable = torch.from_numpy(P.copy())
+    np.testing.assert_array_equal(ch.ch_convex_hull_host(pageable, p, ws).numpy(),
+                                  oracle.hull_points(P))
+    big = torch.from_numpy(np.concatenate([P[:1], P])).pin_memory()
+    sub = big[1:]
+    assert sub.data_ptr() % 16 == 8 and sub.is_contiguous()
+    np.testing.assert_array_equal(ch.ch_convex_hull_host(sub, p, ws).numpy(), oracle.hull_points(P))
+    for n in (0, 1, 2, 3, 1001):
+        Q = torch.from_numpy(P[:n].copy()).pin_memory()
+        np.testing.assert_array_equal(ch.ch_convex_hull_host(Q, p, ws).numpy(),
+                                      oracle.hull_points(P[:n]))
 
 
 @pytest.mark.parametrize("dist", ["uniform", "disc", "gaussian"])
