@@ -167,14 +167,11 @@ int ch_convex_hull_u16(const uint32_t *pts, int64_t n, int32_t p, int32_t *L, in
 
 int ch_convex_hull_host_workspace_size(int64_t n, int32_t p, size_t *bytes);
 
-/* End to end from HOST memory: host_pts (int32[n][2]) is read in place by
- * the kernels when it is page-locked memory mapped for the device (e.g.
- * cudaHostAlloc / cudaHostRegister; on Grace Blackwell over the coherent
- * chip-to-chip link), and is copied to the device workspace first when it is
- * pageable; then ch_convex_hull runs, the hull is copied to host_hull
- * (capacity 2p pairs) and its size to *host_hull_count, and the call waits
- * for the stream.  Returns the data status too (it calls ch_sync_status).
- * A page-locked buffer must stay valid and unchanged until the call returns. */
+/* End to end from HOST memory: copies host_pts (int32[n][2]; pinned memory
+ * gives full copy speed) to the device workspace, runs ch_convex_hull, copies
+ * the hull to host_hull (capacity 2p pairs) and its size to
+ * *host_hull_count, and waits for the stream.  Returns the data status too
+ * (it calls ch_sync_status). */
 int ch_convex_hull_host(const int32_t *host_pts, int64_t n, int32_t p,
                         int32_t *host_hull, int32_t *host_hull_count,
                         void *workspace, size_t ws_bytes, ch_stream_t stream);

@@ -20,29 +20,6 @@ int g_sms[MAX_DEV] = {};
 
 inline bool aligned8(const void *p) { return ((uintptr_t)p & 7) == 0; }
 
-// The device address of host memory [p, p + bytes) when both of its ends
-// are page-locked host memory mapped for the device, else nullptr.
-const int32_t *mapped_host(const int32_t *p, size_t bytes)
-{
-    if (!p || bytes == 0)
-        return nullptr;
-    cudaPointerAttributes a0, a1;
-    if (cudaPointerGetAttributes(&a0, p) != cudaSuccess ||
-        cudaPointerGetAttributes(&a1, reinterpret_cast<const char *>(p) + bytes - 1) !=
-            cudaSuccess) {
-        cudaGetLastError();  // clear the error of an unknown pointer
-        return nullptr;
-    }
-    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer ||
-        !a1.devicePointer)
-        return nullptr;
-    const char *d0 = reinterpret_cast<const char *>(a0.devicePointer);
-    const char *d1 = reinterpret_cast<const char *>(a1.devicePointer);
-    if (d1 - d0 != (ptrdiff_t)(bytes - 1))
-        return nullptr;  // the two ends are not one mapping
-    return reinterpret_cast<const int32_t *>(d0);
-}
-
 // ch_trace_set ring of event pairs around the reduction kernel.
 std::mutex g_trace_mu;
 cudaEvent_t g_trace[2 * 1024];
@@ -873,18 +850,10 @@ int ch_convex_hull_host(const int32_t *host_pts, int64_t n, int32_t p, int32_t *
     const size_t inner_off = l.take(0);
     void *inner = b + inner_off;
     const size_t inner_bytes = ws_bytes - inner_off;
-    // Page-locked host memory is mapped into the device's address space: the
-    // kernels then stream the points straight over the host link (on Grace
-    // Blackwell the coherent chip-to-chip link), with no staging copy.
-    // Pageable memory is copied into the workspace first.
-    const int32_t *src = mapped_host(host_pts, (size_t)n * 8);
-    if (!src) {
-        if (n > 0 && cudaMemcpyAsync(d_pts, host_pts, (size_t)n * 8, cudaMemcpyHostToDevice, s) !=
-                         cudaSuccess)
-            return CH_ERR_CUDA;
-        src = d_pts;
-    }
-    rc = ch_convex_hull(src, n, p, nullptr, nullptr, nullptr, nullptr, d_hull, d_cnt, inner,
+    if (n > 0 && cudaMemcpyAsync(d_pts, host_pts, (size_t)n * 8, cudaMemcpyHostToDevice, s) !=
+                     cudaSuccess)
+        return CH_ERR_CUDA;
+    rc = ch_convex_hull(d_pts, n, p, nullptr, nullptr, nullptr, nullptr, d_hull, d_cnt, inner,
                         inner_bytes, stream);
     if (rc != CH_OK)
         return rc;

@@ -190,9 +190,8 @@ def test_argument_errors():
 
 
 def test_host_entry_point_matches():
-    """Page-locked points are read in place, pageable ones copied first; a
-    page-locked array starting 8 bytes into its buffer (not 16-byte aligned)
-    and odd lengths take the edge paths of the in-place read."""
+    """Page-locked and pageable host points; a page-locked array starting 8
+    bytes into its buffer (not 16-byte aligned) and short lengths."""
     p = 4096
     P = synth.shells(300_001, p, seed=2)
     nbytes = ch.ch_convex_hull_host_workspace_size(P.shape[0], p)
