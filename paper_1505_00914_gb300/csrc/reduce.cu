@@ -177,8 +177,13 @@ __global__ void __launch_bounds__(RT)
             bad = true;
             return;
         }
-        atomicMin(slo + c, (int)rr + 1);
-        atomicMax(shi + c, (int)rr + 1);
+        const int r = (int)rr + 1;
+        // a read first: the entry only ever tightens, so a point that cannot
+        // improve the value read cannot improve the current one either
+        if (r < slo[c])
+            atomicMin(slo + c, r);
+        if (r > shi[c])
+            atomicMax(shi + c, r);
     };
     const VecView pv = vec_view<FM>(pts, n);
     fold_edges<FM>(pts, n, pv, fold);
