@@ -56,12 +56,8 @@ __device__ __forceinline__ void fold(int *slo, int *shi, uint32_t up, int x, int
         bad = true;
         return;
     }
-    // a read first: the entry only ever tightens, so a point that cannot
-    // improve the value read cannot improve the current one either
-    if (y < slo[c])
-        atomicMin(slo + c, y);
-    if (y > shi[c])
-        atomicMax(shi + c, y);
+    atomicMin(slo + c, y);
+    atomicMax(shi + c, y);
 }
 
 // Folds points [0, n) of `base` (8-byte aligned) into slo/shi; whole CTA.
