@@ -113,3 +113,36 @@ def test_batched_config_full_size_sampled():
                     | {int(np.argmax(np.diff(offsets)))})
     check_sets(pts, offsets, ps, hull, hoff, cnt, sets=sample)
     assert np.all(cnt >= 1)
+
+
+def test_culling_polygon_shapes():
+    """Sets for which the extreme-point polygon of the finishing step is
+    degenerate, tight or full of boundary points: every hull exact."""
+    rng = np.random.default_rng(21)
+    sets, ps = [], []
+    p = 4096
+    t = np.linspace(0, 2 * np.pi, 20000, endpoint=False)
+    circle = np.stack([2048 + 2000 * np.cos(t), 2048 + 2000 * np.sin(t)], 1).round().astype(np.int32)
+    sets.append(circle); ps.append(p)
+    g = np.arange(1, 65)
+    sets.append(np.stack(np.meshgrid(g, g), -1).reshape(-1, 2).astype(np.int32)); ps.append(64)
+    tri = rng.integers(1, p + 1, size=(200_000, 2))
+    sets.append(tri[tri[:, 1] <= tri[:, 0]].astype(np.int32)); ps.append(p)
+    diag = np.stack([np.arange(1, 5001), np.arange(1, 5001)], 1).astype(np.int32)
+    sets.append(diag); ps.append(5000)
+    two = np.asarray([[5, 1], [5, 9], [9, 3], [9, 4], [5, 5]], np.int32)
+    sets.append(two); ps.append(9)
+    # points on the octagon-like boundary of a square with cut corners, plus interior
+    sq = rng.integers(100, 3900, size=(100_000, 2))
+    edge = np.concatenate([np.stack([np.arange(100, 3900), np.full(3800, 100)], 1),
+                           np.stack([np.full(3800, 3899), np.arange(100, 3900)], 1)])
+    sets.append(np.concatenate([sq, edge]).astype(np.int32)); ps.append(p)
+    for d in ("uniform", "disc", "gaussian", "annulus"):
+        sets.append(synth.points(d, 300_000, 16384, seed=len(sets))); ps.append(16384)
+    ps = np.asarray(ps, np.int32)
+    offsets = np.zeros(len(sets) + 1, np.int64)
+    np.cumsum([s.shape[0] for s in sets], out=offsets[1:])
+    pts = np.concatenate(sets)
+    for cm in (1, 64):
+        hull, hoff, cnt = run_batch(pts, offsets, ps, chunk_mult=cm)
+        check_sets(pts, offsets, ps, hull, hoff, cnt)
