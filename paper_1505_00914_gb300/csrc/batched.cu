@@ -103,165 +103,11 @@ __device__ void fold_range(const int32_t *__restrict__ base, int64_t n, int p, i
     }
 }
 
-constexpr int SPARSE_TILE = 64;  // tiles with at most this many points per chain skip the pre-filter
-
-// Culling of a set's chains before the tile pre-filter.  The extreme chain
-// points in 16 integer directions (the lower chain for the 7 that point down,
-// the upper chain for the 7 that point up, both chains of the first and last
-// valid columns for +-x) are input points; a chain point strictly inside
-// their convex polygon is no hull vertex and is dropped.  The first and last
-// valid columns are never strictly inside, so both chains keep their ends
-// and the stitch is unchanged.  On dense sets most points go, and most tiles
-// then take the short path instead of the ten-level min-tree filter.
-constexpr int CPOLY = 20;  // polygon vertices at most (16 extremes + the 4 end points)
-
-struct CullPoly {
-    int nlo, nup;          // lower / upper boundary vertices, increasing x; 0: no culling
-    int xmin, xmax;
-    int2 lo[CPOLY], up[CPOLY];
-};
-
-__device__ __forceinline__ int orient2(int2 o, int2 a, int2 b)
-{
-    // coordinates below 2^14 in a batch: the products fit in 32 bits
-    return (a.x - o.x) * (b.y - o.y) - (a.y - o.y) * (b.x - o.x);
-}
-
-// Largest i < n - 1 with v[i].x <= x (v sorted by increasing x, v[0].x <= x).
-__device__ __forceinline__ int edge_at(const int2 *v, int n, int x)
-{
-    int a = 0, b = n - 1;  // v[a].x <= x < v[b].x
-    while (b - a > 1) {
-        const int m = (a + b) >> 1;
-        if (v[m].x <= x)
-            a = m;
-        else
-            b = m;
-    }
-    return a;
-}
-
-// q strictly inside the polygon (x strictly between its extreme x).
-__device__ __forceinline__ bool strictly_inside(const CullPoly &cp, int2 q)
-{
-    if (q.x <= cp.xmin || q.x >= cp.xmax)
-        return false;
-    const int i = edge_at(cp.lo, cp.nlo, q.x), j = edge_at(cp.up, cp.nup, q.x);
-    return orient2(cp.lo[i], cp.lo[i + 1], q) > 0 && orient2(cp.up[j], cp.up[j + 1], q) < 0;
-}
-
-// Extremes of the set's chains and their polygon into cp; whole CTA.
-__device__ void build_cull_poly(int p, const int *slo, const int *shi, CullPoly &cp,
-                                unsigned long long *s_key, int *s_ends)
-{
-    // directions (dx, dy): k < 7 point down (lower chain), k >= 7 point up
-    constexpr int DX[14] = {-2, -1, -1, 0, 1, 1, 2, 2, 1, 1, 0, -1, -1, -2};
-    constexpr int DY[14] = {-1, -1, -2, -1, -2, -1, -1, 1, 1, 2, 1, 2, 1, 1};
-    if (threadIdx.x < 14)
-        s_key[threadIdx.x] = 0;
-    if (threadIdx.x == 0) {
-        s_ends[0] = p;
-        s_ends[1] = -1;
-    }
-    __syncthreads();
-    unsigned long long key[14];
-#pragma unroll
-    for (int k = 0; k < 14; ++k)
-        key[k] = 0;
-    int cmin = p, cmax = -1;
-    for (int c = threadIdx.x; c < p; c += BT) {
-        const int lo = slo[c], hi = shi[c];
-        if (lo > hi)
-            continue;
-        cmin = min(cmin, c);
-        cmax = max(cmax, c);
-        const int x = c + 1;
-#pragma unroll
-        for (int k = 0; k < 14; ++k) {
-            const int y = k < 7 ? lo : hi;
-            // dot + 2^17 > 0; ties go to the larger column (any input point will do)
-            const unsigned long long kv =
-                ((unsigned long long)(unsigned)(DX[k] * x + DY[k] * y + (1 << 17)) << 32) |
-                (unsigned)c;
-            key[k] = max(key[k], kv);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 14; ++k) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            key[k] = max(key[k], __shfl_xor_sync(0xFFFFFFFFu, key[k], o));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        cmin = min(cmin, __shfl_xor_sync(0xFFFFFFFFu, cmin, o));
-        cmax = max(cmax, __shfl_xor_sync(0xFFFFFFFFu, cmax, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int k = 0; k < 14; ++k)
-            if (key[k])
-                atomicMax(s_key + k, key[k]);
-        atomicMin(s_ends, cmin);
-        atomicMax(s_ends + 1, cmax);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        cp.nlo = cp.nup = 0;
-        const int c0 = s_ends[0], c1 = s_ends[1];
-        int2 v[18];
-        int m = 0;
-        if (c1 > c0) {  // at least two columns
-            v[m++] = make_int2(c0 + 1, slo[c0]);
-            v[m++] = make_int2(c0 + 1, shi[c0]);
-            v[m++] = make_int2(c1 + 1, slo[c1]);
-            v[m++] = make_int2(c1 + 1, shi[c1]);
-            for (int k = 0; k < 14; ++k) {
-                const int c = (int)(unsigned)(s_key[k] & 0xFFFFFFFFu);
-                v[m++] = make_int2(c + 1, k < 7 ? slo[c] : shi[c]);
-            }
-        }
-        // sort by (x, y), drop duplicates, Andrew's strict hull
-        for (int i = 1; i < m; ++i) {
-            const int2 t = v[i];
-            int j = i - 1;
-            while (j >= 0 && (v[j].x > t.x || (v[j].x == t.x && v[j].y > t.y))) {
-                v[j + 1] = v[j];
-                --j;
-            }
-            v[j + 1] = t;
-        }
-        int u = 0;
-        for (int i = 0; i < m; ++i)
-            if (u == 0 || v[i].x != v[u - 1].x || v[i].y != v[u - 1].y)
-                v[u++] = v[i];
-        m = u;
-        int nl = 0, nu = 0;
-        for (int i = 0; i < m; ++i) {  // lower boundary, left to right
-            while (nl >= 2 && orient2(cp.lo[nl - 2], cp.lo[nl - 1], v[i]) <= 0)
-                --nl;
-            cp.lo[nl++] = v[i];
-        }
-        for (int i = 0; i < m; ++i) {  // upper boundary, left to right
-            while (nu >= 2 && orient2(cp.up[nu - 2], cp.up[nu - 1], v[i]) >= 0)
-                --nu;
-            cp.up[nu++] = v[i];
-        }
-        // an interior needs both boundaries to span the x-range
-        if (m >= 3 && nl >= 2 && nu >= 2 && nl + nu >= 5) {
-            cp.nlo = nl;
-            cp.nup = nu;
-            cp.xmin = v[0].x;
-            cp.xmax = v[m - 1].x;
-        }
-    }
-    __syncthreads();
-}
+constexpr int SPARSE_TILE = 64;  // tiles with at most this many columns skip the pre-filter
 
 // Hull of the set whose L is in slo/shi (p columns); whole CTA.
 __device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 *scr,
-                           int2 *hull, int *hull_count, int *s_warp, int *s_total, int *s_cnt,
-                           CullPoly &cp, unsigned long long *s_key)
+                           int2 *hull, int *hull_count, int *s_warp, int *s_total, int *s_cnt)
 {
     int2 *A = reinterpret_cast<int2 *>(smem + SM_L);
     int2 *P0 = reinterpret_cast<int2 *>(smem + SM_L + SM_A);
@@ -271,22 +117,13 @@ __device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 
     // survivors are appended to the per-CTA global lists first (capacity p each)
     int2 *glo = scr, *gup = scr + BATCH_MAX_P;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    build_cull_poly(p, slo, shi, cp, s_key, s_cnt);
-    const bool cull = cp.nlo > 0;
     int T0 = 0, T1 = 0;
     for (int t0 = 0; t0 < p; t0 += RUN) {
         const int c = t0 + threadIdx.x;
         const bool valid = c < p && slo[c] <= shi[c];
-        int2 ql = make_int2(0, 0), qh = ql;
-        if (valid) {
-            ql = make_int2(c + 1, slo[c]);
-            qh = make_int2(c + 1, shi[c]);
-        }
-        const bool k0 = valid && !(cull && strictly_inside(cp, ql));
-        const bool k1 = valid && !(cull && strictly_inside(cp, qh));
-        const unsigned b0 = __ballot_sync(0xFFFFFFFFu, k0), b1 = __ballot_sync(0xFFFFFFFFu, k1);
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, valid);
         if (lane == 0)
-            s_warp[w] = __popc(b0) | (__popc(b1) << 16);
+            s_warp[w] = __popc(bal);
         __syncthreads();
         if (w == 0) {
             const int v = s_warp[lane];
@@ -302,30 +139,29 @@ __device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 
                 *s_cnt = incl;
         }
         __syncthreads();
-        const int cnt0 = *s_cnt & 0xFFFF, cnt1 = *s_cnt >> 16;
-        const unsigned below = (1u << lane) - 1u;
-        const int r0 = (s_warp[w] & 0xFFFF) + __popc(b0 & below);
-        const int r1 = (s_warp[w] >> 16) + __popc(b1 & below);
-        if (cnt0 <= SPARSE_TILE && cnt1 <= SPARSE_TILE) {  // few points: keep them all, the merge copes
-            if (k0)
-                glo[T0 + r0] = ql;
-            if (k1)
-                gup[T1 + r1] = make_int2(qh.x, -qh.y);
-            T0 += cnt0;
-            T1 += cnt1;
+        const int cnt = *s_cnt;
+        if (cnt <= SPARSE_TILE) {  // few columns: keep them all, the merge copes
+            if (valid) {
+                const int r = s_warp[w] + __popc(bal & ((1u << lane) - 1u));
+                glo[T0 + r] = make_int2(c + 1, slo[c]);
+                gup[T1 + r] = make_int2(c + 1, -shi[c]);
+            }
+            T0 += cnt;
+            T1 += cnt;
             __syncthreads();  // s_warp and s_cnt are rewritten by the next tile
             continue;
         }
-        if (k0)
-            P0[r0] = ql;
-        if (k1)
-            P1[r1] = make_int2(qh.x, -qh.y);
+        if (valid) {
+            const int r = s_warp[w] + __popc(bal & ((1u << lane) - 1u));
+            P0[r] = make_int2(c + 1, slo[c]);
+            P1[r] = make_int2(c + 1, -shi[c]);
+        }
         __syncthreads();
-        build_min_trees(P0, M0, cnt0, P1, M1, cnt1);
-        const bool f0 = run_keeps<true>(P0, M0, cnt0, threadIdx.x);
-        const bool f1 = run_keeps<true>(P1, M1, cnt1, threadIdx.x);
-        T0 += compact_run(P0, f0, glo + T0, s_warp);
-        T1 += compact_run(P1, f1, gup + T1, s_warp);
+        build_min_trees(P0, M0, cnt, P1, M1, cnt);
+        const bool k0 = run_keeps<true>(P0, M0, cnt, threadIdx.x);
+        const bool k1 = run_keeps<true>(P1, M1, cnt, threadIdx.x);
+        T0 += compact_run(P0, k0, glo + T0, s_warp);
+        T1 += compact_run(P1, k1, gup + T1, s_warp);
         __syncthreads();
     }
     const int T = T0 + T1;
@@ -357,10 +193,8 @@ __global__ void __launch_bounds__(BT, 1)
               unsigned char *scratch, unsigned *status)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_item, s_ticket, s_total, s_cnt[2];
+    __shared__ int s_item, s_ticket, s_total, s_cnt;
     __shared__ int s_warp[33];
-    __shared__ CullPoly s_poly;
-    __shared__ unsigned long long s_key[14];
     int *slo = reinterpret_cast<int *>(smem);
     int2 *scr = reinterpret_cast<int2 *>(scratch + (size_t)blockIdx.x * SCR_BYTES);
     bool bad = false;
@@ -412,7 +246,7 @@ __global__ void __launch_bounds__(BT, 1)
         }
         if (last)
             finish_set(p, slo, shi, smem, scr, hull_out + hull_offsets[item.set],
-                       hull_counts + item.set, s_warp, &s_total, s_cnt, s_poly, s_key);
+                       hull_counts + item.set, s_warp, &s_total, &s_cnt);
         __syncthreads();
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0)
