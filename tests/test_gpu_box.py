@@ -87,3 +87,17 @@ def test_box_sides_beyond_the_limit_are_rejected():
     assert e.value.code == ch.CH_ERR_ARG
     with pytest.raises(ch.ChError):
         ch.ch_convex_hull_box(d, [5, 4, 0, 10])  # empty box
+
+
+@pytest.mark.slow
+def test_box_path_at_bench_size():
+    """The bench's Steps 1-2 workload, one instance at full size (2^26 points
+    of a 120000 x 40000 box at (1e9, -2e9), columns along y): the box, the
+    hull through the user call, against the oracle's Steps 1-2."""
+    P = synth.boxed("disc", 1 << 26, 120_000, 40_000, 1_000_000_000, -2_000_000_000, seed=32)
+    H = oracle.hull_box(P)
+    d = dev(P).reshape(-1, 2)
+    box = host(ch.ch_bbox(d))
+    np.testing.assert_array_equal(box, [P[:, 0].min(), P[:, 0].max(), P[:, 1].min(), P[:, 1].max()])
+    del P
+    np.testing.assert_array_equal(host(ch.convex_hull(d)), H)
