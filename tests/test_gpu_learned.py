@@ -112,6 +112,15 @@ def test_learned_path_matches_oracle(dist, p, n):
     check_learned(P, p, params=_params(2))
 
 
+@pytest.mark.parametrize("dist", ("uniform", "disc", "annulus"))
+def test_learned_path_long_chains(dist):
+    """p = 262144: the global-L reduction form and 256 runs per chain, so the
+    survivors take the second filter pass before the final CTA."""
+    P = synth.points(dist, 2_000_000, 262_144, seed=12)
+    check_learned(P, 262_144)
+    check_learned(P, 262_144, params=_params(5))
+
+
 @pytest.mark.parametrize("p", [1, 2, 3, 5, 31, 33, 1025])
 @pytest.mark.parametrize("n", [0, 1, 2, 7, 1000])
 def test_learned_small_and_degenerate(p, n):
