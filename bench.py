@@ -212,6 +212,29 @@ def cpu_oracle_rate(p, inputs, budget_s):
     return done / dt / 1e9, dt, passes
 
 
+def cpu_andrew_all_points(p, inputs, m=1 << 22):
+    """The paper's comparison on the host: the hull of all points (sort +
+    Andrew, t_n) against Algorithm 1 + the hull of the reduced set
+    (t_r + t_s), single thread, on the first m points of each instance."""
+    import oracle
+    t_n = t_rs = 0.0
+    for _, P in inputs:
+        Q = np.ascontiguousarray(P[:m])
+        t0 = time.perf_counter()
+        a = oracle.hull_points(Q)
+        t1 = time.perf_counter()
+        b = oracle.hull_chain(oracle.reduce(Q, p))
+        t2 = time.perf_counter()
+        if not np.array_equal(a, b):
+            raise RuntimeError("oracle hulls differ")
+        t_n += t1 - t0
+        t_rs += t2 - t1
+    pts = m * len(inputs)
+    return {"sample": f"first {m} points of each instance, single thread",
+            "sort_andrew_gpoints_s": pts / t_n / 1e9, "reduce_then_hull_gpoints_s": pts / t_rs / 1e9,
+            "speedup_t_n_over_t_r_plus_t_s": t_n / t_rs}
+
+
 def workload_config(workload):
     """The `config` object of a workload, the same for both arms."""
     if workload == "learned":
@@ -473,6 +496,7 @@ def run_ours(args):
     achieved = kernel_bytes / (red_avg / 1e3) / 1e9
     kname = KERNEL_OF_FORM[ch.ch_plan_info(n, p)[0]]
     cpu_v, cpu_dt, cpu_passes = cpu_oracle_rate(p, inputs, args.cpu_budget)
+    cpu_tn = cpu_andrew_all_points(p, inputs)
     line = {
         "metric": METRIC,
         "value": value,
@@ -498,7 +522,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps},
         "cpu_baseline": {"value": cpu_v, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
                          "sample": f"{cpu_passes} pass(es) over the step's {len(inputs)} instances "
-                                   f"({cpu_dt:.1f} s, single thread)"},
+                                   f"({cpu_dt:.1f} s, single thread)",
+                         "hull_of_all_points": cpu_tn},
         "gpu_launches": args.steps * len(inputs) * ch.ch_plan_info(n, p)[1],
         "clocks": clocks,
         "hull_vertices": hsz,
