@@ -230,8 +230,9 @@ def cpu_andrew_all_points(p, inputs, m=1 << 22):
             raise RuntimeError("oracle hulls differ")
         t_n += t1 - t0
         t_rs += t2 - t1
-    pts = m * len(inputs)
-    return {"sample": f"first {m} points of each instance, single thread",
+    pts = sum(min(m, P.shape[0]) for _, P in inputs)
+    return {"sample": f"the first {min(m, inputs[0][1].shape[0])} points of each instance, "
+                      f"single thread",
             "sort_andrew_gpoints_s": pts / t_n / 1e9, "reduce_then_hull_gpoints_s": pts / t_rs / 1e9,
             "speedup_t_n_over_t_r_plus_t_s": t_n / t_rs}
 
