@@ -88,8 +88,9 @@ int ch_trace_set(void *const *events, int npairs);
 /* How ch_convex_hull will run n points of side p on the current device:
  * *form = 0 (private shared-memory copies of L, p <= 29056), 1 (filtered
  * global L, p <= 116224) or 2 (global L with a read-then-atomic test), and
- * *kernels = the number of kernels one ch_convex_hull call launches.  Either
- * pointer may be NULL. */
+ * *kernels = the number of kernels one ch_convex_hull call launches (with the
+ * second filter pass of the hull step from 128 runs of 1024 columns on).
+ * Either pointer may be NULL. */
 int ch_plan_info(int64_t n, int32_t p, int32_t *form, int32_t *kernels);
 
 /* ---------------------------------------------------------------------- */
