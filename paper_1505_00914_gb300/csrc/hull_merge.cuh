@@ -200,7 +200,9 @@ __device__ void merge_tree(Tree &t)
 }
 
 // True when point i of the chain stored at D[cs..ce) lies on or above a
-// segment between two of its neighbours (at most two places away).
+// segment between two of its neighbours: any of the pairs at most two places
+// away, or the pairs three and four places away on both sides (those end a
+// long concave run in fewer rounds).
 __device__ __forceinline__ bool peel_drops(const int2 *D, int cs, int ce, int i)
 {
     if (i - 1 < cs || i + 1 >= ce)
@@ -210,8 +212,13 @@ __device__ __forceinline__ bool peel_drops(const int2 *D, int cs, int ce, int i)
         return true;
     const bool l2 = i - 2 >= cs, r2 = i + 2 < ce;
     const int2 a2 = l2 ? D[i - 2] : l1, b2 = r2 ? D[i + 2] : r1;
-    return (r2 && cross3(l1, b2, q) >= 0) || (l2 && cross3(a2, r1, q) >= 0) ||
-           (l2 && r2 && cross3(a2, b2, q) >= 0);
+    if ((r2 && cross3(l1, b2, q) >= 0) || (l2 && cross3(a2, r1, q) >= 0) ||
+        (l2 && r2 && cross3(a2, b2, q) >= 0))
+        return true;
+    const bool l3 = i - 3 >= cs, r3 = i + 3 < ce, l4 = i - 4 >= cs, r4 = i + 4 < ce;
+    const int2 a3 = l3 ? D[i - 3] : a2, b3 = r3 ? D[i + 3] : b2;
+    const int2 a4 = l4 ? D[i - 4] : a3, b4 = r4 ? D[i + 4] : b3;
+    return (l3 && r3 && cross3(a3, b3, q) >= 0) || (l4 && r4 && cross3(a4, b4, q) >= 0);
 }
 
 // Peel, merge fallback and stitch, run by a whole CTA of FT threads.  A holds
