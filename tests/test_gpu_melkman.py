@@ -226,3 +226,27 @@ def test_full_scale_coordinates_at_the_32_bit_boundary(p):
     poly = np.concatenate([lo, hi]).astype(np.int32)
     np.testing.assert_array_equal(oracle.melkman(poly), oracle.hull_points(poly))
     np.testing.assert_array_equal(gpu_melkman(poly, p), oracle.hull_points(poly))
+
+
+def test_coordinates_up_to_two_to_the_thirty():
+    """p = 2^30, the largest side: the deque in global memory and the 64-bit
+    orientation, on star-shaped polylines spanning the whole square (vertices
+    in angular order around the centre, every gap below pi, so simple)."""
+    p = 1 << 30
+    rng = np.random.default_rng(30)
+    c = (p + 1) // 2
+    for m in (5, 300, 20_000):
+        ang = np.sort(rng.uniform(-np.pi, np.pi, size=m))
+        ang = ang[np.concatenate([[True], np.diff(ang) > 1e-6])]
+        r = rng.uniform(0.2, 0.499, size=ang.shape[0]) * p
+        poly = np.stack([c + np.rint(r * np.cos(ang)), c + np.rint(r * np.sin(ang))], 1)
+        poly = poly.astype(np.int64)
+        d = poly - c
+        a2 = np.arctan2(d[:, 1], d[:, 0])
+        gaps = np.diff(np.concatenate([a2, a2[:1] + 2 * np.pi]))
+        assert np.all(np.diff(a2) > 0) and np.all(gaps < np.pi)  # still a star in angular order
+        poly = poly[:-1].astype(np.int32)  # open
+        assert poly.min() >= 1 and poly.max() <= p
+        H = oracle.hull_points(poly)
+        np.testing.assert_array_equal(oracle.melkman(poly), H)
+        np.testing.assert_array_equal(gpu_melkman(poly, p), H)
