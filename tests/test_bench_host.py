@@ -1,0 +1,49 @@
+"""Host-side logic of bench.py (no GPU): the packed 16-bit point format,
+the workload descriptions (each says how L2 is handled), the traffic lookup
+keyed by the kernel's source, and the host t_n comparison."""
+import numpy as np
+import pytest
+
+import bench
+from paper_1505_00914_gb300 import synth
+
+
+def test_pack_u16_layout():
+    P = np.asarray([[1, 1], [65536, 1], [1, 65536], [300, 7000]], np.int32)
+    w = bench.pack_u16(P).view(np.uint32)
+    np.testing.assert_array_equal(w & 0xFFFF, P[:, 0] - 1)
+    np.testing.assert_array_equal(w >> 16, P[:, 1] - 1)
+    # little-endian uint16 pairs (x - 1, y - 1)
+    np.testing.assert_array_equal(w.view(np.uint16).reshape(-1, 2), P - 1)
+
+
+@pytest.mark.parametrize("workload", sorted(bench.WORKLOADS) + ["learned", "batched", "box",
+                                                                 "melkman", "rxy", "sparse"])
+def test_every_workload_has_a_config(workload):
+    c = bench.workload_config(workload)
+    assert c["workload"] == workload
+    assert "l2" in c and ("256 MB write" in c["l2"] or "larger than L2" in c["l2"])
+
+
+def test_small_inputs_are_flushed_and_large_ones_not():
+    assert "256 MB write" in bench.workload_config("projected_shells")["l2"]
+    assert "256 MB write" in bench.workload_config("plain_small")["l2"]
+    assert "no flush" in bench.workload_config("plain_at_scale")["l2"]
+    assert "no flush" in bench.workload_config("plain_at_scale_u16")["l2"]
+
+
+def test_traffic_lookup_follows_the_kernel_source():
+    t = bench._traffic("k_reduce_filtered", 1 << 26, 65536)
+    assert t is not None and 8 * (1 << 26) <= t <= 1.05 * 8 * (1 << 26)
+    t16 = bench._traffic("k_reduce_filtered", 1 << 26, 65536, u16=True)
+    assert t16 is not None and 4 * (1 << 26) <= t16 <= 1.05 * 4 * (1 << 26)
+    assert bench._traffic("k_reduce_filtered", 1 << 26, 4096) is None  # captured at another p
+    assert bench._traffic("k_reduce_private", 1 << 26, 65536) is None
+
+
+def test_host_t_n_comparison():
+    p = 1024
+    inputs = [(d, synth.points(d, 50_000, p, seed=3)) for d in ("uniform", "disc")]
+    r = bench.cpu_andrew_all_points(p, inputs, m=20_000)
+    assert r["speedup_t_n_over_t_r_plus_t_s"] > 0
+    assert r["sort_andrew_gpoints_s"] > 0 and r["reduce_then_hull_gpoints_s"] > 0
