@@ -262,7 +262,8 @@ def workload_config(workload):
         p, n, dists = WORKLOADS[MELKMAN]
         return {"workload": workload, "p": p, "n_per_instance": n, "distributions": list(dists),
                 "instances_per_step": 1,
-                "l2": "80 MB of points, below L2 (129 MB): an L2 flush precedes every step"}
+                "l2": "80 MB of points, below L2 (129 MB): a 256 MB write precedes every step "
+                      "and its time is subtracted"}
     if workload == "batched":
         return {"workload": "batched", "sets": BATCH_SETS, "ps": [256, 1024, 4096, 16384],
                 "n_range": [100, 1_000_000], "distributions": ["uniform", "disc", "gaussian"],
