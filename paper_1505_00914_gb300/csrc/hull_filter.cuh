@@ -23,43 +23,30 @@ constexpr int RUN_LOG = 10;
 // tree_off(k); 2 * RUN shorts hold every level.
 __device__ __forceinline__ int tree_off(int k) { return 2 * RUN - ((2 * RUN) >> (k - 1)); }
 
-// The better of two point indices of P[0..n) for a min-tree node: the
-// lower y, ties to the left (a); -1 stands for no point.
-__device__ __forceinline__ int tree_pick(const int2 *P, int n, int a, int b)
-{
-    const bool va = a >= 0 && a < n, vb = b >= 0 && b < n;
-    if (!va)
-        return vb ? b : -1;
-    return (vb && P[b].y < P[a].y) ? b : a;
-}
-
-// Builds the min-y index trees of two runs, P0[0..n0) and P1[0..n1); every
-// thread of the CTA calls it.  Two levels per step: thread t combines the
-// four nodes under node t of level 2s (points for s = 1) into the two nodes
-// of level 2s - 1 and the node of level 2s, so the ten levels cost five
-// block barriers.
+// Builds the min-y index trees of two runs, P0[0..n0) and P1[0..n1), level by
+// level; every thread of the CTA calls it.
 __device__ __forceinline__ void build_min_trees(const int2 *P0, short *M0, int n0, const int2 *P1,
                                                 short *M1, int n1)
 {
-    const int t = threadIdx.x;
-#pragma unroll
-    for (int s = 1; 2 * s <= RUN_LOG; ++s) {
-        const int k = 2 * s;
-        if (t < (RUN >> k)) {
-            int a0[4], a1[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                a0[u] = k == 2 ? 4 * t + u : M0[tree_off(k - 2) + 4 * t + u];
-                a1[u] = k == 2 ? 4 * t + u : M1[tree_off(k - 2) + 4 * t + u];
+    const int i = threadIdx.x;
+    for (int k = 1; k <= RUN_LOG; ++k) {
+        if (i < (RUN >> k)) {
+            int a0, b0, a1, b1;
+            if (k == 1) {
+                a0 = a1 = 2 * i;
+                b0 = b1 = 2 * i + 1;
+            } else {
+                a0 = M0[tree_off(k - 1) + 2 * i];
+                b0 = M0[tree_off(k - 1) + 2 * i + 1];
+                a1 = M1[tree_off(k - 1) + 2 * i];
+                b1 = M1[tree_off(k - 1) + 2 * i + 1];
             }
-            const int l0 = tree_pick(P0, n0, a0[0], a0[1]), r0 = tree_pick(P0, n0, a0[2], a0[3]);
-            const int l1 = tree_pick(P1, n1, a1[0], a1[1]), r1 = tree_pick(P1, n1, a1[2], a1[3]);
-            M0[tree_off(k - 1) + 2 * t] = (short)l0;
-            M0[tree_off(k - 1) + 2 * t + 1] = (short)r0;
-            M0[tree_off(k) + t] = (short)tree_pick(P0, n0, l0, r0);
-            M1[tree_off(k - 1) + 2 * t] = (short)l1;
-            M1[tree_off(k - 1) + 2 * t + 1] = (short)r1;
-            M1[tree_off(k) + t] = (short)tree_pick(P1, n1, l1, r1);
+            const bool va0 = a0 >= 0 && a0 < n0, vb0 = b0 >= 0 && b0 < n0;
+            const bool va1 = a1 >= 0 && a1 < n1, vb1 = b1 >= 0 && b1 < n1;
+            const int ya0 = va0 ? P0[a0].y : 0, yb0 = vb0 ? P0[b0].y : 0;
+            const int ya1 = va1 ? P1[a1].y : 0, yb1 = vb1 ? P1[b1].y : 0;
+            M0[tree_off(k) + i] = (short)(va0 ? ((vb0 && yb0 < ya0) ? b0 : a0) : (vb0 ? b0 : -1));
+            M1[tree_off(k) + i] = (short)(va1 ? ((vb1 && yb1 < ya1) ? b1 : a1) : (vb1 ? b1 : -1));
         }
         __syncthreads();
     }
