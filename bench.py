@@ -264,10 +264,13 @@ def workload_config(workload):
                 "instances_per_step": 1,
                 "l2": "80 MB of points, below L2 (129 MB): a 256 MB write precedes every step "
                       "and its time is subtracted"}
-    if workload == "batched":
-        return {"workload": "batched", "sets": BATCH_SETS, "ps": [256, 1024, 4096, 16384],
+    if workload in ("batched", "profile_batched"):
+        return {"workload": workload,
+                "sets": BATCH_SETS if workload == "batched" else PROFILE_BATCH_SETS,
+                "ps": [256, 1024, 4096, 16384],
                 "n_range": [100, 1_000_000], "distributions": ["uniform", "disc", "gaussian"],
-                "l2": "about 8.5 GB of points per step, larger than L2; no flush"}
+                "l2": ("about 8.5 GB" if workload == "batched" else "about 0.9 GB")
+                      + " of points per step, larger than L2; no flush"}
     p, n, dists = WORKLOADS[workload]
     bpp = 4 if workload.endswith("_u16") else 8
     return {"workload": workload, "p": p, "n_per_instance": n, "distributions": list(dists),
@@ -565,6 +568,7 @@ def box_inputs(rank):
             for i, (d, sx, sy, x0, y0) in enumerate(BOX)]
 WEIGHTS = os.path.join(ROOT, "paper_1505_00914_gb300", "weights", "cull_mlp_k16.npz")
 BATCH_SETS = 10_000
+PROFILE_BATCH_SETS = 1_000  # the profiling case of the batched kernel (~0.9 GB of points)
 
 
 def _setup_dist():
@@ -776,7 +780,8 @@ def run_batched(args):
     torch, dist, world, rank = _setup_dist()
     from paper_1505_00914_gb300 import autotune, ch, synth
     ch.lib()
-    pts, off, ps, _ = synth.batched(BATCH_SETS, seed=4 + 1000 * rank)
+    sets = BATCH_SETS if args.workload == "batched" else PROFILE_BATCH_SETS
+    pts, off, ps, _ = synth.batched(sets, seed=4 + 1000 * rank)
     ps = ps.astype(np.int32)
     B = len(ps)
     n_tot = int(off[-1])
@@ -787,7 +792,10 @@ def run_batched(args):
     d_hoff = torch.from_numpy(hoff).cuda()
     hull = torch.zeros((int(hoff[-1]), 2), dtype=torch.int32, device="cuda")
     cnt = torch.zeros(B, dtype=torch.int32, device="cuda")
-    best, tune_ms = autotune.tune_batched(d_pts, off, ps, d_off, d_ps, hull, d_hoff, cnt)
+    if args.no_aux:  # profiling runs: the usual choice, no tuning launches
+        best, tune_ms = 1024, {}
+    else:
+        best, tune_ms = autotune.tune_batched(d_pts, off, ps, d_off, d_ps, hull, d_hoff, cnt)
     ws = torch.empty(ch.ch_batched_workspace_size(off, ps, best), dtype=torch.uint8, device="cuda")
     ch.ch_batched_prepare(off, ps, ws, best)
     stream = torch.cuda.Stream()
@@ -870,7 +878,7 @@ def run_batched(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": workload_config("batched"),
+        "config": workload_config(args.workload),
         "batched": {"points": n_tot, "chunk_mult": best,
                     "launch": "one captured CUDA graph replay per step",
                     "per_set_plain_gpoints_s": world * n_tot / (ms_plain / 1e3) / 1e9,
@@ -1369,7 +1377,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["learned", "batched", "box",
-                                                                "melkman", "rxy", "sparse"],
+                                                                "melkman", "rxy", "sparse",
+                                                                "profile_batched"],
                     default="plain_at_scale")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-aux", action="store_true",
@@ -1382,7 +1391,7 @@ def main():
         run_reference(args)
     elif args.workload == "learned":
         run_learned(args)
-    elif args.workload == "batched":
+    elif args.workload in ("batched", "profile_batched"):
         run_batched(args)
     elif args.workload == "box":
         run_box(args)

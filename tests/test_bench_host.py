@@ -17,7 +17,7 @@ def test_pack_u16_layout():
     np.testing.assert_array_equal(w.view(np.uint16).reshape(-1, 2), P - 1)
 
 
-@pytest.mark.parametrize("workload", sorted(bench.WORKLOADS) + ["learned", "batched", "box",
+@pytest.mark.parametrize("workload", sorted(bench.WORKLOADS) + ["learned", "batched", "box", "profile_batched",
                                                                  "melkman", "rxy", "sparse"])
 def test_every_workload_has_a_config(workload):
     c = bench.workload_config(workload)
