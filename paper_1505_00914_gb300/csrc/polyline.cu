@@ -15,11 +15,12 @@
 //             entries at each end take part in the tests, so they live in
 //             registers and the deque itself in shared memory (global memory
 //             when the hull can outgrow it).  The vertex stream is staged in
-//             shared memory 1024 at a time.  The 32 lanes test the next 32
-//             vertices against the current hull at once (a skipped vertex
+//             shared memory 1024 at a time.  The next vertex is tested on
+//             its own; after one that is inside, the 32 lanes test the next
+//             32 vertices against the current hull at once (a skipped vertex
 //             leaves the hull unchanged, so every test of the batch up to the
-//             first vertex outside is the sequential test); the update for a
-//             vertex outside is sequential, executed by all lanes alike.
+//             first vertex outside is the sequential test).  The update for
+//             a vertex outside is sequential, executed by all lanes alike.
 //             Skipping on "left of or on" and popping on "not strictly left"
 //             drop collinear points: the hull lists strict vertices,
 //             counter-clockwise from the lexicographic minimum.
@@ -255,19 +256,32 @@ __global__ void __launch_bounds__(32)
         }
         if (phase == 1) {
             while (i < cnt) {
-                const int j = i + lane;
-                bool out = false;
-                if (j < cnt) {
-                    const int2 u = stage[j];
-                    out = !(orient<SMALL>(t1, t0, u) >= 0 && orient<SMALL>(b0, b1, u) >= 0);
+                // the next vertex alone first: on a polyline that keeps
+                // leaving the hull (as Lemma 1's does) that is the common case
+                int2 u = stage[i];
+                if (orient<SMALL>(t1, t0, u) >= 0 && orient<SMALL>(b0, b1, u) >= 0) {
+                    // inside: skip on, testing 32 vertices at a time
+                    ++i;
+                    bool found = false;
+                    while (i < cnt) {
+                        const int j = i + lane;
+                        bool out = false;
+                        if (j < cnt) {
+                            const int2 v = stage[j];
+                            out = !(orient<SMALL>(t1, t0, v) >= 0 && orient<SMALL>(b0, b1, v) >= 0);
+                        }
+                        const unsigned ob = __ballot_sync(FULL, out);
+                        if (ob) {
+                            i += __ffs(ob) - 1;
+                            found = true;
+                            break;
+                        }
+                        i += 32;
+                    }
+                    if (!found)
+                        break;
+                    u = stage[i];
                 }
-                const unsigned ob = __ballot_sync(FULL, out);
-                if (!ob) {
-                    i += 32;
-                    continue;
-                }
-                i += __ffs(ob) - 1;
-                const int2 u = stage[i];
                 ++i;
                 // top: pop while u is not strictly left of the top edge
                 while (top - bot > 1 && orient<SMALL>(t1, t0, u) <= 0) {
