@@ -254,11 +254,11 @@ __global__ void __launch_bounds__(32)
                 ++k;
             }
         }
-        if (phase == 1 && i < cnt) {
-            int2 u = stage[i];
-            for (;;) {
+        if (phase == 1) {
+            while (i < cnt) {
                 // the next vertex alone first: on a polyline that keeps
                 // leaving the hull (as Lemma 1's does) that is the common case
+                int2 u = stage[i];
                 if (orient<SMALL>(t1, t0, u) >= 0 && orient<SMALL>(b0, b1, u) >= 0) {
                     // inside: skip on, testing 32 vertices at a time
                     ++i;
@@ -283,8 +283,6 @@ __global__ void __launch_bounds__(32)
                     u = stage[i];
                 }
                 ++i;
-                const bool more = i < cnt;
-                const int2 nxt = more ? stage[i] : u;  // in flight during the update
                 // top: pop while u is not strictly left of the top edge
                 while (top - bot > 1 && orient<SMALL>(t1, t0, u) <= 0) {
                     --top;
@@ -313,9 +311,6 @@ __global__ void __launch_bounds__(32)
                 dq[(unsigned)bot & mask] = u;
                 b1 = b0;
                 b0 = u;
-                if (!more)
-                    break;
-                u = nxt;
             }
             if (bad && lane == 0)
                 atomicOr(status, ST_CAPACITY);
