@@ -201,10 +201,7 @@ __global__ void __launch_bounds__(32)
     int k = 0;                     // vertices of the collinear prefix
     int2 a = make_int2(0, 0), b = a;  // its lexicographic extremes
     int top = 0, bot = 0;          // deque ends, taken modulo dq_cap
-    // D[top-2], D[top-1], D[top] and D[bot], D[bot+1], D[bot+2]: each pop
-    // shifts them and loads the next one, which is only needed by the pop
-    // after, so no pop waits for shared memory
-    int2 t2 = a, t1 = a, t0 = a, b0 = a, b1 = a, b2 = a;
+    int2 t1 = a, t0 = a, b0 = a, b1 = a;  // D[top-1], D[top], D[bot], D[bot+1]
     bool bad = false;
     for (int base = 0; base < m && !bad; base += MK_STAGE) {
         const int cnt = min(MK_STAGE, m - base);
@@ -244,8 +241,6 @@ __global__ void __launch_bounds__(32)
                     top = 3;
                     b0 = u;
                     b1 = q1;
-                    b2 = q2;
-                    t2 = q1;
                     t1 = q2;
                     t0 = u;
                     phase = 1;
@@ -288,24 +283,11 @@ __global__ void __launch_bounds__(32)
                     u = stage[i];
                 }
                 ++i;
-                // a push can overwrite an entry cached for the other end only
-                // while the deque holds four entries or fewer: reload then
-                auto reload = [&]() {
-                    if (top - bot <= 3) {
-                        t0 = dq[(unsigned)top & mask];
-                        t1 = dq[(unsigned)(top - 1) & mask];
-                        t2 = top - 2 >= bot ? dq[(unsigned)(top - 2) & mask] : t1;
-                        b0 = dq[(unsigned)bot & mask];
-                        b1 = dq[(unsigned)(bot + 1) & mask];
-                        b2 = bot + 2 <= top ? dq[(unsigned)(bot + 2) & mask] : b1;
-                    }
-                };
                 // top: pop while u is not strictly left of the top edge
                 while (top - bot > 1 && orient<SMALL>(t1, t0, u) <= 0) {
                     --top;
                     t0 = t1;
-                    t1 = t2;
-                    t2 = dq[(unsigned)(top - 2) & mask];  // used only by a further pop
+                    t1 = dq[(unsigned)(top - 1) & mask];
                 }
                 if (top + 1 - bot + 1 > (int)dq_cap) {
                     bad = true;
@@ -313,16 +295,13 @@ __global__ void __launch_bounds__(32)
                 }
                 ++top;
                 dq[(unsigned)top & mask] = u;  // every lane stores the same value
-                t2 = t1;
                 t1 = t0;
                 t0 = u;
-                reload();
                 // bottom: pop while (u, D[bot], D[bot+1]) is not a strict left turn
                 while (top - bot > 1 && orient<SMALL>(u, b0, b1) <= 0) {
                     ++bot;
                     b0 = b1;
-                    b1 = b2;
-                    b2 = dq[(unsigned)(bot + 2) & mask];  // used only by a further pop
+                    b1 = dq[(unsigned)(bot + 1) & mask];
                 }
                 if (top - (bot - 1) + 1 > (int)dq_cap) {
                     bad = true;
@@ -330,10 +309,8 @@ __global__ void __launch_bounds__(32)
                 }
                 --bot;
                 dq[(unsigned)bot & mask] = u;
-                b2 = b1;
                 b1 = b0;
                 b0 = u;
-                reload();
             }
             if (bad && lane == 0)
                 atomicOr(status, ST_CAPACITY);
