@@ -243,6 +243,7 @@ def workload_config(workload):
         p, n, dists = LEARNED
         return {"workload": "learned", "p": p, "n_per_instance": n, "distributions": list(dists),
                 "instances_per_step": len(dists),
+                "concurrency": "each instance on its own CUDA stream and workspace, in every arm",
                 "l2": "inputs 8n bytes per instance, larger than L2; no flush"}
     if workload == "box":
         return {"workload": "box", "n_per_instance": BOX_N,
@@ -620,23 +621,38 @@ def run_learned(args):
     have_w = os.path.exists(WEIGHTS)
     params = train.load_params(WEIGHTS) if have_w else None
     nws = max(ch.ch_hull_learned_workspace_size(n, p), ch.ch_convex_hull_workspace_size(n, p))
-    ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+    # as in the plain workload, the independent instances of a step run on
+    # their own streams and workspaces, in every arm alike
+    wss = [torch.empty(nws, dtype=torch.uint8, device="cuda") for _ in inputs]
+    ws = wss[0]
     stream = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream() for _ in inputs]
     arms = ("learned", "centres", "plain")
     hulls = {a: [torch.empty((2 * p, 2), dtype=torch.int32, device="cuda") for _ in inputs] for a in arms}
     hcs = {a: [torch.empty(1, dtype=torch.int32, device="cuda") for _ in inputs] for a in arms}
     Linit = {a: [torch.empty((p, 2), dtype=torch.int32, device="cuda") for _ in inputs]
              for a in ("learned", "centres")}
 
-    def step(arm):
+    def step(arm, concurrent=True):
+        sts = streams if concurrent else [stream] * len(inputs)
+        if concurrent:
+            fork = torch.cuda.Event()
+            fork.record(stream)
         for i, d in enumerate(dev_in):
-            h, c = hulls[arm][i], hcs[arm][i]
+            h, c, st = hulls[arm][i], hcs[arm][i], sts[i]
+            if concurrent:
+                st.wait_event(fork)
             if arm == "plain":
-                ch.ch_convex_hull(d, p, hull=h, hull_count=c, workspace=ws, stream=stream)
+                ch.ch_convex_hull(d, p, hull=h, hull_count=c, workspace=wss[i], stream=st)
             else:
                 ch.ch_hull_learned(d, p, params=params if arm == "learned" else None,
-                                   Linit=Linit[arm][i], hull=h, hull_count=c, workspace=ws,
-                                   stream=stream)
+                                   Linit=Linit[arm][i], hull=h, hull_count=c, workspace=wss[i],
+                                   stream=st)
+        if concurrent:
+            for st in streams:
+                join = torch.cuda.Event()
+                join.record(st)
+                stream.wait_event(join)
 
     for arm in arms:
         for _ in range(args.warmup):
@@ -701,8 +717,10 @@ def run_learned(args):
     ms = {}
     for arm in ("learned", "plain", "centres"):
         ms[arm] = _timed(torch, dist, world, lambda arm=arm: step(arm), args.steps, stream)
-    ch.ch_trace_set(evs)  # the learned arm again, the reduction kernel timed by events
-    ms_traced = _timed(torch, dist, world, lambda: step("learned"), args.steps, stream)
+    for _ in range(2):
+        step("learned", False)
+    ch.ch_trace_set(evs)  # the learned arm again, one instance after another, reductions timed
+    ms_traced = _timed(torch, dist, world, lambda: step("learned", False), args.steps, stream)
     ch.ch_trace_set([])
     clocks = sampler.stop()
     rc = ch.ch_sync_status()
