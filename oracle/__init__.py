@@ -172,6 +172,19 @@ def rxy_points(R) -> np.ndarray:
     return np.ascontiguousarray(q[:, ::-1])
 
 
+def tree_words(p: int, w: int) -> list[int]:
+    """Words per level of the w-ary tree of bit words over p columns
+    (Section 4, "Extraction using a tree structure"): level 0 has one bit per
+    column, each level above one bit per word of the level below, up to a
+    single word."""
+    words, n = [], p
+    while True:
+        n = -(-n // w)
+        words.append(n)
+        if n <= 1:
+            return words
+
+
 def mask(L) -> np.ndarray:
     """Bit array M ("Extraction using an array of bits"): uint32 words,
     column i at bit (i-1)&31 of word (i-1)>>5."""

@@ -54,3 +54,16 @@ def test_library_loads_and_binds_without_gpu(lib_path):
 def test_objects_target_sm_103a(lib_path):
     """The build passes one -gencode, for sm_103a only."""
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
+
+
+def test_sparse_workspace_holds_the_tree_of_bit_words():
+    """The persistent part of the sparse path's workspace is L (8 bytes a
+    column) and the 32-bit words of every level of the w = 32 tree, each
+    region rounded up to 256 bytes (no GPU needed for the size query)."""
+    import oracle
+    from paper_1505_00914_gb300 import ch
+    r = lambda b: (b + 255) // 256 * 256
+    for p in (1, 31, 32, 33, 1024, 1025, 65536, 1 << 24, (1 << 30) - 7, 1 << 30):
+        expect = r(8 * p) + sum(r(4 * k) for k in oracle.tree_words(p, 32))
+        assert ch.ch_sparse_workspace_size(1000, p)[1] == expect, p
+        assert len(oracle.tree_words(p, 32)) <= 7

@@ -210,3 +210,18 @@ def test_second_scan_is_algorithm1_on_the_transposed_rx_points():
         rxy = oracle.rxy_points(oracle.reduce_rows(L))
         assert rxy.shape[0] < oracle.rx_points(L).shape[0]
         np.testing.assert_array_equal(oracle.hull_points(rxy), oracle.hull_points(P))
+
+
+def test_tree_sizes_printed_in_the_paper():
+    """Section 4: for p = 2^24 and 64-bit words the tree has height 3 above
+    its leaf words and 266305 words, 4161 more than the flat array of 262144
+    words; height h = log_w((w - 1) p + w) - 2 and m = (w^(h+1) - 1)/(w - 1)."""
+    import math
+    p, w = 1 << 24, 64
+    words = oracle.tree_words(p, w)
+    assert words == [262144, 4096, 64, 1]
+    assert sum(words) == 266305 and sum(words) - words[0] == 4161
+    h = len(words) - 1
+    assert h == 3 == math.ceil(math.log((w - 1) * p + w, w) - 2)
+    assert sum(words) == (w ** (h + 1) - 1) // (w - 1)
+    assert oracle.tree_words(1, 32) == [1] and oracle.tree_words(33, 32) == [2, 1]
