@@ -13,7 +13,10 @@ Prints ONE JSON line (rank 0).  `value` is device-timed whole-job throughput in
 Gpoints/s; `e2e` is the same metric through ch_convex_hull_host (host buffers,
 copies inside the timed region); `roofline` is for the dominant kernel (the
 reduction), timed per launch with CUDA events recorded on its stream;
-`cpu_baseline` is the CPU oracle on the host cores.  `value` comes from a
+`cpu_baseline` is the CPU oracle on one host core (Algorithm 1 + the hull of
+the reduced set), with two more host figures beside it: the hull of all points
+by sort + Andrew (the paper's t_n) and Algorithm 1 alone on every host core
+(one L per thread, merged by min/max).  `value` comes from a
 timed region without instrumentation; the roofline's launch times come from
 a second timed region of the same steps, instances one after another on one
 stream, with events around each reduction launch (its step time is reported
@@ -235,6 +238,45 @@ def cpu_andrew_all_points(p, inputs, m=1 << 22):
                       f"single thread",
             "sort_andrew_gpoints_s": pts / t_n / 1e9, "reduce_then_hull_gpoints_s": pts / t_rs / 1e9,
             "speedup_t_n_over_t_r_plus_t_s": t_n / t_rs}
+
+
+def cpu_reduce_all_cores(p, inputs, passes=3):
+    """Algorithm 1 on every host core: each thread reduces a contiguous shard
+    of an instance into its own L with the oracle, and the partial arrays are
+    merged column by column (min of ly, max of hy; exact because min and max
+    commute).  The oracle's C call releases the interpreter lock, so the
+    threads run in parallel.  Best of `passes` passes over all instances."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = max(1, int(threads or 1))
+
+    def shards(P):
+        cut = np.linspace(0, P.shape[0], threads + 1).astype(np.int64)
+        return [P[cut[k]:cut[k + 1]] for k in range(threads)]
+
+    parts = [shards(P) for _, P in inputs]
+    best, merged = None, []
+    with ThreadPoolExecutor(max_workers=threads) as pool:
+        for _ in range(passes):
+            merged = []
+            t0 = time.perf_counter()
+            for sh in parts:
+                Ls = list(pool.map(lambda q: oracle.reduce(q, p), sh))
+                L = Ls[0].copy()
+                for Lk in Ls[1:]:
+                    np.minimum(L[:, 0], Lk[:, 0], out=L[:, 0])
+                    np.maximum(L[:, 1], Lk[:, 1], out=L[:, 1])
+                merged.append(L)
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+    for L, (_, P) in zip(merged, inputs):
+        if not np.array_equal(L, oracle.reduce(P, p)):
+            raise RuntimeError("merged partial arrays differ from one pass of Algorithm 1")
+    pts = sum(P.shape[0] for _, P in inputs)
+    return {"reduce_gpoints_s": pts / best / 1e9, "threads": threads,
+            "sample": f"all {len(inputs)} instances, Algorithm 1 only, one L per thread "
+                      f"merged by min/max, best of {passes} passes"}
 
 
 def workload_config(workload):
@@ -514,6 +556,7 @@ def run_ours(args):
     kname = KERNEL_OF_FORM[ch.ch_plan_info(n, p)[0]]
     cpu_v, cpu_dt, cpu_passes = cpu_oracle_rate(p, inputs, args.cpu_budget)
     cpu_tn = cpu_andrew_all_points(p, inputs)
+    cpu_mt = cpu_reduce_all_cores(p, inputs)
     line = {
         "metric": METRIC,
         "value": value,
@@ -540,7 +583,7 @@ def run_ours(args):
         "cpu_baseline": {"value": cpu_v, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
                          "sample": f"{cpu_passes} pass(es) over the step's {len(inputs)} instances "
                                    f"({cpu_dt:.1f} s, single thread)",
-                         "hull_of_all_points": cpu_tn},
+                         "hull_of_all_points": cpu_tn, "reduce_all_cores": cpu_mt},
         "gpu_launches": args.steps * len(inputs) * ch.ch_plan_info(n, p)[1],
         "clocks": clocks,
         "l2_flush_ms_subtracted": fl / args.steps,

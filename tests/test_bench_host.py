@@ -47,3 +47,14 @@ def test_host_t_n_comparison():
     r = bench.cpu_andrew_all_points(p, inputs, m=20_000)
     assert r["speedup_t_n_over_t_r_plus_t_s"] > 0
     assert r["sort_andrew_gpoints_s"] > 0 and r["reduce_then_hull_gpoints_s"] > 0
+
+
+def test_all_core_reduction_merges_to_one_pass_of_algorithm_1():
+    """Per-thread partial arrays merged by min/max equal Algorithm 1 over all
+    points (the function raises otherwise); shards smaller than a thread
+    count, and empty shards, are covered by the tiny instance."""
+    p = 512
+    inputs = [("uniform", synth.points("uniform", 200_003, p, seed=5)),
+              ("gaussian", synth.points("gaussian", 3, p, seed=6))]
+    r = bench.cpu_reduce_all_cores(p, inputs, passes=1)
+    assert r["threads"] >= 1 and r["reduce_gpoints_s"] > 0
