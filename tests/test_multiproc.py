@@ -52,3 +52,29 @@ def test_sharded_reduce_merges_exactly(tmp_path):
     L = oracle.reduce(P, p)
     np.testing.assert_array_equal(merged, L)
     np.testing.assert_array_equal(oracle.hull_chain(merged), oracle.hull_points(P))
+
+
+def _bench_worker(rank, world, port, out):
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # the slowest rank's time is the job's time
+        t = bench._max_over_ranks(torch, dist, world, 1.5 + rank)
+        # weak scaling: every rank draws its own instances of the same shape
+        p, n, inputs = bench.gen_inputs("plain_small", rank)
+        h = [int(np.frombuffer(P.tobytes(), np.uint8).sum()) for _, P in inputs]
+        np.save(out + f".{rank}.npy", np.array([t, p, n] + h, dtype=np.float64))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_bench_ranks_time_and_inputs(tmp_path):
+    out = str(tmp_path / "r")
+    mp.start_processes(_bench_worker, args=(2, _free_port(), out), nprocs=2, join=True,
+                       start_method="spawn")
+    r0, r1 = np.load(out + ".0.npy"), np.load(out + ".1.npy")
+    assert r0[0] == r1[0] == 2.5
+    assert tuple(r0[1:3]) == tuple(r1[1:3])
+    assert not np.array_equal(r0[3:], r1[3:])
