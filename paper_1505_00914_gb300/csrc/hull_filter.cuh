@@ -24,12 +24,14 @@ constexpr int RUN_LOG = 10;
 __device__ __forceinline__ int tree_off(int k) { return 2 * RUN - ((2 * RUN) >> (k - 1)); }
 
 // Builds the min-y index trees of two runs, P0[0..n0) and P1[0..n1), level by
-// level; every thread of the CTA calls it.
+// level; every thread of the CTA calls it.  Levels 5 and up have at most 32
+// nodes and read only nodes that warp 0 wrote, so warp 0 builds them alone
+// with warp barriers between levels.
 __device__ __forceinline__ void build_min_trees(const int2 *P0, short *M0, int n0, const int2 *P1,
                                                 short *M1, int n1)
 {
     const int i = threadIdx.x;
-    for (int k = 1; k <= RUN_LOG; ++k) {
+    auto level = [&](int k) {
         if (i < (RUN >> k)) {
             int a0, b0, a1, b1;
             if (k == 1) {
@@ -48,8 +50,20 @@ __device__ __forceinline__ void build_min_trees(const int2 *P0, short *M0, int n
             M0[tree_off(k) + i] = (short)(va0 ? ((vb0 && yb0 < ya0) ? b0 : a0) : (vb0 ? b0 : -1));
             M1[tree_off(k) + i] = (short)(va1 ? ((vb1 && yb1 < ya1) ? b1 : a1) : (vb1 ? b1 : -1));
         }
+    };
+    constexpr int WARP_LEVEL = 5;  // RUN >> 5 = 32 nodes
+    static_assert((RUN >> WARP_LEVEL) == 32, "levels from WARP_LEVEL on fit one warp");
+    for (int k = 1; k < WARP_LEVEL; ++k) {
+        level(k);
         __syncthreads();
     }
+    if (i < 32) {
+        for (int k = WARP_LEVEL; k <= RUN_LOG; ++k) {
+            level(k);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
 }
 
 // True when point i of P[0..n) may be a strict lower-hull vertex.  The anchor
@@ -125,6 +139,41 @@ __device__ __forceinline__ int compact_run(const int2 *P, bool keep, int2 *out, 
     if (keep)
         out[s_wc[w] + __popc(bal & ((1u << lane) - 1u))] = P[threadIdx.x];
     return s_wc[RUN / 32];
+}
+
+// compact_run for two runs at once: one scan over both counts (packed in
+// 16-bit halves; each is at most RUN).  Returns (kept of P0, kept of P1).
+__device__ __forceinline__ int2 compact_runs(const int2 *P0, bool keep0, int2 *out0, const int2 *P1,
+                                             bool keep1, int2 *out1, int *s_wc)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned b0 = __ballot_sync(0xFFFFFFFFu, keep0), b1 = __ballot_sync(0xFFFFFFFFu, keep1);
+    __syncthreads();  // s_wc may still be read by a previous call
+    if (lane == 0)
+        s_wc[w] = __popc(b0) | (__popc(b1) << 16);
+    __syncthreads();
+    if (w == 0) {
+        const int v = s_wc[lane];
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o)
+                incl += x;
+        }
+        s_wc[lane] = incl - v;
+        if (lane == 31)
+            s_wc[RUN / 32] = incl;
+    }
+    __syncthreads();
+    const int base = s_wc[w];
+    const unsigned below = (1u << lane) - 1u;
+    if (keep0)
+        out0[(base & 0xFFFF) + __popc(b0 & below)] = P0[threadIdx.x];
+    if (keep1)
+        out1[(base >> 16) + __popc(b1 & below)] = P1[threadIdx.x];
+    const int tot = s_wc[RUN / 32];
+    return make_int2(tot & 0xFFFF, tot >> 16);
 }
 
 }  // namespace ch
