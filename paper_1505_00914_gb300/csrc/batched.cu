@@ -118,7 +118,12 @@ __device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 
     int2 *glo = scr, *gup = scr + BATCH_MAX_P;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int T0 = 0, T1 = 0;
+    int *const s_warp2 = s_warp;
     for (int t0 = 0; t0 < p; t0 += RUN) {
+        // consecutive tiles alternate between two scan buffers, so a tile
+        // needs no closing barrier: every other shared value it reads is
+        // rewritten only after the next tile's first two barriers
+        s_warp = s_warp2 + ((t0 / RUN) & 1) * (RUN / 32 + 1);
         const int c = t0 + threadIdx.x;
         const bool valid = c < p && slo[c] <= shi[c];
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, valid);
@@ -148,7 +153,6 @@ __device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 
             }
             T0 += cnt;
             T1 += cnt;
-            __syncthreads();  // s_warp and s_cnt are rewritten by the next tile
             continue;
         }
         if (valid) {
@@ -163,8 +167,9 @@ __device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 
         const int2 nk = compact_runs(P0, k0, glo + T0, P1, k1, gup + T1, s_warp);
         T0 += nk.x;
         T1 += nk.y;
-        __syncthreads();
     }
+    __syncthreads();  // the last tile's survivor lists are copied below by other threads
+    s_warp = s_warp2;
     const int T = T0 + T1;
     const bool in_smem = T <= BPCAP;
     int2 *D = in_smem ? A : scr + 2 * BATCH_MAX_P;  // compact: lower then upper
@@ -195,7 +200,7 @@ __global__ void __launch_bounds__(BT, 1)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item, s_ticket, s_total, s_cnt;
-    __shared__ int s_warp[33];
+    __shared__ int s_warp[2 * (RUN / 32 + 1)];
     int *slo = reinterpret_cast<int *>(smem);
     int2 *scr = reinterpret_cast<int2 *>(scratch + (size_t)blockIdx.x * SCR_BYTES);
     bool bad = false;

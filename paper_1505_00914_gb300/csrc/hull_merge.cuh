@@ -234,9 +234,48 @@ __device__ __forceinline__ bool peel_drops(const int2 *D, int cs, int ce, int i)
 __device__ void peel_merge_stitch(int2 *A, int2 *B, int *F, int *ix, int T0, int T, int2 *hull,
                                   int *hull_count, int *s_warp, int *s_total)
 {
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     bool done = false;
     for (int round = 0; round < PEEL_MAX && !done; ++round) {
+        if (T <= FT) {  // one point per thread: a ballot scan, three block barriers
+            const bool c1 = t >= T0;
+            const bool keep = t < T && !peel_drops(A, c1 ? T0 : 0, c1 ? T : T0, t);
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+            if (lane == 0)
+                s_warp[w] = __popc(bal);
+            __syncthreads();
+            if (w == 0) {
+                const int v = s_warp[lane];
+                int incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o)
+                        incl += x;
+                }
+                s_warp[lane] = incl - v;
+                if (lane == 31)
+                    *s_total = incl;
+            }
+            __syncthreads();
+            const int kept = *s_total;
+            if (kept == T) {
+                done = true;  // block-uniform
+                break;
+            }
+            const int pos = s_warp[w] + __popc(bal & ((1u << lane) - 1u));
+            if (keep)
+                B[pos] = A[t];
+            if (t == T0 && T0 < T)
+                F[0] = pos;  // points kept before the upper chain
+            __syncthreads();
+            T0 = T0 < T ? F[0] : kept;
+            T = kept;
+            int2 *x = A;
+            A = B;
+            B = x;
+            continue;
+        }
         for (int i = t; i < T; i += FT) {
             const bool c1 = i >= T0;
             F[i] = peel_drops(A, c1 ? T0 : 0, c1 ? T : T0, i) ? 0 : 1;
