@@ -19,7 +19,7 @@ import torch
 
 from . import ch
 
-CANDIDATES = (8, 16, 32, 64, 128, 256, 1024)
+CANDIDATES = (8, 16, 32, 64, 128, 256, 1024, 4096)
 
 
 def _cache_path() -> str:

@@ -164,7 +164,7 @@ __device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 
         build_min_trees(P0, M0, cnt, P1, M1, cnt);
         const bool k0 = run_keeps<true>(P0, M0, cnt, threadIdx.x);
         const bool k1 = run_keeps<true>(P1, M1, cnt, threadIdx.x);
-        const int2 nk = compact_runs(P0, k0, glo + T0, P1, k1, gup + T1, s_warp);
+        const int2 nk = compact_runs<false>(P0, k0, glo + T0, P1, k1, gup + T1, s_warp);
         T0 += nk.x;
         T1 += nk.y;
     }

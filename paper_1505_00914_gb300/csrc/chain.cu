@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(TILE)
             const bool k0 = run_keeps(fs.P[0], fs.M[0], cnt0, threadIdx.x);
             const bool k1 = run_keeps(fs.P[1], fs.M[1], cnt1, threadIdx.x);
             __shared__ int s_cw[WPB + 1];
-            const int2 nk = compact_runs(fs.P[0], k0, cand + (size_t)tile * TILE, fs.P[1], k1,
+            const int2 nk = compact_runs<false>(fs.P[0], k0, cand + (size_t)tile * TILE, fs.P[1], k1,
                                          cand + ((size_t)ntiles + tile) * TILE, s_cw);
             if (threadIdx.x == 0) {
                 ccnt[tile] = nk.x;

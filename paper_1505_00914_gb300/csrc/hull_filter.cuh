@@ -143,12 +143,16 @@ __device__ __forceinline__ int compact_run(const int2 *P, bool keep, int2 *out, 
 
 // compact_run for two runs at once: one scan over both counts (packed in
 // 16-bit halves; each is at most RUN).  Returns (kept of P0, kept of P1).
+// LEAD = false when no thread can still be reading s_wc (a block barrier
+// since its last read).
+template <bool LEAD = true>
 __device__ __forceinline__ int2 compact_runs(const int2 *P0, bool keep0, int2 *out0, const int2 *P1,
                                              bool keep1, int2 *out1, int *s_wc)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned b0 = __ballot_sync(0xFFFFFFFFu, keep0), b1 = __ballot_sync(0xFFFFFFFFu, keep1);
-    __syncthreads();  // s_wc may still be read by a previous call
+    if (LEAD)
+        __syncthreads();  // s_wc may still be read by a previous call
     if (lane == 0)
         s_wc[w] = __popc(b0) | (__popc(b1) << 16);
     __syncthreads();

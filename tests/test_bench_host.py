@@ -58,3 +58,26 @@ def test_all_core_reduction_merges_to_one_pass_of_algorithm_1():
               ("gaussian", synth.points("gaussian", 3, p, seed=6))]
     r = bench.cpu_reduce_all_cores(p, inputs, passes=1)
     assert r["threads"] >= 1 and r["reduce_gpoints_s"] > 0
+
+
+def test_bench_reads_no_undefined_global():
+    """Every global name a function of bench.py reads is defined at module
+    level or is a builtin (a stray name fails only when its workload runs)."""
+    import builtins
+    import os
+    import symtable
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py")
+    top = symtable.symtable(open(path).read(), path, "exec")
+    defined = {s.get_name() for s in top.get_symbols() if s.is_assigned() or s.is_imported()
+               or s.is_namespace()} | set(dir(builtins)) | {"__file__", "__name__"}
+    missing = []
+
+    def walk(t):
+        for s in t.get_symbols():
+            if s.is_referenced() and s.is_global() and s.get_name() not in defined:
+                missing.append((t.get_name(), s.get_name()))
+        for c in t.get_children():
+            walk(c)
+
+    walk(top)
+    assert not missing, missing
