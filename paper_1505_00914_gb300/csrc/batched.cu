@@ -103,7 +103,7 @@ __device__ void fold_range(const int32_t *__restrict__ base, int64_t n, int p, i
     }
 }
 
-constexpr int SPARSE_TILE = 64;  // tiles with at most this many columns skip the pre-filter
+constexpr int SPARSE_TILE = 512;  // tiles with at most this many columns skip the pre-filter
 
 // Hull of the set whose L is in slo/shi (p columns); whole CTA.
 __device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 *scr,
