@@ -1127,7 +1127,7 @@ int ch_convex_hull_rxy(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int
     if (e == cudaSuccess)
         e = hull_final_launch(hl, hw, hull_t, count_t, s);
     if (e == cudaSuccess)
-        e = unframe_launch(hull_t, count_t, Frame{1, 1, p, p, 1}, hull, hull_count, s);
+        e = unframe_launch(hull_t, count_t, Frame{1, 1, p, p, 1, 0}, hull, hull_count, s);
     return cuda_rc(e);
 }
 

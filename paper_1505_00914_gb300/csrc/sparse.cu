@@ -35,7 +35,6 @@
 namespace ch {
 namespace {
 
-constexpr int SP_T = 1024;        // list entries per tile
 constexpr int SP_RED_T = 512;     // threads per reduction block
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
@@ -92,8 +91,8 @@ __global__ void __launch_bounds__(SP_RED_T)
         atomicOr(status, ST_RANGE);
 }
 
-// Block-wide exclusive scan of v over the SP_T threads of a CTA; returns the block total
-// in *tot (all threads).
+// Block-wide exclusive scan of v over the 1024 threads (32 warps) of a CTA; returns the
+// block total in *tot (all threads).
 __device__ __forceinline__ int block_excl_scan(int v, int *s_w, int *tot)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
