@@ -8,9 +8,10 @@
 // chunk is finished by that CTA at once; a set of several chunks has each
 // chunk write its L as a packed partial row, and the CTA that completes the
 // last chunk (per-set atomic ticket) merges the rows and finishes the set.
-// Finishing scans L in 1024-column tiles: the valid columns of each tile go
-// through the exact hull pre-filter (hull_filter.cuh) and its survivors are
-// appended to per-chain lists; the lists are then peeled, merged and
+// Finishing scans L in 1024-column tiles: the valid columns of a tile with
+// more than SPARSE_TILE of them go through the exact hull pre-filter
+// (hull_filter.cuh), those of the other tiles are kept as they are, and both
+// are appended to per-chain lists; the lists are then peeled, merged and
 // stitched (hull_merge.cuh) straight into the set's slice of the ragged
 // output.  L never leaves shared memory for one-chunk sets.
 #include <algorithm>
@@ -103,7 +104,9 @@ __device__ void fold_range(const int32_t *__restrict__ base, int64_t n, int p, i
     }
 }
 
-constexpr int SPARSE_TILE = 512;  // tiles with at most this many columns skip the pre-filter
+// Tiles with at most this many valid columns skip the pre-filter: below it
+// the peeling rounds remove their non-vertices for less than the trees cost.
+constexpr int SPARSE_TILE = 512;
 
 // Hull of the set whose L is in slo/shi (p columns); whole CTA.
 __device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 *scr,
