@@ -307,6 +307,27 @@ int ch_hull_batched(const int32_t *pts, const int64_t *offsets, const int32_t *p
                     int32_t *hull_out, const int64_t *hull_offsets, int32_t *hull_counts,
                     void *workspace, size_t ws_bytes, ch_stream_t stream);
 
+/* Algorithm 1 (Section 2.1) for each set of the prepared plan in the same
+ * persistent launch as ch_hull_batched, stopping after the reduction: set s
+ * writes its L, int32[ps[s]][2] (L[x-1] = (min y, max y), (ps[s]+1, -1) for a
+ * column with no point), to L_out[L_offsets[s] ...] (device int64[B+1]
+ * offsets counted in pairs; capacity at least ps[s] pairs per set).  Points
+ * outside [1, ps[s]]^2 are skipped and recorded as CH_ERR_RANGE.  Returns
+ * CH_ERR_ARG if no plan for B sets was prepared in `workspace`. */
+int ch_reduce_batched(const int32_t *pts, const int64_t *offsets, const int32_t *ps, int32_t B,
+                      int32_t *L_out, const int64_t *L_offsets, void *workspace, size_t ws_bytes,
+                      ch_stream_t stream);
+
+/* Chains of every set (Lemma 1; ch_chain for B sets in one launch).  L and
+ * L_offsets as written by ch_reduce_batched; ps: device int32[B] (any side
+ * >= 1).  A column is valid when its entry differs from (ps[s]+1, -1).  Set s
+ * writes, in increasing x, lower[L_offsets[s] + k] = (x, ly) and
+ * upper[L_offsets[s] + k] = (x, hy) for its k-th valid column, and
+ * counts[2s] = counts[2s+1] = its number of valid columns (device
+ * int32[B][2]).  No workspace. */
+int ch_chain_batched(const int32_t *L, const int64_t *L_offsets, const int32_t *ps, int32_t B,
+                     int32_t *lower, int32_t *upper, int32_t *counts, ch_stream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* Integer points anywhere in int32: Steps 1 and 2 of the paper's general   */
 /* procedure (Section 2, "Implementation of the proposed heuristic": find   */

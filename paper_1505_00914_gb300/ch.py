@@ -49,6 +49,8 @@ def _declare(lib):
         "ch_batched_workspace_size": (ctypes.c_int, [i32, P, P, i32, szp]),
         "ch_batched_prepare": (ctypes.c_int, [i32, P, P, i32, P, sz, P]),
         "ch_hull_batched": (ctypes.c_int, [P, P, P, i32, P, P, P, P, sz, P]),
+        "ch_reduce_batched": (ctypes.c_int, [P, P, P, i32, P, P, P, sz, P]),
+        "ch_chain_batched": (ctypes.c_int, [P, P, P, i32, P, P, P, P]),
         "ch_reduce_workspace_size": (ctypes.c_int, [i64, i32, szp]),
         "ch_reduce": (ctypes.c_int, [P, i64, i32, P, P, sz, P]),
         "ch_chain_workspace_size": (ctypes.c_int, [i32, szp]),
@@ -514,6 +516,36 @@ def ch_hull_batched(pts, offsets, ps, hull_out, hull_offsets, hull_counts, works
                                  _ptr(hull_offsets), _ptr(hull_counts), _ptr(workspace),
                                  workspace.numel(), _stream(stream)), "ch_hull_batched")
     return hull_out, hull_counts
+
+
+def ch_reduce_batched(pts, offsets, ps, L_out, L_offsets, workspace, stream=None):
+    """Algorithm 1 for all sets of the prepared batch: set s writes its L
+    (ps[s] int32 pairs) at L_out[L_offsets[s]] (device tensors)."""
+    pts = _pts(pts)
+    B = int(ps.shape[0])
+    _check(lib().ch_reduce_batched(_ptr(pts), _ptr(offsets), _ptr(ps), B, _ptr(L_out),
+                                   _ptr(L_offsets), _ptr(workspace), workspace.numel(),
+                                   _stream(stream)), "ch_reduce_batched")
+    return L_out
+
+
+def ch_chain_batched(L, L_offsets, ps, lower, upper, counts, stream=None):
+    """Lemma 1 chains of all sets from their L (layout of ch_reduce_batched);
+    counts: int32 (B, 2)."""
+    B = int(ps.shape[0])
+    _check(lib().ch_chain_batched(_ptr(L), _ptr(L_offsets), _ptr(ps), B, _ptr(lower), _ptr(upper),
+                                  _ptr(counts), _stream(stream)), "ch_chain_batched")
+    return lower, upper, counts
+
+
+def L_offsets_of(ps):
+    """int64 (B+1,) offsets giving set s ps[s] pairs (the layout of L and of
+    the chains in the batched reduce and chain calls)."""
+    import numpy as np
+    pp = np.asarray(ps.cpu() if hasattr(ps, "cpu") else ps, dtype=np.int64)
+    out = np.zeros(pp.shape[0] + 1, dtype=np.int64)
+    np.cumsum(pp, out=out[1:])
+    return out
 
 
 def hull_capacity_offsets(offsets, ps):

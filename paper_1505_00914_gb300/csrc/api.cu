@@ -486,8 +486,46 @@ int ch_hull_batched(const int32_t *pts, const int64_t *offsets, const int32_t *p
     unsigned *st = device_status_ptr();
     if (!st)
         return CH_ERR_CUDA;
-    return batch_launch(pts, reinterpret_cast<int2 *>(hull_out), hull_offsets, hull_counts,
+    return batch_launch(pts, reinterpret_cast<int2 *>(hull_out), hull_offsets, hull_counts, nullptr,
+                        nullptr, workspace, ws_bytes, info, st, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int ch_reduce_batched(const int32_t *pts, const int64_t *offsets, const int32_t *ps, int32_t B,
+                      int32_t *L_out, const int64_t *L_offsets, void *workspace, size_t ws_bytes,
+                      ch_stream_t stream)
+{
+    (void)offsets;
+    (void)ps;
+    if (B < 0 || (B > 0 && (!pts || !L_out || !L_offsets)) || !aligned8(pts) || !aligned8(L_out))
+        return CH_ERR_ARG;
+    if (B == 0)
+        return CH_OK;
+    BatchPlanInfo info;
+    {
+        std::lock_guard<std::mutex> g(g_batch_mu);
+        auto it = g_batch_plans.find(workspace);
+        if (it == g_batch_plans.end() || it->second.B != B)
+            return CH_ERR_ARG;  // no plan prepared in this workspace for B sets
+        info = it->second;
+    }
+    unsigned *st = device_status_ptr();
+    if (!st)
+        return CH_ERR_CUDA;
+    return batch_launch(pts, nullptr, nullptr, nullptr, reinterpret_cast<int2 *>(L_out), L_offsets,
                         workspace, ws_bytes, info, st, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int ch_chain_batched(const int32_t *L, const int64_t *L_offsets, const int32_t *ps, int32_t B,
+                     int32_t *lower, int32_t *upper, int32_t *counts, ch_stream_t stream)
+{
+    if (B < 0 || (B > 0 && (!L || !L_offsets || !ps || !lower || !upper || !counts)) ||
+        !aligned8(L) || !aligned8(lower) || !aligned8(upper))
+        return CH_ERR_ARG;
+    if (B == 0)
+        return CH_OK;
+    return chain_batched_launch(reinterpret_cast<const int2 *>(L), L_offsets, ps, B,
+                                reinterpret_cast<int2 *>(lower), reinterpret_cast<int2 *>(upper),
+                                counts, reinterpret_cast<cudaStream_t>(stream));
 }
 
 // ---------------------------------------------------------------- MLP

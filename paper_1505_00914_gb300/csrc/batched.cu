@@ -195,11 +195,15 @@ __device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 
     peel_merge_stitch(D, B, F, ix, T0, T, hull, hull_count, s_warp, s_total);
 }
 
+// WRITE_L: instead of finishing a set, write its L (Algorithm 1's array,
+// (p+1, -1) for an empty column) to L_out[L_offsets[set] ...].
+template <bool WRITE_L>
 __global__ void __launch_bounds__(BT, 1)
     k_batched(const int32_t *__restrict__ pts, const BItem *__restrict__ items, int nitems,
               const BSet *__restrict__ sets, int *queue, int *set_done, uint32_t *part,
               int2 *hull_out, const int64_t *__restrict__ hull_offsets, int *hull_counts,
-              unsigned char *scratch, unsigned *status)
+              int2 *L_out, const int64_t *__restrict__ L_offsets, unsigned char *scratch,
+              unsigned *status)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item, s_ticket, s_total, s_cnt;
@@ -253,13 +257,75 @@ __global__ void __launch_bounds__(BT, 1)
                 __syncthreads();
             }
         }
-        if (last)
-            finish_set(p, slo, shi, smem, scr, hull_out + hull_offsets[item.set],
-                       hull_counts + item.set, s_warp, &s_total, &s_cnt);
+        if (last) {
+            if constexpr (WRITE_L) {
+                int2 *Lo = L_out + L_offsets[item.set];
+                for (int i = threadIdx.x; i < p; i += BT)
+                    Lo[i] = make_int2(slo[i], shi[i]);
+            } else {
+                finish_set(p, slo, shi, smem, scr, hull_out + hull_offsets[item.set],
+                           hull_counts + item.set, s_warp, &s_total, &s_cnt);
+            }
+        }
         __syncthreads();
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0)
         atomicOr(status, ST_RANGE);
+}
+
+// Chains of every set from its L (as ch_chain does for one set): set s has
+// side ps[s] and L at L[L_offsets[s] ...]; its k-th valid column (an entry
+// other than (p+1, -1)) x gives lower[L_offsets[s] + k] = (x, ly) and
+// upper[L_offsets[s] + k] = (x, hy); counts[2s] = counts[2s+1] = the number of
+// valid columns.  CTAs stride over the sets; a set is scanned in tiles of BT
+// columns (ballot, block scan).  Consecutive tiles, across sets too,
+// alternate between two scan buffers, so no tile needs a closing barrier.
+__global__ void __launch_bounds__(BT)
+    k_chain_batched(const int2 *__restrict__ L, const int64_t *__restrict__ L_offsets,
+                    const int *__restrict__ ps, int B, int2 *lower, int2 *upper, int *counts)
+{
+    __shared__ int s_buf[2][RUN / 32 + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int k = 0;
+    for (int set = blockIdx.x; set < B; set += gridDim.x) {
+        const int p = ps[set];
+        const int64_t base = L_offsets[set];
+        int T = 0;
+        for (int t0 = 0; t0 < p; t0 += BT, ++k) {
+            int *sw = s_buf[k & 1];
+            const int c = t0 + threadIdx.x;
+            const int2 e = c < p ? L[base + c] : make_int2(p + 1, -1);
+            const bool valid = c < p && !(e.x == p + 1 && e.y == -1);
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, valid);
+            if (lane == 0)
+                sw[w] = __popc(bal);
+            __syncthreads();
+            if (w == 0) {
+                const int v = sw[lane];
+                int incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o)
+                        incl += x;
+                }
+                sw[lane] = incl - v;
+                if (lane == 31)
+                    sw[RUN / 32] = incl;
+            }
+            __syncthreads();
+            if (valid) {
+                const int64_t r = base + T + sw[w] + __popc(bal & ((1u << lane) - 1u));
+                lower[r] = make_int2(c + 1, e.x);
+                upper[r] = make_int2(c + 1, e.y);
+            }
+            T += sw[RUN / 32];
+        }
+        if (threadIdx.x == 0) {
+            counts[2 * set] = T;
+            counts[2 * set + 1] = T;
+        }
+    }
 }
 
 struct BatchWs {
@@ -364,8 +430,8 @@ int batch_prepare(int B, const int64_t *off, const int32_t *ps, int chunk_mult, 
 }
 
 int batch_launch(const int32_t *pts, int2 *hull_out, const int64_t *hull_offsets, int *hull_counts,
-                 void *ws, size_t ws_bytes, const BatchPlanInfo &info, unsigned *status,
-                 cudaStream_t s)
+                 int2 *L_out, const int64_t *L_offsets, void *ws, size_t ws_bytes,
+                 const BatchPlanInfo &info, unsigned *status, cudaStream_t s)
 {
     const BatchWs l = batch_layout(info.B, (size_t)info.nitems, (size_t)info.part_words, info.grid);
     if (ws_bytes < l.end)
@@ -374,7 +440,9 @@ int batch_launch(const int32_t *pts, int2 *hull_out, const int64_t *hull_offsets
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr[dev]) {
-        if (cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_batched<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)BATCH_SMEM) != cudaSuccess ||
+            cudaFuncSetAttribute(k_batched<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)BATCH_SMEM) != cudaSuccess)
             return CH_ERR_CUDA;
         attr[dev] = true;
@@ -383,11 +451,23 @@ int batch_launch(const int32_t *pts, int2 *hull_out, const int64_t *hull_offsets
     int *head = reinterpret_cast<int *>(b + l.head);
     if (cudaMemsetAsync(head, 0, (size_t)(info.B + 2) * sizeof(int), s) != cudaSuccess)
         return CH_ERR_CUDA;
-    k_batched<<<info.grid, BT, BATCH_SMEM, s>>>(
+    auto kern = L_out ? k_batched<true> : k_batched<false>;
+    kern<<<info.grid, BT, BATCH_SMEM, s>>>(
         pts, reinterpret_cast<const BItem *>(b + l.items), info.nitems,
         reinterpret_cast<const BSet *>(b + l.sets), head, head + 1,
-        reinterpret_cast<uint32_t *>(b + l.part), hull_out, hull_offsets, hull_counts,
-        reinterpret_cast<unsigned char *>(b + l.scratch), status);
+        reinterpret_cast<uint32_t *>(b + l.part), hull_out, hull_offsets, hull_counts, L_out,
+        L_offsets, reinterpret_cast<unsigned char *>(b + l.scratch), status);
+    return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ERR_CUDA;
+}
+
+int chain_batched_launch(const int2 *L, const int64_t *L_offsets, const int *ps, int B, int2 *lower,
+                         int2 *upper, int *counts, cudaStream_t s)
+{
+    const int sms = sm_count();
+    if (sms <= 0)
+        return CH_ERR_CUDA;
+    const int grid = std::max(1, std::min(B, 2 * sms));
+    k_chain_batched<<<grid, BT, 0, s>>>(L, L_offsets, ps, B, lower, upper, counts);
     return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ERR_CUDA;
 }
 

@@ -186,9 +186,13 @@ int batch_sizes(int B, const int64_t *off, const int32_t *ps, int chunk_mult, si
                 BatchPlanInfo *info);
 int batch_prepare(int B, const int64_t *off, const int32_t *ps, int chunk_mult, void *ws,
                   size_t ws_bytes, cudaStream_t s, BatchPlanInfo *info);
+// L_out == nullptr: hulls into hull_out; otherwise each set's L into
+// L_out[L_offsets[s] ...] and no hull.
 int batch_launch(const int32_t *pts, int2 *hull_out, const int64_t *hull_offsets, int *hull_counts,
-                 void *ws, size_t ws_bytes, const BatchPlanInfo &info, unsigned *status,
-                 cudaStream_t s);
+                 int2 *L_out, const int64_t *L_offsets, void *ws, size_t ws_bytes,
+                 const BatchPlanInfo &info, unsigned *status, cudaStream_t s);
+int chain_batched_launch(const int2 *L, const int64_t *L_offsets, const int *ps, int B, int2 *lower,
+                         int2 *upper, int *counts, cudaStream_t s);
 
 // ---- MLP (mlp.cu) ----
 // C[M x N] = epi(A[M x K] B[K x N] (+ bias)) (+ beta * C); element (r, c) of A
