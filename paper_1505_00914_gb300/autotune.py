@@ -27,12 +27,26 @@ def _cache_path() -> str:
                           os.path.join(os.path.expanduser("~"), ".cache", "chull_gb300", "autotune.json"))
 
 
-def batch_key(offsets, ps) -> str:
-    """Device name + a digest of the batch's shape (n and p per set)."""
+def _kernel_digest() -> str:
+    """Digest of the batched kernel's source, so that a tuning measured on
+    another version of the kernel is not reused."""
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "batched.cu")
+    try:
+        with open(src, "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()[:12]
+    except OSError:
+        return "unknown"
+
+
+def batch_key(offsets, ps, candidates=CANDIDATES) -> str:
+    """Device name + digests of the batch's shape (n and p per set), of the
+    candidate chunk sizes and of the kernel source."""
     off = np.asarray(offsets, np.int64)
     pp = np.asarray(ps, np.int32)
     h = hashlib.sha256(np.diff(off).tobytes() + pp.tobytes()).hexdigest()[:16]
-    return f"{torch.cuda.get_device_name()}|B={pp.shape[0]}|{h}"
+    c = ",".join(str(int(x)) for x in candidates)
+    dev = torch.cuda.get_device_name() if torch.cuda.is_available() else "no-device"
+    return f"{dev}|B={pp.shape[0]}|{h}|C={c}|K={_kernel_digest()}"
 
 
 def _load():
@@ -60,7 +74,7 @@ def tune_batched(d_pts, offsets, ps, d_off, d_ps, hull, d_hoff, counts, candidat
     """Returns (best chunk_mult, {chunk_mult: ms}) for this batch; the host
     arrays offsets/ps describe it, the device tensors are those the caller
     will launch with."""
-    key = batch_key(offsets, ps)
+    key = batch_key(offsets, ps, candidates)
     db = _load() if use_cache else {}
     if key in db:
         return int(db[key]["chunk_mult"]), {int(k): v for k, v in db[key]["ms"].items()}
