@@ -67,3 +67,33 @@ def test_sparse_workspace_holds_the_tree_of_bit_words():
         expect = r(8 * p) + sum(r(4 * k) for k in oracle.tree_words(p, 32))
         assert ch.ch_sparse_workspace_size(1000, p)[1] == expect, p
         assert len(oracle.tree_words(p, 32)) <= 7
+
+
+def test_product_path_never_reaches_the_oracle():
+    """The package and the C ABI neither import, include nor link the CPU
+    oracle (test infrastructure only), and the binding has no CPU fallback:
+    it raises when libch.so cannot be loaded."""
+    import ast
+    pkg = os.path.join(ROOT, "paper_1505_00914_gb300")
+    for path in glob.glob(os.path.join(pkg, "*.py")):
+        tree = ast.parse(open(path).read(), path)
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                assert all(a.name.split(".")[0] != "oracle" for a in node.names), path
+            if isinstance(node, ast.ImportFrom):
+                assert (node.module or "").split(".")[0] != "oracle", path
+    for path in glob.glob(os.path.join(pkg, "csrc", "*")) + glob.glob(os.path.join(ROOT, "include", "*")):
+        text = open(path).read()
+        assert "oracle" not in re.findall(r'#include\s*[<"]([^>"]+)', text).__str__(), path
+        assert "liboracle" not in text, path
+
+
+def test_binding_raises_without_the_library(tmp_path, monkeypatch):
+    """No fallback: a library that cannot be loaded is an error."""
+    from paper_1505_00914_gb300 import ch
+    bad = tmp_path / "libch.so"
+    bad.write_bytes(b"not a shared object")
+    monkeypatch.setattr(ch, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", str(bad))
+    with pytest.raises(RuntimeError, match="could not be loaded"):
+        ch.lib()
