@@ -97,3 +97,18 @@ def test_binding_raises_without_the_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_build, "LIB", str(bad))
     with pytest.raises(RuntimeError, match="could not be loaded"):
         ch.lib()
+
+
+def test_oracle_uses_only_the_generators_of_the_package():
+    """The oracle shares no code with the CUDA path: from the package it may
+    import the seeded input generators (synth) and nothing else."""
+    import ast
+    for path in glob.glob(os.path.join(ROOT, "oracle", "*.py")):
+        tree = ast.parse(open(path).read(), path)
+        for node in ast.walk(tree):
+            if isinstance(node, ast.ImportFrom) and (node.module or "").startswith("paper_1505_00914_gb300"):
+                assert node.module == "paper_1505_00914_gb300" and [a.name for a in node.names] == ["synth"], path
+            if isinstance(node, ast.Import):
+                assert all(not a.name.startswith("paper_1505_00914_gb300") for a in node.names), path
+    text = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+    assert re.findall(r'#include\s*[<"]([^>"]+)', text) and "ch.h" not in text
