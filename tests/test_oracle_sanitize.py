@@ -34,3 +34,25 @@ def test_oracle_is_clean_under_sanitizers(tmp_path):
         r = subprocess.run([str(exe), "20000"], capture_output=True, text=True, env=env, timeout=600)
     assert r.returncode == 0, r.stderr[-3000:]
     assert "oracle sanitize ok" in r.stdout
+
+
+def test_a_planted_overrun_is_reported(tmp_path):
+    """The harness can see a mistake: a copy of the oracle whose bit-array
+    writer stores one word past its buffer fails the run."""
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    text = open(SRC[0]).read()
+    head = "void oracle_mask(const int32_t *L, int32_t p, uint32_t *M)\n{"
+    assert head in text
+    planted = tmp_path / "oracle_planted.c"
+    planted.write_text(text.replace(head, head + "\n    M[(p + 31) / 32] = 0;", 1))
+    exe = tmp_path / "osan_planted"
+    san = subprocess.run([gcc, "-std=gnu11", "-O1", "-g", "-fsanitize=address,undefined",
+                          "-fno-sanitize-recover=all", "-fno-omit-frame-pointer", str(planted), SRC[1],
+                          "-lm", "-o", str(exe)], capture_output=True, text=True)
+    if san.returncode != 0:
+        pytest.skip("no sanitizer runtime for gcc here")
+    r = subprocess.run([str(exe), "50"], capture_output=True, text=True,
+                       env=dict(os.environ, ASAN_OPTIONS="detect_leaks=0"), timeout=300)
+    assert r.returncode != 0 and "heap-buffer-overflow" in r.stderr
