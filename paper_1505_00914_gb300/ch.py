@@ -160,8 +160,9 @@ def _ws(nbytes: int, device, ws):
 
 
 def _pts(pts):
-    if pts.dtype != torch.int32 or pts.dim() != 2 or pts.shape[1] != 2 or not pts.is_contiguous():
-        raise ValueError("points must be a contiguous int32 tensor of shape (n, 2)")
+    if (not pts.is_cuda or pts.dtype != torch.int32 or pts.dim() != 2 or pts.shape[1] != 2
+            or not pts.is_contiguous()):
+        raise ValueError("points must be a contiguous int32 CUDA tensor of shape (n, 2)")
     return pts
 
 
@@ -293,8 +294,8 @@ def pack_u16(pts):
 
 
 def _pts16(pts):
-    if pts.dtype != torch.int32 or pts.dim() != 1 or not pts.is_contiguous():
-        raise ValueError("packed points must be a contiguous int32 tensor of shape (n,)")
+    if not pts.is_cuda or pts.dtype != torch.int32 or pts.dim() != 1 or not pts.is_contiguous():
+        raise ValueError("packed points must be a contiguous int32 CUDA tensor of shape (n,)")
     return pts
 
 

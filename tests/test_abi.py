@@ -112,3 +112,19 @@ def test_oracle_uses_only_the_generators_of_the_package():
                 assert all(not a.name.startswith("paper_1505_00914_gb300") for a in node.names), path
     text = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
     assert re.findall(r'#include\s*[<"]([^>"]+)', text) and "ch.h" not in text
+
+
+def test_binding_rejects_host_point_arrays():
+    """Device entry points refuse CPU tensors before any call into the
+    library (a host pointer must never reach a kernel)."""
+    import torch
+    from paper_1505_00914_gb300 import ch
+    host = torch.ones((4, 2), dtype=torch.int32)
+    for call in (lambda: ch.ch_reduce(host, 4), lambda: ch.ch_convex_hull(host, 4),
+                 lambda: ch.ch_reduce_u16(torch.zeros(4, dtype=torch.int32), 4),
+                 lambda: ch.ch_hull_batched(host, None, torch.ones(1, dtype=torch.int32), None, None,
+                                            None, None),
+                 lambda: ch.ch_reduce_batched(host, None, torch.ones(1, dtype=torch.int32), None,
+                                              None, None)):
+        with pytest.raises(ValueError, match="CUDA tensor"):
+            call()
