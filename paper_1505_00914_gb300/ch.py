@@ -128,8 +128,19 @@ def _check(rc: int, where: str):
 
 
 def _ptr(t):
+    """Device pointer of a CUDA tensor (None -> NULL); a host tensor is an
+    error, so host memory never reaches a kernel through a device argument."""
     if t is None:
         return None
+    if not t.is_cuda:
+        raise ValueError("device arguments must be CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(t):
+    """Pointer of a CPU tensor, for the host arguments of ch_convex_hull_host."""
+    if t.is_cuda:
+        raise ValueError("host arguments must be CPU tensors")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -340,7 +351,7 @@ def ch_convex_hull_host(host_pts, p: int, workspace, stream=None, host_hull=None
     if host_hull is None:
         host_hull = torch.empty((2 * p, 2), dtype=torch.int32)
     cnt = ctypes.c_int32(0)
-    _check(lib().ch_convex_hull_host(_ptr(host_pts), n, int(p), _ptr(host_hull),
+    _check(lib().ch_convex_hull_host(_host_ptr(host_pts), n, int(p), _host_ptr(host_hull),
                                      ctypes.byref(cnt), _ptr(workspace), workspace.numel(),
                                      _stream(stream)), "ch_convex_hull_host")
     return host_hull[: cnt.value]

@@ -128,3 +128,7 @@ def test_binding_rejects_host_point_arrays():
                                               None, None)):
         with pytest.raises(ValueError, match="CUDA tensor"):
             call()
+    # any device argument, not only the points: the pointer helper refuses host memory
+    with pytest.raises(ValueError, match="CUDA tensors"):
+        ch._ptr(torch.zeros(3, dtype=torch.int32))
+    assert ch._ptr(None) is None
