@@ -97,3 +97,18 @@ def test_autotune_cache_key_and_lookup(tmp_path, monkeypatch):
     autotune._store({k: {"chunk_mult": 256, "ms": {"8": 2.0, "256": 1.5}}})
     best, times = autotune.tune_batched(None, off, ps, None, None, None, None, None)
     assert best == 256 and times == {8: 2.0, 256: 1.5}
+
+
+def test_clock_summary_from_nvidia_smi_rows():
+    rows = [
+        "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+        "0, 2070, 2070, 1000.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "garbage line\n",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active\n",
+    ]
+    c = bench.ClockSampler.summarize(rows)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = rows[:1] + ["0, 1500, 2070, 1400.0, 0x48, Active, Not Active, Active, Not Active\n"]
+    assert bench.ClockSampler.summarize(hot)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.ClockSampler.summarize(["garbage\n"]) is None
