@@ -480,7 +480,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    rc = ch.ch_sync_status()
+    rc = _status(ch, None, *streams)
     if rc != ch.CH_OK:
         raise RuntimeError(f"warm-up failed: {ch.strerror(rc)}")
 
@@ -507,7 +507,7 @@ def run_ours(args):
     ms_traced = _timed(torch, dist, world, lambda: step(False), args.steps, stream) - fl
     ch.ch_trace_set([])
     clocks = sampler.stop()
-    rc = ch.ch_sync_status()
+    rc = _status(ch, None, *streams)
     if rc != ch.CH_OK:
         raise RuntimeError(f"timed run failed: {ch.strerror(rc)}")
     red_ms = [a.elapsed_time(b) for a, b in evs]
@@ -646,6 +646,17 @@ def _max_over_ranks(torch, dist, world, v):
     return float(t.item())
 
 
+def _status(ch, *streams):
+    """The first error recorded on any of the given streams (None: torch's
+    current stream); every stream's status word is read and cleared."""
+    rc = ch.CH_OK
+    for st in streams:
+        r = ch.ch_sync_status(st)
+        if rc == ch.CH_OK:
+            rc = r
+    return rc
+
+
 def _timed(torch, dist, world, fn, steps, stream):
     """Device time in ms of `steps` calls of fn, barrier + synchronize on
     both sides, max over ranks."""
@@ -710,7 +721,7 @@ def run_learned(args):
         for _ in range(args.warmup):
             step(arm)
     torch.cuda.synchronize()
-    rc = ch.ch_sync_status()
+    rc = _status(ch, None, *streams)
     if rc != ch.CH_OK:
         raise RuntimeError(f"warm-up failed: {ch.strerror(rc)}")
     # every arm must give the same hull
@@ -722,17 +733,20 @@ def run_learned(args):
         for arm in ("learned", "centres"):
             got = hulls[arm][i][: int(hcs[arm][i].item())].cpu()
             exact &= bool(torch.equal(got, ref))
-    # cull rate: share of the points strictly inside the culling polygon,
-    # i.e. Linit.lo <= y <= Linit.hi in their column
+    # cull rate: share of the points strictly inside the culling polygon
+    # (Linit.lo <= y <= Linit.hi in their column), counted by the library
+    # (the call's ch_cull_stats output; one untimed call per instance and arm)
     cull = {}
     for i, (dname, _) in enumerate(inputs):
         cull[dname] = {}
         for arm in ("learned", "centres"):
-            li = Linit[arm][i].long()
-            d = dev_in[i].long()
-            col = li[d[:, 0] - 1]
-            inside = (d[:, 1] >= col[:, 0]) & (d[:, 1] <= col[:, 1])
-            cull[dname][arm] = float(inside.float().mean().item())
+            stt = ch.cull_stats_tensor()
+            ch.ch_hull_learned(dev_in[i], p, params=params if arm == "learned" else None,
+                               hull=hulls[arm][i], hull_count=hcs[arm][i], stats=stt,
+                               workspace=wss[i], stream=stream)
+            cs = ch.cull_stats(stt)
+            cull[dname][arm] = cs["culled"] / n
+            cull[dname][arm + "_polygon_vertices"] = cs["poly_vertices"]
 
     # the network's gain on held-out stretched and rotated shapes of the
     # training family (seeds the training set never used)
@@ -775,7 +789,7 @@ def run_learned(args):
     ms_traced = _timed(torch, dist, world, lambda: step("learned", False), args.steps, stream)
     ch.ch_trace_set([])
     clocks = sampler.stop()
-    rc = ch.ch_sync_status()
+    rc = _status(ch, None, *streams)
     if rc != ch.CH_OK:
         raise RuntimeError(f"timed run failed: {ch.strerror(rc)}")
     red_avg = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
@@ -878,7 +892,7 @@ def run_batched(args):
     for _ in range(args.warmup):
         graph.replay()
     torch.cuda.synchronize()
-    rc = ch.ch_sync_status()
+    rc = _status(ch, stream, None)
     if rc != ch.CH_OK:
         raise RuntimeError(f"warm-up failed: {ch.strerror(rc)}")
     sampler = ClockSampler(torch.cuda.current_device())
@@ -902,7 +916,17 @@ def run_batched(args):
 
     per_set()  # warm-up
     ms_plain = _timed(torch, dist, world, per_set, 1, cur)
-    rc = ch.ch_sync_status()
+    # the same per-set calls captured in one CUDA graph (no host launch cost)
+    gstream = torch.cuda.Stream()
+    gstream.wait_stream(cur)
+    per_graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(per_graph, stream=gstream):
+        for s in range(B):
+            ch.ch_convex_hull(views[s], int(ps[s]), hull=h1[s], hull_count=c1[s], workspace=ws1,
+                              stream=gstream)
+    per_graph.replay()  # warm-up
+    ms_plain_graph = _timed(torch, dist, world, per_graph.replay, 1, cur)
+    rc = _status(ch, stream, cur, gstream)
     if rc != ch.CH_OK:
         raise RuntimeError(f"timed run failed: {ch.strerror(rc)}")
     # identical hulls, set by set
@@ -953,6 +977,9 @@ def run_batched(args):
                     "launch": "one captured CUDA graph replay per step",
                     "per_set_plain_gpoints_s": world * n_tot / (ms_plain / 1e3) / 1e9,
                     "per_set_plain_ms": ms_plain, "speedup_vs_per_set": ms_plain / (ms / args.steps),
+                    "per_set_plain_graph_ms": ms_plain_graph,
+                    "per_set_plain_graph_gpoints_s": world * n_tot / (ms_plain_graph / 1e3) / 1e9,
+                    "speedup_vs_per_set_graph": ms_plain_graph / (ms / args.steps),
                     "hulls_identical": exact, "autotune_ms": tune_ms},
         "roofline": {"bound": "hbm", "kernel": "k_batched", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -1020,7 +1047,7 @@ def run_box(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    rc = ch.ch_sync_status()
+    rc = _status(ch, None, *streams)
     if rc != ch.CH_OK:
         raise RuntimeError(f"warm-up failed: {ch.strerror(rc)}")
     for i in range(len(inputs)):
@@ -1042,7 +1069,7 @@ def run_box(args):
     ms_traced = _timed(torch, dist, world, lambda: step(False), args.steps, stream)
     ch.ch_trace_set([])
     clocks = sampler.stop()
-    rc = ch.ch_sync_status()
+    rc = _status(ch, None, *streams)
     if rc != ch.CH_OK:
         raise RuntimeError(f"timed run failed: {ch.strerror(rc)}")
     # launches follow the instances in order: the reduction of instance i
@@ -1180,7 +1207,7 @@ def run_alt(args):
         for _ in range(args.warmup):
             step(arm)
     torch.cuda.synchronize()
-    rc = ch.ch_sync_status()
+    rc = _status(ch, None)
     if rc != ch.CH_OK:
         raise RuntimeError(f"warm-up failed: {ch.strerror(rc)}")
     same = bool(torch.equal(ha[: int(hca.item())].cpu(), hp[: int(hcp.item())].cpu()))
@@ -1221,7 +1248,7 @@ def run_alt(args):
     ms_traced = _timed(torch, dist, world, lambda: step(alt), args.steps, stream) - fl
     ch.ch_trace_set([])
     clocks = sampler.stop()
-    rc = ch.ch_sync_status()
+    rc = _status(ch, None)
     if rc != ch.CH_OK:
         raise RuntimeError(f"timed run failed: {ch.strerror(rc)}")
     red_avg = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
@@ -1330,7 +1357,7 @@ def run_sparse(args):
         for _ in range(args.warmup):
             step(arm)
     torch.cuda.synchronize()
-    rc = ch.ch_sync_status()
+    rc = _status(ch, None, *streams)
     if rc != ch.CH_OK:
         raise RuntimeError(f"warm-up failed: {ch.strerror(rc)}")
     same = all(torch.equal(out["sparse"][i][0][: int(out["sparse"][i][1].item())].cpu(),
@@ -1377,7 +1404,7 @@ def run_sparse(args):
         sweep.append(row)
         del wsd, wpd, Q
     clocks = sampler.stop()
-    rc = ch.ch_sync_status()
+    rc = _status(ch, None, *streams)
     if rc != ch.CH_OK:
         raise RuntimeError(f"timed run failed: {ch.strerror(rc)}")
     red_avg = sum(a.elapsed_time(b) for a, b in evs) / len(evs)

@@ -31,9 +31,12 @@
  *     default stream).  The return value reports argument and launch errors
  *     only.  Errors that depend on the data (a point outside [1,p]^2, a
  *     capacity overflow, a bounded wait that ran out) are recorded in a sticky
- *     per-device status word; ch_sync_status() waits for the stream and
- *     returns (and clears) it.  After such an error the outputs of that call
- *     are unspecified but every kernel has returned: no call ever hangs.
+ *     status word of the stream the call was made on (a call captured in a
+ *     CUDA graph records into the word of the stream it was captured on);
+ *     ch_sync_status(stream) waits for that stream and returns (and clears)
+ *     its word, so an error is reported only to the stream whose call made
+ *     it.  After such an error the outputs of that call are unspecified but
+ *     every kernel has returned: no call ever hangs.
  *   - p must satisfy 1 <= p <= 2^30 (so int64 cross products of coordinate
  *     differences cannot overflow); n >= 0.
  */
@@ -67,12 +70,18 @@ const char *ch_strerror(int code);
 /* ABI version, (major << 16) | minor. */
 int ch_version(void);
 
-/* Wait for `stream`, then read and clear the calling device's status word.
- * Returns CH_OK or the first recorded error (RANGE, CAPACITY, TIMEOUT), or
- * CH_ERR_CUDA if the stream itself failed. */
+/* Read and clear the status word of `stream` on the current device, then
+ * wait for the stream.  The word is taken by an atomic exchange with zero that
+ * runs on `stream` after the work queued there before, and is copied back on
+ * the same stream, so calls on other streams neither wait nor lose their own
+ * errors.  Returns CH_OK or a recorded error (RANGE before CAPACITY before
+ * TIMEOUT when several bits are set), or CH_ERR_CUDA if the stream itself
+ * failed.  A device keeps a word of its own for each of the first 1024
+ * distinct stream handles used on it; later handles share one further word.
+ * Two host threads reading the same stream's word at once race. */
 int ch_sync_status(ch_stream_t stream);
 
-/* Clear the calling device's status word (stream-ordered). */
+/* Clear the status word of `stream` (stream-ordered, does not wait). */
 int ch_clear_status(ch_stream_t stream);
 
 /* Profiling aid (not part of the method).  events: npairs pairs of
@@ -450,9 +459,21 @@ int ch_cull_propose(const int32_t *pts, int64_t n, int32_t p, const float *param
                     int32_t *poly_count, int64_t *extremes, int32_t *chosen, void *workspace,
                     size_t ws_bytes, ch_stream_t stream);
 
+/* Quality of one culling step, written by the kernels of ch_hull_learned
+ * (device memory, 16 bytes). */
+typedef struct ch_cull_stats {
+    int64_t culled;         /* input points strictly inside the culling polygon, i.e.
+                               Linit.lo <= y <= Linit.hi in their column (points
+                               outside [1,p]^2 are not counted); cull rate = culled / n */
+    int32_t poly_vertices;  /* strict vertices of the polygon used (0 .. 16) */
+    int32_t chosen;         /* 1: the network's polygon, 0: the sector centres',
+                               -1: no network (params NULL) */
+} ch_cull_stats;
+
 int ch_hull_learned_workspace_size(int64_t n, int32_t p, size_t *bytes);
 
-/* Kernels one ch_hull_learned call launches (with_net != 0: params given). */
+/* Kernels one ch_hull_learned call launches (with_net != 0: params given)
+ * when stats is NULL; a non-NULL stats adds one counting kernel. */
 int ch_hull_learned_kernel_count(int64_t n, int32_t p, int32_t with_net, int32_t *kernels);
 
 /* The whole path with culling: the proposal above, Algorithm 1 started from
@@ -460,10 +481,13 @@ int ch_hull_learned_kernel_count(int64_t n, int32_t p, int32_t with_net, int32_t
  * columns where L moved past Linit (lower: L.lo < Linit.lo, upper: L.hi >
  * Linit.hi; counts[0], counts[1] may differ), and the strict hull, which is
  * the same as ch_convex_hull's for every params (NULL included).  Arguments
- * as in ch_convex_hull; L, Linit, lower, upper, counts may be NULL. */
+ * as in ch_convex_hull; L, Linit, lower, upper, counts may be NULL.
+ * stats: NULL, or a device ch_cull_stats filled in by this call (the count
+ * of culled points costs one more pass over the points, after the hull). */
 int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *params, int32_t *L,
                     int32_t *Linit, int32_t *lower, int32_t *upper, int32_t *counts, int32_t *hull,
-                    int32_t *hull_count, void *workspace, size_t ws_bytes, ch_stream_t stream);
+                    int32_t *hull_count, ch_cull_stats *stats, void *workspace, size_t ws_bytes,
+                    ch_stream_t stream);
 
 #ifdef __cplusplus
 }

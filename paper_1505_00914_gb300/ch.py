@@ -76,7 +76,7 @@ def _declare(lib):
         "ch_cull_propose": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P, P, P, P, sz, P]),
         "ch_hull_learned_workspace_size": (ctypes.c_int, [i64, i32, szp]),
         "ch_hull_learned_kernel_count": (ctypes.c_int, [i64, i32, i32, ctypes.POINTER(i32)]),
-        "ch_hull_learned": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P, P, P, sz, P]),
+        "ch_hull_learned": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P, P, P, P, sz, P]),
         "ch_polyline_workspace_size": (ctypes.c_int, [i32, szp]),
         "ch_polyline": (ctypes.c_int, [P, i32, P, P, P, sz, P]),
         "ch_hull_melkman_workspace_size": (ctypes.c_int, [i32, szp]),
@@ -178,6 +178,8 @@ def _pts(pts):
 
 
 def ch_sync_status(stream=None) -> int:
+    """Status of the calls made on `stream` (default: torch's current stream)
+    since its last read; waits for that stream and clears its word."""
     return int(lib().ch_sync_status(_stream(stream)))
 
 
@@ -223,6 +225,23 @@ def ch_chain_workspace_size(p: int) -> int:
     return _size(lib().ch_chain_workspace_size, int(p))
 
 
+def _check_chain_args(L, p, lower, upper, counts, mask):
+    """The chain step's arrays: contiguous int32 CUDA tensors, L with at least
+    p rows of 2, lower and upper with room for p rows of 2, counts for 2
+    values and mask (when given) for ceil(p / 32) words; ValueError else."""
+    need = (("L", L, 2 * p), ("lower", lower, 2 * p), ("upper", upper, 2 * p),
+            ("counts", counts, 2), ("mask", mask, (p + 31) // 32))
+    for name, t, k in need:
+        if t is None:
+            if name != "mask":
+                raise ValueError(f"{name} is required")
+            continue
+        if not t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous int32 CUDA tensor")
+        if t.numel() < k:
+            raise ValueError(f"{name} holds {t.numel()} int32 values, {k} needed for p = {p}")
+
+
 def ch_chain(L, p: int | None = None, lower=None, upper=None, counts=None, mask=None,
              workspace=None, stream=None, with_mask: bool = False):
     """Lemma 1 chains of L: returns (lower, upper, counts[, mask]); lower and
@@ -237,6 +256,8 @@ def ch_chain(L, p: int | None = None, lower=None, upper=None, counts=None, mask=
         counts = torch.empty(2, dtype=torch.int32, device=dev)
     if with_mask and mask is None:
         mask = torch.empty(((p + 31) // 32,), dtype=torch.int32, device=dev)
+    if p >= 1:
+        _check_chain_args(L, p, lower, upper, counts, mask)
     ws = _ws(ch_chain_workspace_size(p), dev, workspace)
     _check(lib().ch_chain(_ptr(L), p, _ptr(lower), _ptr(upper), _ptr(counts), _ptr(mask),
                           _ptr(ws), ws.numel(), _stream(stream)), "ch_chain")
@@ -245,12 +266,16 @@ def ch_chain(L, p: int | None = None, lower=None, upper=None, counts=None, mask=
     return lower, upper, counts
 
 
-CH_CHAIN_NOALLOC_MAX_P = 1 << 24
+CH_CHAIN_NOALLOC_MAX_P = 1 << 24  # the header's #define of the same name
 
 
 def ch_chain_noalloc(L, p: int, lower, upper, counts, mask=None, stream=None):
     """ch_chain with the library's own fixed scratch (no workspace, no
-    allocation in the call); outputs are the caller's tensors."""
+    allocation in the call); outputs are the caller's tensors.  p above
+    CH_CHAIN_NOALLOC_MAX_P is refused by the library (CH_ERR_CAPACITY)
+    before any array is touched."""
+    if 1 <= int(p) <= CH_CHAIN_NOALLOC_MAX_P:
+        _check_chain_args(L, int(p), lower, upper, counts, mask)
     _check(lib().ch_chain_noalloc(_ptr(L), int(p), _ptr(lower), _ptr(upper), _ptr(counts),
                                   _ptr(mask), _stream(stream)), "ch_chain_noalloc")
 
@@ -672,14 +697,32 @@ def ch_hull_learned_kernel_count(n: int, p: int, with_net: bool) -> int:
     return int(k.value)
 
 
+def cull_stats_tensor(device="cuda"):
+    """Device buffer for ch_hull_learned's ch_cull_stats (16 bytes as int64 (2,))."""
+    return torch.zeros(2, dtype=torch.int64, device=device)
+
+
+def cull_stats(t) -> dict:
+    """The fields of a ch_cull_stats buffer: culled (points strictly inside the
+    culling polygon), poly_vertices and chosen (1 network, 0 sector centres,
+    -1 no network)."""
+    w = t.cpu().view(torch.int32)
+    return {"culled": int(t[0].item()), "poly_vertices": int(w[2]), "chosen": int(w[3])}
+
+
 def ch_hull_learned(pts, p: int, params=None, L=None, Linit=None, lower=None, upper=None,
-                    counts=None, hull=None, hull_count=None, workspace=None, stream=None):
-    """The whole path with the culling proposal; returns (hull, hull_count)."""
+                    counts=None, hull=None, hull_count=None, stats=None, workspace=None,
+                    stream=None):
+    """The whole path with the culling proposal; returns (hull, hull_count).
+    stats: None, or a cull_stats_tensor() the call fills in."""
     pts = _pts(pts)
     dev = _dev(pts)
     n = pts.shape[0]
     if params is not None:
         _f32(params, (CH_MLP_PARAMS,), "params")
+    if stats is not None and (stats.dtype != torch.int64 or stats.numel() != 2
+                              or not stats.is_contiguous()):
+        raise ValueError("stats must be a contiguous int64 CUDA tensor of 2 elements")
     if hull is None:
         hull = torch.empty((2 * p, 2), dtype=torch.int32, device=dev)
     if hull_count is None:
@@ -687,7 +730,8 @@ def ch_hull_learned(pts, p: int, params=None, L=None, Linit=None, lower=None, up
     ws = _ws(ch_hull_learned_workspace_size(n, p), dev, workspace)
     _check(lib().ch_hull_learned(_ptr(pts), n, int(p), _ptr(params), _ptr(L), _ptr(Linit),
                                  _ptr(lower), _ptr(upper), _ptr(counts), _ptr(hull),
-                                 _ptr(hull_count), _ptr(ws), ws.numel(), _stream(stream)),
+                                 _ptr(hull_count), _ptr(stats), _ptr(ws), ws.numel(),
+                                 _stream(stream)),
            "ch_hull_learned")
     return hull, hull_count
 

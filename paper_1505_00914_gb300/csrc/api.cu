@@ -1,5 +1,5 @@
 // C ABI of libch.so (declared in include/ch.h): argument checks, workspace
-// layouts, the per-device status word and launch sequencing.  No entry point
+// layouts, the per-stream status words and launch sequencing.  No entry point
 // allocates device memory; every launch goes to the caller's stream.
 #include <cmath>
 #include <map>
@@ -7,15 +7,25 @@
 
 #include "ch_internal.cuh"
 
-// Sticky per-device error word written by the kernels (ST_* bits).
-__device__ unsigned g_ch_status = 0;
+// Sticky error words written by the kernels (ST_* bits), one per stream: a
+// call's kernels record into the word of the stream the call was made on, so
+// an error is reported to the caller of ch_sync_status on that stream only.
+// Slots are handed out to streams in order of first use and never recycled;
+// streams beyond the STATUS_SLOTS-th distinct one share the last word.
+constexpr int STATUS_SLOTS = 1024;
+__device__ unsigned g_ch_status[STATUS_SLOTS + 1];
+// ch_sync_status moves a stream's word here (atomic exchange with 0, on that
+// stream) and reads it back with a copy ordered on the same stream.
+__device__ unsigned g_ch_taken[STATUS_SLOTS + 1];
 
 namespace ch {
 
 namespace {
 constexpr int MAX_DEV = 64;
 std::mutex g_mu;
-unsigned *g_status_ptr[MAX_DEV] = {};
+unsigned *g_status_base[MAX_DEV] = {};
+unsigned *g_taken_base[MAX_DEV] = {};
+std::map<cudaStream_t, int> g_slot_of[MAX_DEV];
 int g_sms[MAX_DEV] = {};
 
 inline bool aligned8(const void *p) { return ((uintptr_t)p & 7) == 0; }
@@ -38,21 +48,47 @@ void next_trace(cudaEvent_t *e0, cudaEvent_t *e1)
     }
 }
 inline int cuda_rc(cudaError_t e) { return e == cudaSuccess ? CH_OK : CH_ERR_CUDA; }
-}  // namespace
 
-unsigned *device_status_ptr()
+// Slot index of stream s on the current device (-1 on failure); the device
+// addresses of both word arrays are resolved on the device's first use.
+int status_slot(cudaStream_t s, unsigned **word, unsigned **taken)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV)
-        return nullptr;
+        return -1;
     std::lock_guard<std::mutex> g(g_mu);
-    if (!g_status_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_ch_status) != cudaSuccess)
-            return nullptr;
-        g_status_ptr[dev] = reinterpret_cast<unsigned *>(p);
+    if (!g_status_base[dev]) {
+        void *a = nullptr, *b = nullptr;
+        if (cudaGetSymbolAddress(&a, g_ch_status) != cudaSuccess ||
+            cudaGetSymbolAddress(&b, g_ch_taken) != cudaSuccess)
+            return -1;
+        g_status_base[dev] = reinterpret_cast<unsigned *>(a);
+        g_taken_base[dev] = reinterpret_cast<unsigned *>(b);
     }
-    return g_status_ptr[dev];
+    auto &m = g_slot_of[dev];
+    auto it = m.find(s);
+    int k;
+    if (it != m.end()) {
+        k = it->second;
+    } else {
+        k = std::min((int)m.size(), STATUS_SLOTS);
+        m.emplace(s, k);
+    }
+    if (word)
+        *word = g_status_base[dev] + k;
+    if (taken)
+        *taken = g_taken_base[dev] + k;
+    return k;
+}
+
+// Moves the stream's status word to its read-back word (stream-ordered).
+__global__ void k_status_take(unsigned *word, unsigned *taken) { *taken = atomicExch(word, 0u); }
+}  // namespace
+
+unsigned *device_status_ptr(cudaStream_t s)
+{
+    unsigned *w = nullptr;
+    return status_slot(s, &w, nullptr) < 0 ? nullptr : w;
 }
 
 int sm_count()
@@ -148,19 +184,17 @@ int ch_version(void) { return (1 << 16) | 0; }
 int ch_sync_status(ch_stream_t stream)
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (cudaStreamSynchronize(s) != cudaSuccess)
+    unsigned *word = nullptr, *taken = nullptr;
+    if (status_slot(s, &word, &taken) < 0)
         return CH_ERR_CUDA;
-    unsigned *st = device_status_ptr();
-    if (!st)
-        return CH_ERR_CUDA;
+    // exchange and read-back are ordered after the stream's earlier work and
+    // touch only this stream's word; other streams keep running
+    k_status_take<<<1, 1, 0, s>>>(word, taken);
     unsigned v = 0;
-    if (cudaMemcpy(&v, st, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&v, taken, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
         return CH_ERR_CUDA;
-    if (v) {
-        const unsigned zero = 0;
-        if (cudaMemcpy(st, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
-            return CH_ERR_CUDA;
-    }
     if (v & ST_RANGE)
         return CH_ERR_RANGE;
     if (v & ST_CAPACITY)
@@ -172,10 +206,11 @@ int ch_sync_status(ch_stream_t stream)
 
 int ch_clear_status(ch_stream_t stream)
 {
-    unsigned *st = device_status_ptr();
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned *st = device_status_ptr(s);
     if (!st)
         return CH_ERR_CUDA;
-    return cuda_rc(cudaMemsetAsync(st, 0, sizeof(unsigned), reinterpret_cast<cudaStream_t>(stream)));
+    return cuda_rc(cudaMemsetAsync(st, 0, sizeof(unsigned), s));
 }
 
 int ch_trace_set(void *const *events, int npairs)
@@ -233,7 +268,7 @@ int ch_reduce(const int32_t *pts, int64_t n, int32_t p, int32_t *L, void *worksp
     const size_t need = reduce_partials_bytes(pl, p);
     if (ws_bytes < need || (need > 0 && !workspace))
         return CH_ERR_WORKSPACE;
-    unsigned *st = device_status_ptr();
+    unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
     if (!st)
         return CH_ERR_CUDA;
     void *part = workspace;
@@ -265,7 +300,7 @@ int ch_chain(const int32_t *L, int32_t p, int32_t *lower, int32_t *upper, int32_
     ch_chain_workspace_size(p, &need);
     if (ws_bytes < need || !workspace)
         return CH_ERR_WORKSPACE;
-    unsigned *st = device_status_ptr();
+    unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
     if (!st)
         return CH_ERR_CUDA;
     return cuda_rc(chain_launch(L, p, lower, upper, counts, mask, workspace, false, nullptr,
@@ -289,7 +324,7 @@ int ch_hull(const int32_t *lower, const int32_t *upper, const int32_t *counts, i
         return CH_ERR_ARG;
     if (ws_bytes < hull_ws_bytes(p) || !workspace)
         return CH_ERR_WORKSPACE;
-    unsigned *st = device_status_ptr();
+    unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
     if (!st)
         return CH_ERR_CUDA;
     return cuda_rc(hull_launch(lower, upper, counts, p, hull, hull_count, workspace, st,
@@ -328,10 +363,10 @@ int convex_hull_square(const int32_t *pts, int64_t n, int32_t p, const Frame &fr
         return rc;
     if (ws_bytes < w.end || !workspace)
         return CH_ERR_WORKSPACE;
-    unsigned *st = device_status_ptr();
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned *st = device_status_ptr(s);
     if (!st)
         return CH_ERR_CUDA;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *b = reinterpret_cast<char *>(workspace);
     if (!L && w.plan.mode != 0)
         L = reinterpret_cast<int32_t *>(b + w.L);  // the filtered forms write L directly
@@ -406,7 +441,7 @@ int ch_reduce_u16(const uint32_t *pts, int64_t n, int32_t p, int32_t *L, void *w
     const size_t need = reduce_partials_bytes(pl, p);
     if (ws_bytes < need || (need > 0 && !workspace))
         return CH_ERR_WORKSPACE;
-    unsigned *st = device_status_ptr();
+    unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
     if (!st)
         return CH_ERR_CUDA;
     cudaEvent_t ev0, ev1;
@@ -483,7 +518,7 @@ int ch_hull_batched(const int32_t *pts, const int64_t *offsets, const int32_t *p
             return CH_ERR_ARG;  // no plan prepared in this workspace for B sets
         info = it->second;
     }
-    unsigned *st = device_status_ptr();
+    unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
     if (!st)
         return CH_ERR_CUDA;
     return batch_launch(pts, reinterpret_cast<int2 *>(hull_out), hull_offsets, hull_counts, nullptr,
@@ -508,7 +543,7 @@ int ch_reduce_batched(const int32_t *pts, const int64_t *offsets, const int32_t 
             return CH_ERR_ARG;  // no plan prepared in this workspace for B sets
         info = it->second;
     }
-    unsigned *st = device_status_ptr();
+    unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
     if (!st)
         return CH_ERR_CUDA;
     return batch_launch(pts, nullptr, nullptr, nullptr, reinterpret_cast<int2 *>(L_out), L_offsets,
@@ -690,10 +725,12 @@ int ch_hull_learned_kernel_count(int64_t n, int32_t p, int32_t with_net, int32_t
 
 int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *params, int32_t *L,
                     int32_t *Linit, int32_t *lower, int32_t *upper, int32_t *counts, int32_t *hull,
-                    int32_t *hull_count, void *workspace, size_t ws_bytes, ch_stream_t stream)
+                    int32_t *hull_count, ch_cull_stats *stats, void *workspace, size_t ws_bytes,
+                    ch_stream_t stream)
 {
     if (check_np(n, p) != CH_OK || (n > 0 && !pts) || !hull || !hull_count || !aligned8(pts) ||
-        !aligned8(L) || !aligned8(Linit) || !aligned8(lower) || !aligned8(upper) || !aligned8(hull))
+        !aligned8(L) || !aligned8(Linit) || !aligned8(lower) || !aligned8(upper) ||
+        !aligned8(hull) || !aligned8(stats))
         return CH_ERR_ARG;
     LearnedWs w;
     int rc = learned_layout(n, p, &w);
@@ -701,10 +738,10 @@ int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *param
         return rc;
     if (ws_bytes < w.end || !workspace)
         return CH_ERR_WORKSPACE;
-    unsigned *st = device_status_ptr();
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned *st = device_status_ptr(s);
     if (!st)
         return CH_ERR_CUDA;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *b = reinterpret_cast<char *>(workspace);
     const PathWs &pw = w.path;
     if (!L)
@@ -726,11 +763,14 @@ int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *param
     // Linit, the start of L (filtered forms) and tightens the filter with
     // the polygon (mode 1); in mode 0 it clears the look-back state itself
     cudaError_t e = reduce_warm_launch(pw.plan, pts, n, square_frame(p), part, L, s, zero, nzero);
+    if (e == cudaSuccess && stats)
+        e = cudaMemsetAsync(&stats->culled, 0, sizeof(stats->culled), s);
     if (e == cudaSuccess)
         e = cull_launch(pts, n, p, params, b + w.cull, Linit, mode != 0 ? L : nullptr,
                         mode == 1 ? reinterpret_cast<uint16_t *>(part) : nullptr, mode == 1,
                         pw.plan.shift, mode == 0 ? zero : nullptr, mode == 0 ? nzero : 0, nullptr,
-                        nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, s);
+                        nullptr, nullptr, nullptr, stats ? &stats->poly_vertices : nullptr,
+                        nullptr, stats ? &stats->chosen : nullptr, s);
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
     cudaEvent_t ev0, ev1;
@@ -747,7 +787,11 @@ int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *param
                      st, s, Linit);
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
-    return cuda_rc(hull_final_launch(hl, hw, hull, hull_count, s));
+    e = hull_final_launch(hl, hw, hull, hull_count, s);
+    if (e == cudaSuccess && stats)
+        e = cull_count_launch(pts, n, p, Linit, reinterpret_cast<unsigned long long *>(&stats->culled),
+                              s);
+    return cuda_rc(e);
 }
 
 // ---------------------------------------------------------------- any integer points
@@ -815,10 +859,10 @@ int ch_convex_hull_box(const int32_t *pts, int64_t n, const int32_t *host_box, i
         return rc;
     if (ws_bytes < w.end || !workspace)
         return CH_ERR_WORKSPACE;
-    unsigned *st = device_status_ptr();
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned *st = device_status_ptr(s);
     if (!st)
         return CH_ERR_CUDA;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *b = reinterpret_cast<char *>(workspace);
     const PathWs &pw = w.path;
     int32_t *L = reinterpret_cast<int32_t *>(b + pw.L);
@@ -925,7 +969,7 @@ int ch_polyline(const int32_t *L, int32_t p, int32_t *poly, int32_t *count, void
         return CH_ERR_ARG;
     if (ws_bytes < polyline_state_bytes(p) || !workspace)
         return CH_ERR_WORKSPACE;
-    unsigned *st = device_status_ptr();
+    unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
     if (!st)
         return CH_ERR_CUDA;
     return cuda_rc(polyline_launch(L, p, p, poly, count, workspace, false, st,
@@ -949,7 +993,7 @@ int ch_hull_melkman(const int32_t *poly, const int32_t *count, int32_t p, int32_
     const size_t need = melkman_ws_bytes(p);
     if (ws_bytes < need || (need && !workspace))
         return CH_ERR_WORKSPACE;
-    unsigned *st = device_status_ptr();
+    unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
     if (!st)
         return CH_ERR_CUDA;
     return cuda_rc(melkman_launch(poly, count, p, hull, hull_count, workspace, st,
@@ -1003,10 +1047,10 @@ int ch_convex_hull_melkman(const int32_t *pts, int64_t n, int32_t p, int32_t *L,
         return rc;
     if (ws_bytes < w.end || !workspace)
         return CH_ERR_WORKSPACE;
-    unsigned *st = device_status_ptr();
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned *st = device_status_ptr(s);
     if (!st)
         return CH_ERR_CUDA;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *b = reinterpret_cast<char *>(workspace);
     if (!L)
         L = reinterpret_cast<int32_t *>(b + w.L);
@@ -1060,7 +1104,7 @@ int ch_convex_hull_sparse(const int32_t *pts, int64_t n, int32_t p, int32_t *low
     const SparseLayout L = sparse_layout(n, p);
     if (ws_bytes < L.end || !workspace)
         return CH_ERR_WORKSPACE;
-    unsigned *st = device_status_ptr();
+    unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
     if (!st)
         return CH_ERR_CUDA;
     char *b = reinterpret_cast<char *>(workspace);
@@ -1082,7 +1126,7 @@ int ch_reduce_rows(const int32_t *L, int32_t p, int32_t *R, ch_stream_t stream)
 {
     if (p < 1 || p > CH_MAX_P || !L || !R || !aligned8(L) || !aligned8(R))
         return CH_ERR_ARG;
-    unsigned *st = device_status_ptr();
+    unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
     if (!st)
         return CH_ERR_CUDA;
     return cuda_rc(rows_launch(L, p, R, st, reinterpret_cast<cudaStream_t>(stream)));
@@ -1133,10 +1177,10 @@ int ch_convex_hull_rxy(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int
         return rc;
     if (ws_bytes < w.end || !workspace)
         return CH_ERR_WORKSPACE;
-    unsigned *st = device_status_ptr();
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned *st = device_status_ptr(s);
     if (!st)
         return CH_ERR_CUDA;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *b = reinterpret_cast<char *>(workspace);
     const PathWs &pw = w.path;
     if (!L)

@@ -10,7 +10,7 @@
 
 namespace ch {
 
-// Bits of the per-device sticky status word.
+// Bits of the per-stream sticky status word.
 enum : unsigned {
     ST_RANGE = 1u,
     ST_CAPACITY = 2u,
@@ -49,6 +49,29 @@ inline cudaError_t launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// launch() for a grid of thread-block clusters of `cluster` CTAs along x
+// (the grid's x extent a multiple of it).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_cluster(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                  cudaStream_t s, int cluster, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    at[1].id = cudaLaunchAttributeClusterDimension;
+    at[1].val.clusterDim.x = (unsigned)cluster;
+    at[1].val.clusterDim.y = 1;
+    at[1].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
@@ -105,7 +128,7 @@ inline int frame_mode(const Frame &f)
 // ---- reduction (reduce.cu) ----
 struct ReducePlan {
     int mode;      // 0: private copies, 1: filtered global L, 2: global L only
-    int cluster;   // CTAs per cluster (always 1)
+    int cluster;   // mode 1: CTAs per cluster of the filter warm-up (1, 2, 4 or 8)
     int grid;      // CTAs of the main reduction kernel
     int threads;   // threads per CTA of the main reduction kernel
     int copies;    // mode 0: number of int2[p] partial arrays
@@ -223,6 +246,10 @@ cudaError_t cull_launch(const int32_t *pts, int64_t n, int p, const float *param
                         float *dirs_out, int32_t *poly_out, int32_t *poly_count, int64_t *ext_out,
                         int32_t *chosen, cudaStream_t s);
 int cull_kernel_count(bool net);
+// *culled += the points strictly inside the culling polygon of Linit
+// (Linit.lo <= y <= Linit.hi in their column); no launch when n = 0.
+cudaError_t cull_count_launch(const int32_t *pts, int64_t n, int p, const int32_t *Linit,
+                              unsigned long long *culled, cudaStream_t s);
 
 // ---- bounding box and frames (box.cu) ----
 int bbox_parts();
@@ -274,7 +301,8 @@ int sparse_kernel_count(const SparseLayout &L);
 cudaError_t rows_launch(const int32_t *L, int p, int32_t *R, unsigned *status, cudaStream_t s);
 
 // ---- api.cu ----
-unsigned *device_status_ptr();  // this device's status word (nullptr on failure)
+// The status word of stream s on the current device (nullptr on failure).
+unsigned *device_status_ptr(cudaStream_t s);
 int sm_count();
 
 }  // namespace ch

@@ -55,7 +55,7 @@ extern "C" int ch_chain_noalloc(const int32_t *L, int32_t p, int32_t *lower, int
     if (ch::chain_state_bytes(p) > sizeof(g_chain_scratch))
         return CH_ERR_CAPACITY;
     void *state = scratch_ptr();
-    unsigned *st = ch::device_status_ptr();
+    unsigned *st = ch::device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
     if (!state || !st)
         return CH_ERR_CUDA;
     const cudaError_t e = ch::chain_launch(L, p, lower, upper, counts, mask, state, false, nullptr,

@@ -570,7 +570,43 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Points strictly inside the culling polygon (Linit.lo <= y <= Linit.hi in
+// their column); points outside [1,p]^2 are not counted.  Adds to *culled.
+__global__ void __launch_bounds__(256)
+    k_cull_count(const int2 *__restrict__ pts, long long n, int p, const int2 *__restrict__ Linit,
+                 unsigned long long *culled)
+{
+    pdl_wait();
+    pdl_trigger();
+    unsigned long long k = 0;
+    const unsigned up = (unsigned)p;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int2 q = __ldcs(pts + i);
+        const unsigned c = (unsigned)(q.x - 1);
+        if (c < up && (unsigned)(q.y - 1) < up) {
+            const int2 li = __ldg(Linit + c);
+            k += (li.x <= q.y && q.y <= li.y) ? 1ull : 0ull;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        k += __shfl_xor_sync(0xFFFFFFFFu, k, o);
+    if ((threadIdx.x & 31) == 0 && k)
+        atomicAdd(culled, k);
+}
+
 }  // namespace
+
+cudaError_t cull_count_launch(const int32_t *pts, int64_t n, int p, const int32_t *Linit,
+                              unsigned long long *culled, cudaStream_t s)
+{
+    const long long blocks = std::min<long long>((n + 255) / 256, (long long)sm_count() * 8);
+    if (blocks > 0)
+        launch(k_cull_count, (int)blocks, 256, 0, s, reinterpret_cast<const int2 *>(pts), (long long)n,
+               p, reinterpret_cast<const int2 *>(Linit), culled);
+    return cudaGetLastError();
+}
 
 size_t cull_ws_bytes(int p)
 {

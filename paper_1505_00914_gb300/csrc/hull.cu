@@ -245,7 +245,7 @@ cudaError_t hull_final_launch(const HullLayout &h, void *ws, int32_t *hull, int3
     char *b = reinterpret_cast<char *>(ws);
     size_t cand = h.cand, ccnt = h.ccnt;
     if (h.refilter) {
-        unsigned *status = device_status_ptr();
+        unsigned *status = device_status_ptr(s);
         if (!status)
             return cudaErrorUnknown;
         const int ntile = (h.nblk + 31) / 32;

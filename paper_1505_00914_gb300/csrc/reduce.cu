@@ -34,6 +34,7 @@
 //   point takes a read-then-atomic test against the global L.
 #include <map>
 #include <mutex>
+#include <tuple>
 
 #include "ch_internal.cuh"
 
@@ -270,6 +271,45 @@ __device__ __forceinline__ uint4 tighter8(uint4 a, uint4 b)
     return make_uint4(tighter2(a.x, b.x), tighter2(a.y, b.y), tighter2(a.z, b.z), tighter2(a.w, b.w));
 }
 
+// Thread-block cluster helpers (a launch without clusters is a cluster of one).
+__device__ __forceinline__ unsigned cluster_ctas()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Every thread of every CTA of the cluster; orders the shared-memory writes
+// before it with the reads after it, cluster-wide.
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+// 16 bytes at the same shared-memory offset as `p`, in CTA `rank` of the cluster.
+__device__ __forceinline__ uint4 ld_cluster_v4(const void *p, unsigned rank)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    unsigned ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    uint4 v;
+    asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(ra)
+                 : "memory");
+    return v;
+}
+
+// Each CTA builds a filter from the first 1/WARM_DIV of its slice.  Launched
+// in clusters of C CTAs, the C filters of a cluster are merged through
+// distributed shared memory (CTA rank r merges the r-th C-th of the columns
+// over all C) and the cluster writes one slot row, so the merge kernel reads
+// grid / C rows instead of grid.
 template <int RT, int FM>
 __global__ void __launch_bounds__(RT)
     k_filter_warm(const int32_t *__restrict__ pts, int64_t n, Frame fr, int shift, int grid,
@@ -300,10 +340,25 @@ __global__ void __launch_bounds__(RT)
     slice_of(pv.nvec, blockIdx.x, grid, s0, e0);
     const int64_t warm = s0 + (e0 - s0) / WARM_DIV;
     stream_pairs<RT, true>(pv.p4, s0, warm, [&](const int4 &v) { each_point<FM>(v, learn); });
-    __syncthreads();
-    uint4 *out = reinterpret_cast<uint4 *>(slots) + (size_t)blockIdx.x * words;
-    for (int i = threadIdx.x; i < words; i += RT)
-        __stcg(out + i, F4[i]);
+    const unsigned C = cluster_ctas();
+    uint4 *out = reinterpret_cast<uint4 *>(slots) + (size_t)(blockIdx.x / C) * words;
+    if (C == 1) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < words; i += RT)
+            __stcg(out + i, F4[i]);
+        return;
+    }
+    cluster_sync();  // every filter of the cluster is complete
+    const unsigned r = cluster_rank();
+    const int per = (int)((words + C - 1) / C);
+    const int i1 = min(words, (int)(r + 1) * per);
+    for (int i = (int)r * per + threadIdx.x; i < i1; i += RT) {
+        uint4 acc = F4[i];
+        for (unsigned k = 1; k < C; ++k)
+            acc = tighter8(acc, ld_cluster_v4(F4 + i, (r + k) % C));
+        __stcg(out + i, acc);
+    }
+    cluster_sync();  // no CTA exits while another may still read its filter
 }
 
 // G = column-wise tighter-of over the `rows` slot rows; also L = (p+1, -1).
@@ -519,6 +574,50 @@ int private_bps(int dev, size_t smem)
     return bps;
 }
 
+#ifndef CH_WARM_CLUSTER_MAX
+#define CH_WARM_CLUSTER_MAX 8  // largest cluster of the filter warm-up (portable limit)
+#endif
+std::map<std::tuple<int, size_t, int>, int> g_wcl;  // (device, smem, grid) -> cluster size
+
+// Largest cluster size C <= CH_WARM_CLUSTER_MAX (a power of two dividing the
+// grid) for which the whole warm-up grid is resident at once, so that no
+// cluster waits for a second wave; 1 if none.
+int warm_cluster(int dev, size_t smem, int grid)
+{
+    std::lock_guard<std::mutex> g(g_dev_mu);
+    const auto key = std::make_tuple(dev, smem, grid);
+    auto it = g_wcl.find(key);
+    if (it != g_wcl.end())
+        return it->second;
+    int best = 1;
+    for (int C = CH_WARM_CLUSTER_MAX; C >= 2; C /= 2) {
+        if (grid % C)
+            continue;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(1024);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_filter_warm<1024, 0>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if ((long long)nclusters * C >= grid) {
+            best = C;
+            break;
+        }
+    }
+    g_wcl[key] = best;
+    return best;
+}
+
 int filter_shift(int p)
 {
     int s = 0;
@@ -558,6 +657,8 @@ int reduce_plan(int64_t n, int nc, int nr, ReducePlan *pl)
         pl->grid = sms;
         pl->copies = 0;
         pl->shift = filter_shift(nr);
+        if (pl->mode == 1)
+            pl->cluster = warm_cluster(dev, pl->smem, pl->grid);
     }
     return CH_OK;
 }
@@ -587,10 +688,15 @@ void launch_warm(const ReducePlan &pl, const int32_t *pts, int64_t n, const Fram
     uint16_t *G = reinterpret_cast<uint16_t *>(part);
     uint16_t *slots = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(part) +
                                                    ((((size_t)f.nc * 2) + 255) & ~size_t(255)));
-    launch(k_filter_warm<1024, FM>, pl.grid, 1024, pl.smem, s, pts, n, f, pl.shift, pl.grid, slots);
+    if (pl.cluster > 1)
+        launch_cluster(k_filter_warm<1024, FM>, pl.grid, 1024, pl.smem, s, pl.cluster, pts, n, f,
+                       pl.shift, pl.grid, slots);
+    else
+        launch(k_filter_warm<1024, FM>, pl.grid, 1024, pl.smem, s, pts, n, f, pl.shift, pl.grid,
+               slots);
     const int words = (f.nc + 7) / 8;
-    launch(k_filter_merge, (words + MG_V - 1) / MG_V, MG_V * MG_GROUPS, 0, s, slots, pl.grid, f.nc,
-           f.nr, G, L2, zero, nzero);
+    launch(k_filter_merge, (words + MG_V - 1) / MG_V, MG_V * MG_GROUPS, 0, s, slots,
+           pl.grid / pl.cluster, f.nc, f.nr, G, L2, zero, nzero);
 }
 
 template <int FM>

@@ -132,3 +132,36 @@ def test_binding_rejects_host_point_arrays():
     with pytest.raises(ValueError, match="CUDA tensors"):
         ch._ptr(torch.zeros(3, dtype=torch.int32))
     assert ch._ptr(None) is None
+
+
+def test_python_constants_match_the_header():
+    """The binding's copies of the header's #define values agree with it."""
+    from paper_1505_00914_gb300 import ch
+    text = open(os.path.join(ROOT, "include", "ch.h")).read()
+    defs = {m.group(1): m.group(2) for m in re.finditer(r"#define\s+(CH_[A-Z0-9_]+)\s+(.+)", text)}
+
+    def value(expr):
+        expr = re.sub(r"/\*.*?\*/", "", expr).strip()
+        return eval(expr, {}, {})
+
+    names = ["CH_CHAIN_NOALLOC_MAX_P", "CH_OK", "CH_ERR_ARG", "CH_ERR_RANGE", "CH_ERR_CAPACITY",
+             "CH_ERR_TIMEOUT", "CH_ERR_CUDA", "CH_ERR_WORKSPACE", "CH_MLP_IN", "CH_MLP_HID",
+             "CH_MLP_K", "CH_MLP_PARAMS"]
+    for n in names:
+        if hasattr(ch, n):
+            assert getattr(ch, n) == value(defs[n]), n
+    assert ch.CH_CHAIN_NOALLOC_MAX_P == value(defs["CH_CHAIN_NOALLOC_MAX_P"])
+
+
+def test_chain_binding_checks_array_sizes():
+    """The chain bindings refuse arrays too small for p, or of the wrong type,
+    before the library is called (CPU tensors fail the CUDA check first)."""
+    import torch
+    from paper_1505_00914_gb300 import ch
+    L = torch.empty((4, 2), dtype=torch.int32)
+    lo = torch.empty((4, 2), dtype=torch.int32)
+    cnt = torch.empty(2, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        ch.ch_chain_noalloc(L, 4, lo, lo, cnt)  # host tensors
+    with pytest.raises(ValueError):
+        ch._check_chain_args(L, 4, lo, lo, cnt, None)

@@ -5,7 +5,7 @@ import pytest
 import torch
 
 import oracle
-from paper_1505_00914_gb300 import ch, synth
+from paper_1505_00914_gb300 import autotune, ch, synth
 from gpu_util import need_gpu
 
 pytestmark = pytest.mark.gpu
@@ -105,7 +105,10 @@ def test_batched_range_error_and_arguments():
 
 def test_batched_config_full_size_sampled():
     """10,000 sets, n log-uniform in [1e2, 1e6], p in {256, 1024, 4096, 16384},
-    uniform/disc/Gaussian: the launch the benchmark times; 200 sets checked."""
+    uniform/disc/Gaussian (the benchmark's batch), one direct launch at the
+    default chunk multiplier 64; 200 sets and the largest checked.  The
+    benchmark's own launch (autotuned multiplier, CUDA-graph replay) is
+    checked by test_batched_graph_replay_as_benchmarked."""
     pts, offsets, ps, _ = synth.batched(10_000, seed=4)
     hull, hoff, cnt = run_batch(pts, offsets, ps)
     rng = np.random.default_rng(0)
@@ -146,3 +149,99 @@ def test_culling_polygon_shapes():
     for cm in (1, 64):
         hull, hoff, cnt = run_batch(pts, offsets, ps, chunk_mult=cm)
         check_sets(pts, offsets, ps, hull, hoff, cnt)
+
+
+def _device_batch(pts, offsets, ps):
+    d_pts = torch.from_numpy(np.ascontiguousarray(pts, dtype=np.int32).reshape(-1, 2)).cuda()
+    d_off = torch.from_numpy(np.asarray(offsets, np.int64)).cuda()
+    d_ps = torch.from_numpy(np.asarray(ps, np.int32)).cuda()
+    hoff = ch.hull_capacity_offsets(offsets, ps)
+    d_hoff = torch.from_numpy(hoff).cuda()
+    hull = torch.zeros((max(1, int(hoff[-1])), 2), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(len(ps), dtype=torch.int32, device="cuda")
+    return d_pts, d_off, d_ps, hoff, d_hoff, hull, cnt
+
+
+def run_batch_graph(dev_batch, offsets, ps, chunk_mult, replays=2):
+    """The benchmark's launch: prepare the plan, a first call on a side stream
+    (set-up), capture one ch_hull_batched in a CUDA graph on that stream, then
+    replay the graph; the outputs are overwritten with garbage before every
+    replay, so each replay's result is its own.  Returns one (hull, counts)
+    per replay."""
+    d_pts, d_off, d_ps, hoff, d_hoff, hull, cnt = dev_batch
+    ws = torch.empty(ch.ch_batched_workspace_size(offsets, ps, chunk_mult), dtype=torch.uint8,
+                     device="cuda")
+    ch.ch_batched_prepare(offsets, ps, ws, chunk_mult)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        ch.ch_hull_batched(d_pts, d_off, d_ps, hull, d_hoff, cnt, ws)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        ch.ch_hull_batched(d_pts, d_off, d_ps, hull, d_hoff, cnt, ws)
+    out = []
+    for _ in range(replays):
+        hull.fill_(-9)
+        cnt.fill_(-7)
+        graph.replay()
+        torch.cuda.synchronize()
+        out.append((hull.cpu().numpy(), cnt.cpu().numpy()))
+    assert ch.ch_sync_status(stream) == ch.CH_OK
+    del graph
+    return out
+
+
+class _OracleHulls:
+    """Oracle hull of each set (Algorithm 1, then the hull of its chains),
+    computed once per set."""
+
+    def __init__(self, pts, offsets, ps):
+        self.pts, self.off, self.ps, self.h = pts, offsets, ps, {}
+
+    def __call__(self, s):
+        if s not in self.h:
+            P = self.pts[self.off[s]:self.off[s + 1]]
+            self.h[s] = oracle.hull_chain(oracle.reduce(P, int(self.ps[s])))
+        return self.h[s]
+
+
+def _check_against(hulls, hoff, hull, cnt, sets, where):
+    for s in sets:
+        H = hulls(s)
+        assert cnt[s] == H.shape[0], (where, s, int(cnt[s]), H.shape[0])
+        np.testing.assert_array_equal(hull[hoff[s]:hoff[s] + cnt[s]], H, err_msg=f"{where} set {s}")
+
+
+def test_batched_graph_replay_as_benchmarked():
+    """The launch the benchmark times: the 10,000-set batch, the chunk
+    multiplier chosen by the autotuner on this batch (and 4096, the choice of
+    the recorded runs), one ch_hull_batched captured in a CUDA graph and
+    replayed twice; 200 sampled sets and the largest against the oracle."""
+    pts, offsets, ps, _ = synth.batched(10_000, seed=4)
+    db = _device_batch(pts, offsets, ps)
+    d_pts, d_off, d_ps, hoff, d_hoff, hull, cnt = db
+    best, times = autotune.tune_batched(d_pts, offsets, ps, d_off, d_ps, hull, d_hoff, cnt,
+                                        use_cache=False)
+    assert best in autotune.CANDIDATES and set(times) == set(autotune.CANDIDATES)
+    rng = np.random.default_rng(0)
+    sample = sorted(set(rng.choice(len(ps), size=200, replace=False).tolist())
+                    | {int(np.argmax(np.diff(offsets)))})
+    hulls = _OracleHulls(pts, offsets, ps)
+    for cm in sorted({best, 4096}):
+        for r, (h, c) in enumerate(run_batch_graph(db, offsets, ps, cm)):
+            assert np.all(c >= 1)
+            _check_against(hulls, hoff, h, c, sample, f"chunk_mult {cm} replay {r}")
+
+
+def test_batched_graph_replay_every_candidate():
+    """Every chunk multiplier the autotuner may choose, each as a CUDA-graph
+    replay (twice) on a 1,000-set batch of the benchmark's recipe: every set
+    against the oracle."""
+    pts, offsets, ps, _ = synth.batched(1_000, seed=11)
+    db = _device_batch(pts, offsets, ps)
+    hoff = db[3]
+    hulls = _OracleHulls(pts, offsets, ps)
+    for cm in autotune.CANDIDATES:
+        for r, (h, c) in enumerate(run_batch_graph(db, offsets, ps, cm)):
+            _check_against(hulls, hoff, h, c, range(len(ps)), f"chunk_mult {cm} replay {r}")

@@ -45,8 +45,9 @@ def check_proposal(P, p, params=None):
     if params is not None:
         y = o["net_out"].astype(np.float64)
         Y = Lm.forward(host(params).astype(np.float64), o["features"])[2][0]
-        assert np.max(np.abs(y - Y)) <= 2.0 ** -6 * (np.max(np.abs(Y)) + 1)
-        th = Lm.directions(y)
+        if np.all(np.isfinite(Y)):  # NaN weights: the directions fall back (checked below)
+            assert np.max(np.abs(y - Y)) <= 2.0 ** -6 * (np.max(np.abs(Y)) + 1)
+        th = Lm.directions(np.where(np.isnan(y), 0.0, y))
         np.testing.assert_allclose(o["dirs"][1][0], np.cos(th), atol=4e-6)
         np.testing.assert_allclose(o["dirs"][1][1], np.sin(th), atol=4e-6)
     else:
@@ -76,7 +77,9 @@ def check_learned(P, p, params=None):
     lo = torch.empty((p, 2), dtype=torch.int32, device="cuda")
     up = torch.empty((p, 2), dtype=torch.int32, device="cuda")
     cnt = torch.empty(2, dtype=torch.int32, device="cuda")
-    h, hc = ch.ch_hull_learned(d, p, params=params, L=L, Linit=Li, lower=lo, upper=up, counts=cnt)
+    stats = ch.cull_stats_tensor()
+    h, hc = ch.ch_hull_learned(d, p, params=params, L=L, Linit=Li, lower=lo, upper=up, counts=cnt,
+                               stats=stats)
     Li, L = host(Li), host(L)
     Lr = oracle.reduce_from(P, p, Li)
     np.testing.assert_array_equal(L, Lr)
@@ -86,9 +89,33 @@ def check_learned(P, p, params=None):
     np.testing.assert_array_equal(host(lo)[: cnt[0]], lo_o)
     np.testing.assert_array_equal(host(up)[: cnt[1]], up_o)
     np.testing.assert_array_equal(host(h)[: int(host(hc)[0])], H)
-    # the start array is the proposal's
-    np.testing.assert_array_equal(Li, host(ch.ch_cull_propose(d, p, params=params)["Linit"]))
+    # the start array is the proposal's, whose polygon is checked against the oracle
+    o = check_proposal(P, p, params)
+    np.testing.assert_array_equal(Li, o["Linit"])
+    # the call's statistics: the polygon used, and the points strictly inside it
+    st = ch.cull_stats(stats)
+    k = int(o["poly_count"][0])
+    assert st["poly_vertices"] == k and st["chosen"] == int(o["chosen"][0])
+    assert st["culled"] == strictly_inside(P, o["poly"][:k])
+    if P.shape[0]:
+        lo_i, hi_i = Li[P[:, 0] - 1, 0], Li[P[:, 0] - 1, 1]
+        assert st["culled"] == int(np.count_nonzero((lo_i <= P[:, 1]) & (P[:, 1] <= hi_i)))
     return H, Li
+
+
+def strictly_inside(P, poly):
+    """Points strictly inside the convex counter-clockwise polygon: strictly
+    left of every edge (int64 orientation); none for fewer than 3 vertices."""
+    k = poly.shape[0]
+    if k < 3 or P.shape[0] == 0:
+        return 0
+    q = P.astype(np.int64)
+    v = poly.astype(np.int64)
+    inside = np.ones(P.shape[0], bool)
+    for i in range(k):
+        a, b = v[i], v[(i + 1) % k]
+        inside &= (b[0] - a[0]) * (q[:, 1] - a[1]) - (b[1] - a[1]) * (q[:, 0] - a[0]) > 0
+    return int(np.count_nonzero(inside))
 
 
 DISTS = ("uniform", "disc", "gaussian", "annulus", "shells")
