@@ -100,7 +100,8 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_OF_FORM = ("k_reduce_private", "k_reduce_filtered", "k_reduce_global")
+# the dominant kernel of each form ch_plan_info reports (3: the whole path in one launch)
+KERNEL_OF_FORM = ("k_reduce_private", "k_reduce_filtered", "k_reduce_global", "k_small")
 
 
 def _kernel_sha(src_path, name):

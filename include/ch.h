@@ -94,11 +94,15 @@ int ch_clear_status(ch_stream_t stream);
  * the calls that use them. */
 int ch_trace_set(void *const *events, int npairs);
 
-/* How ch_convex_hull will run n points of side p on the current device:
+/* How ch_convex_hull will run n points of side p on the current device
+ * when it is not asked for the chains (lower, upper and counts NULL):
  * *form = 0 (private shared-memory copies of L, p <= 29056), 1 (filtered
- * global L, p <= 116224) or 2 (global L with a read-then-atomic test), and
- * *kernels = the number of kernels one ch_convex_hull call launches (with the
- * second filter pass of the hull step from 128 runs of 1024 columns on).
+ * global L, p <= 116224), 2 (global L with a read-then-atomic test) or 3
+ * (small problems: p <= 16384, at most 16384 points per thread block and
+ * the blocks' partial copies of L at most 65536 words in all, the whole path
+ * in one launch), and *kernels = the number of kernels one ch_convex_hull
+ * call launches (with the second filter pass of the hull step from 128 runs
+ * of 1024 columns on).  A call that asks for the chains never takes form 3.
  * Either pointer may be NULL. */
 int ch_plan_info(int64_t n, int32_t p, int32_t *form, int32_t *kernels);
 
@@ -156,7 +160,12 @@ int ch_hull(const int32_t *lower, const int32_t *upper, const int32_t *counts,
 int ch_convex_hull_workspace_size(int64_t n, int32_t p, size_t *bytes);
 
 /* Same outputs as ch_reduce + ch_chain + ch_hull; L, lower, upper, counts
- * may each be NULL, in which case the workspace holds them. */
+ * may each be NULL, in which case the workspace holds them.  A small problem
+ * (ch_plan_info form 3) called with lower, upper and counts all NULL runs
+ * as one kernel: its thread blocks fold slices of the points into private
+ * copies of L, and the block that finishes last (a ticket word kept per
+ * stream, zero between calls) merges them and computes the hull, so calls
+ * made on one stream must not overlap (as stream order ensures). */
 int ch_convex_hull(const int32_t *pts, int64_t n, int32_t p, int32_t *L,
                    int32_t *lower, int32_t *upper, int32_t *counts,
                    int32_t *hull, int32_t *hull_count,

@@ -17,6 +17,10 @@ __device__ unsigned g_ch_status[STATUS_SLOTS + 1];
 // ch_sync_status moves a stream's word here (atomic exchange with 0, on that
 // stream) and reads it back with a copy ordered on the same stream.
 __device__ unsigned g_ch_taken[STATUS_SLOTS + 1];
+// Ticket of the single-launch path, one per stream slot: zero between calls
+// (the launch that counts it up resets it), so calls on one stream, which
+// never overlap, never share it.  The shared overflow slot has none.
+__device__ unsigned g_ch_ticket[STATUS_SLOTS];
 
 namespace ch {
 
@@ -25,6 +29,7 @@ constexpr int MAX_DEV = 64;
 std::mutex g_mu;
 unsigned *g_status_base[MAX_DEV] = {};
 unsigned *g_taken_base[MAX_DEV] = {};
+unsigned *g_ticket_base[MAX_DEV] = {};
 std::map<cudaStream_t, int> g_slot_of[MAX_DEV];
 int g_sms[MAX_DEV] = {};
 
@@ -58,12 +63,14 @@ int status_slot(cudaStream_t s, unsigned **word, unsigned **taken)
         return -1;
     std::lock_guard<std::mutex> g(g_mu);
     if (!g_status_base[dev]) {
-        void *a = nullptr, *b = nullptr;
+        void *a = nullptr, *b = nullptr, *c = nullptr;
         if (cudaGetSymbolAddress(&a, g_ch_status) != cudaSuccess ||
-            cudaGetSymbolAddress(&b, g_ch_taken) != cudaSuccess)
+            cudaGetSymbolAddress(&b, g_ch_taken) != cudaSuccess ||
+            cudaGetSymbolAddress(&c, g_ch_ticket) != cudaSuccess)
             return -1;
         g_status_base[dev] = reinterpret_cast<unsigned *>(a);
         g_taken_base[dev] = reinterpret_cast<unsigned *>(b);
+        g_ticket_base[dev] = reinterpret_cast<unsigned *>(c);
     }
     auto &m = g_slot_of[dev];
     auto it = m.find(s);
@@ -89,6 +96,18 @@ unsigned *device_status_ptr(cudaStream_t s)
 {
     unsigned *w = nullptr;
     return status_slot(s, &w, nullptr) < 0 ? nullptr : w;
+}
+
+unsigned *device_ticket_ptr(cudaStream_t s)
+{
+    const int k = status_slot(s, nullptr, nullptr);
+    if (k < 0 || k >= STATUS_SLOTS)
+        return nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return nullptr;
+    std::lock_guard<std::mutex> g(g_mu);
+    return g_ticket_base[dev] + k;
 }
 
 int sm_count()
@@ -134,6 +153,14 @@ int path_layout(int64_t n, int nc, int nr, PathWs *w)
 }
 
 int path_layout(int64_t n, int p, PathWs *w) { return path_layout(n, p, p, w); }
+
+// Workspace of ch_convex_hull: the multi-kernel layout, or the single-launch
+// path's rows and scratch, whichever is larger (the call may take either).
+size_t plain_ws_bytes(const PathWs &w, int64_t n, int p)
+{
+    const int G = small_ctas(n, p);
+    return G > 0 ? std::max(w.end, small_ws_bytes(G, p)) : w.end;
+}
 
 // The frame of a bounding box (xmin, xmax, ymin, ymax): columns along the
 // shorter side; CH_ERR_ARG for an empty box or a side above CH_MAX_P.
@@ -233,6 +260,13 @@ int ch_plan_info(int64_t n, int32_t p, int32_t *form, int32_t *kernels)
     int rc = reduce_plan(n, p, &pl);
     if (rc != CH_OK)
         return rc;
+    if (small_ctas(n, p) > 0) {  // the whole path in one launch
+        if (form)
+            *form = 3;
+        if (kernels)
+            *kernels = 1;
+        return CH_OK;
+    }
     if (form)
         *form = pl.mode;
     if (kernels)  // reduction (+ merge of private copies), chain, (second filter pass), final hull
@@ -339,7 +373,7 @@ int ch_convex_hull_workspace_size(int64_t n, int32_t p, size_t *bytes)
     int rc = path_layout(n, p, &w);
     if (rc != CH_OK)
         return rc;
-    *bytes = w.end;
+    *bytes = plain_ws_bytes(w, n, p);
     return CH_OK;
 }
 
@@ -361,12 +395,22 @@ int convex_hull_square(const int32_t *pts, int64_t n, int32_t p, const Frame &fr
     int rc = path_layout(n, p, &w);
     if (rc != CH_OK)
         return rc;
-    if (ws_bytes < w.end || !workspace)
+    const bool int32_pts = frame_mode(frame) == 0;
+    if (ws_bytes < (int32_pts ? plain_ws_bytes(w, n, p) : w.end) || !workspace)
         return CH_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     unsigned *st = device_status_ptr(s);
     if (!st)
         return CH_ERR_CUDA;
+    // small problems without chain outputs: the whole path in one launch
+    const int G = int32_pts && !lower && !upper && !counts ? small_ctas(n, p) : 0;
+    unsigned *ticket = G > 0 ? device_ticket_ptr(s) : nullptr;
+    if (ticket) {
+        cudaEvent_t ev0, ev1;
+        next_trace(&ev0, &ev1);
+        return cuda_rc(small_launch(pts, n, p, G, workspace, ticket, L, hull, hull_count, st, s,
+                                    ev0, ev1));
+    }
     char *b = reinterpret_cast<char *>(workspace);
     if (!L && w.plan.mode != 0)
         L = reinterpret_cast<int32_t *>(b + w.L);  // the filtered forms write L directly
@@ -906,7 +950,7 @@ int ch_convex_hull_host_workspace_size(int64_t n, int32_t p, size_t *bytes)
     l.take((size_t)n * 8);
     l.take((size_t)p * 16);
     l.take(8);
-    l.take(w.end);
+    l.take(plain_ws_bytes(w, n, p));
     *bytes = l.off;
     return CH_OK;
 }

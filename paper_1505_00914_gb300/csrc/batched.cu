@@ -328,6 +328,73 @@ __global__ void __launch_bounds__(BT)
     }
 }
 
+// ---------------------------------------------------------------- one small set
+// One set in one launch: G CTAs fold consecutive slices of the points into
+// private copies of L in shared memory; with G > 1 each writes its copy as a
+// packed partial row and takes a ticket, and the CTA that takes the last one
+// merges the rows.  That CTA (the only one when G = 1) then finishes the set
+// as the batched kernel does (chains, exact pre-filter, peel/merge/stitch)
+// and resets the ticket for the next call.  L_out (optional) receives L.
+__global__ void __launch_bounds__(BT, 1)
+    k_small(const int32_t *__restrict__ pts, int64_t n, int p, uint32_t *part, unsigned *ticket,
+            unsigned char *scratch, int2 *L_out, int2 *hull, int *hull_count, unsigned *status)
+{
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_total, s_cnt;
+    __shared__ unsigned s_ticket;
+    __shared__ int s_warp[2 * (RUN / 32 + 1)];
+    int *slo = reinterpret_cast<int *>(smem), *shi = slo + p;
+    for (int i = threadIdx.x; i < p; i += BT) {
+        slo[i] = p + 1;
+        shi[i] = -1;
+    }
+    __syncthreads();
+    const int G = gridDim.x;
+    const int64_t per = (((n + G - 1) / G) + 1) & ~(int64_t)1;  // even: slices keep pts' alignment
+    const int64_t a = min(n, (int64_t)blockIdx.x * per), e = min(n, a + per);
+    bool bad = false;
+    fold_range(pts + 2 * a, e - a, p, slo, shi, bad);
+    if (__syncthreads_or(bad) && threadIdx.x == 0)
+        atomicOr(status, ST_RANGE);
+    if (G > 1) {
+        uint32_t *row = part + (size_t)blockIdx.x * p;
+        for (int i = threadIdx.x; i < p; i += BT)
+            __stcg(row + i, slo[i] <= p ? ((uint32_t)(slo[i] - 1) << 16) | (uint32_t)(shi[i] - 1)
+                                        : 0xFFFF0000u);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0)
+            s_ticket = atomicAdd(ticket, 1u);
+        __syncthreads();
+        if (s_ticket != (unsigned)(G - 1))
+            return;  // block-uniform: another CTA finishes the set
+        __threadfence();
+        for (int i = threadIdx.x; i < p; i += BT) {
+            uint32_t lo = 0xFFFFu, hi = 0;
+            for (int r = 0; r < G; ++r) {
+                const uint32_t w = __ldcg(part + (size_t)r * p + i);
+                lo = min(lo, w >> 16);
+                hi = max(hi, w & 0xFFFFu);
+            }
+            slo[i] = lo <= hi ? (int)lo + 1 : p + 1;
+            shi[i] = lo <= hi ? (int)hi + 1 : -1;
+        }
+        if (threadIdx.x == 0)
+            *ticket = 0;  // every CTA of this launch has taken its ticket
+        __syncthreads();
+    }
+    if (L_out)
+        for (int i = threadIdx.x; i < p; i += BT)
+            L_out[i] = make_int2(slo[i], shi[i]);
+    finish_set(p, slo, shi, smem, reinterpret_cast<int2 *>(scratch), hull, hull_count, s_warp,
+               &s_total, &s_cnt);
+}
+
+constexpr int SMALL_PPC = 16384;               // points per CTA of k_small
+constexpr long long SMALL_ROW_WORDS = 1 << 16;  // partial-row words the last CTA merges
+
 struct BatchWs {
     size_t head, items, sets, part, scratch, end;
 };
@@ -380,6 +447,55 @@ void build_plan(int B, const int64_t *off, const int32_t *ps, int chunk_mult,
 }  // namespace
 
 size_t batch_smem() { return BATCH_SMEM; }
+
+int small_ctas(int64_t n, int p)
+{
+    if (n < 0 || p < 1 || p > BATCH_MAX_P)
+        return 0;
+    const long long g = std::max<long long>(1, (n + SMALL_PPC - 1) / SMALL_PPC);
+    const long long gmax = std::max<long long>(1, SMALL_ROW_WORDS / p);
+    const int sms = sm_count();
+    if (sms <= 0 || g > gmax || g > sms)
+        return 0;
+    return (int)g;
+}
+
+size_t small_ws_bytes(int G, int p)
+{
+    WsLayout w;
+    w.take(G > 1 ? (size_t)G * p * sizeof(uint32_t) : 0);
+    w.take(SCR_BYTES);
+    return w.off;
+}
+
+cudaError_t small_launch(const int32_t *pts, int64_t n, int p, int G, void *ws, unsigned *ticket,
+                         int32_t *L_out, int32_t *hull, int32_t *hull_count, unsigned *status,
+                         cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    static bool attr[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return cudaErrorUnknown;
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            k_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BATCH_SMEM);
+        if (e != cudaSuccess)
+            return e;
+        attr[dev] = true;
+    }
+    WsLayout w;
+    char *b = reinterpret_cast<char *>(ws);
+    uint32_t *part = reinterpret_cast<uint32_t *>(
+        b + w.take(G > 1 ? (size_t)G * p * sizeof(uint32_t) : 0));
+    unsigned char *scratch = reinterpret_cast<unsigned char *>(b + w.take(SCR_BYTES));
+    if (ev0)
+        cudaEventRecord(ev0, s);
+    launch(k_small, G, BT, BATCH_SMEM, s, pts, n, p, part, ticket, scratch,
+           reinterpret_cast<int2 *>(L_out), reinterpret_cast<int2 *>(hull), hull_count, status);
+    if (ev1)
+        cudaEventRecord(ev1, s);
+    return cudaGetLastError();
+}
 
 int batch_sizes(int B, const int64_t *off, const int32_t *ps, int chunk_mult, size_t *ws_bytes,
                 BatchPlanInfo *info)

@@ -205,6 +205,15 @@ struct BatchPlanInfo {
     long long part_words;
 };
 size_t batch_smem();
+// One set of n points and side p in one launch (k_small): the number of CTAs
+// it takes, or 0 when the set is too large for that path.
+int small_ctas(int64_t n, int p);
+size_t small_ws_bytes(int G, int p);
+// ticket: a zero word that no other launch uses meanwhile (left zero);
+// L_out optional; ev0/ev1 recorded around the launch when given.
+cudaError_t small_launch(const int32_t *pts, int64_t n, int p, int G, void *ws, unsigned *ticket,
+                         int32_t *L_out, int32_t *hull, int32_t *hull_count, unsigned *status,
+                         cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
 int batch_sizes(int B, const int64_t *off, const int32_t *ps, int chunk_mult, size_t *ws_bytes,
                 BatchPlanInfo *info);
 int batch_prepare(int B, const int64_t *off, const int32_t *ps, int chunk_mult, void *ws,
@@ -303,6 +312,10 @@ cudaError_t rows_launch(const int32_t *L, int p, int32_t *R, unsigned *status, c
 // ---- api.cu ----
 // The status word of stream s on the current device (nullptr on failure).
 unsigned *device_status_ptr(cudaStream_t s);
+// A ticket word of stream s on the current device for the single-launch path
+// (zero between calls), or nullptr (also for the streams beyond the ones with
+// words of their own, whose calls take the multi-kernel path).
+unsigned *device_ticket_ptr(cudaStream_t s);
 int sm_count();
 
 }  // namespace ch
