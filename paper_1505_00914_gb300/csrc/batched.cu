@@ -61,14 +61,16 @@ __device__ __forceinline__ void fold(int *slo, int *shi, uint32_t up, int x, int
     atomicMax(shi + c, y);
 }
 
-// Folds points [0, n) of `base` (8-byte aligned) into slo/shi; whole CTA.
+// Folds points [0, n) of `base` (8-byte aligned) into slo/shi; a group of NT
+// threads (tid: the thread's index in the group), by default the whole CTA.
+template <int NT = BT>
 __device__ void fold_range(const int32_t *__restrict__ base, int64_t n, int p, int *slo, int *shi,
-                           bool &bad)
+                           bool &bad, int tid = threadIdx.x)
 {
     const uint32_t up = (uint32_t)p;
     const int64_t head = (((uintptr_t)base & 15) != 0 && n > 0) ? 1 : 0;
     const int64_t npairs = (n - head) >> 1;
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         if (head)
             fold(slo, shi, up, base[0], base[1], bad);
         if ((n - head) & 1)
@@ -81,19 +83,19 @@ __device__ void fold_range(const int32_t *__restrict__ base, int64_t n, int p, i
     int4 v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        const int64_t j = threadIdx.x + (int64_t)u * BT;
+        const int64_t j = tid + (int64_t)u * NT;
         v[u] = j < npairs ? __ldcs(p4 + j) : make_int4(0, 0, 0, 0);
     }
-    for (int64_t i = threadIdx.x; i < npairs; i += (int64_t)BT * U) {
+    for (int64_t i = tid; i < npairs; i += (int64_t)NT * U) {
         int4 nx[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t j = i + (int64_t)(U + u) * BT;
+            const int64_t j = i + (int64_t)(U + u) * NT;
             nx[u] = j < npairs ? __ldcs(p4 + j) : make_int4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (i + (int64_t)u * BT < npairs) {
+            if (i + (int64_t)u * NT < npairs) {
                 fold(slo, shi, up, v[u].x, v[u].y, bad);
                 fold(slo, shi, up, v[u].z, v[u].w, bad);
             }
@@ -108,12 +110,25 @@ __device__ void fold_range(const int32_t *__restrict__ base, int64_t n, int p, i
 // the peeling rounds remove their non-vertices for less than the trees cost.
 constexpr int SPARSE_TILE = 512;
 
-// Hull of the set whose L is in slo/shi (p columns); whole CTA.
-__device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 *scr,
-                           int2 *hull, int *hull_count, int *s_warp, int *s_total, int *s_cnt)
+// What the tile pre-filter leaves of a set: the survivors at D, the lower
+// chain in D[0..T0) and the mirrored upper chain in D[T0..T).
+struct Survivors {
+    int2 *D;
+    int T0, T;
+    bool in_smem;
+};
+
+// The tile phase of finishing a set (a whole CTA of RUN threads): the valid
+// columns of L (slo/shi, p columns), 1024-column tile by tile, through the
+// exact pre-filter (tiles with more than SPARSE_TILE valid columns) or kept
+// as they are, appended to the per-CTA global lists in scr; then copied
+// compactly to Ds when they fit `cap` points, else to the global scratch
+// behind the lists.  runs: the tile buffers P0, P1 (RUN int2 each) and M0,
+// M1 (2 RUN shorts each), contiguous.
+__device__ Survivors collect_survivors(int p, const int *slo, const int *shi, unsigned char *runs,
+                                       int2 *Ds, int cap, int2 *scr, int *s_warp, int *s_cnt)
 {
-    int2 *A = reinterpret_cast<int2 *>(smem + SM_L);
-    int2 *P0 = reinterpret_cast<int2 *>(smem + SM_L + SM_A);
+    int2 *P0 = reinterpret_cast<int2 *>(runs);
     int2 *P1 = P0 + RUN;
     short *M0 = reinterpret_cast<short *>(P1 + RUN);
     short *M1 = M0 + 2 * RUN;
@@ -165,34 +180,50 @@ __device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 
         }
         __syncthreads();
         build_min_trees(P0, M0, cnt, P1, M1, cnt);
-        const bool k0 = run_keeps<true>(P0, M0, cnt, threadIdx.x);
-        const bool k1 = run_keeps<true>(P1, M1, cnt, threadIdx.x);
+        const bool k0 = run_keeps<true, true>(P0, M0, cnt, threadIdx.x);
+        const bool k1 = run_keeps<true, true>(P1, M1, cnt, threadIdx.x);
         const int2 nk = compact_runs<false>(P0, k0, glo + T0, P1, k1, gup + T1, s_warp);
         T0 += nk.x;
         T1 += nk.y;
     }
     __syncthreads();  // the last tile's survivor lists are copied below by other threads
-    s_warp = s_warp2;
     const int T = T0 + T1;
-    const bool in_smem = T <= BPCAP;
-    int2 *D = in_smem ? A : scr + 2 * BATCH_MAX_P;  // compact: lower then upper
+    const bool in_smem = T <= cap;
+    int2 *D = in_smem ? Ds : scr + 2 * BATCH_MAX_P;  // compact: lower then upper
     for (int k = threadIdx.x; k < T0; k += BT)
         D[k] = __ldcg(glo + k);
     for (int k = threadIdx.x; k < T1; k += BT)
         D[T0 + k] = __ldcg(gup + k);
     __syncthreads();
+    return Survivors{D, T0, T, in_smem};
+}
+
+// Peel scratch in the per-CTA global scratch, for survivors beyond the
+// shared-memory capacity: lists [0, 2P), D [2P, 4P), F, ix (P = BATCH_MAX_P).
+__device__ __forceinline__ void global_peel_scratch(int2 *scr, int2 *&B, int *&F, int *&ix)
+{
+    B = scr;  // the survivor lists were copied to D already
+    F = reinterpret_cast<int *>(scr + 4 * BATCH_MAX_P);
+    ix = F + 2 * BATCH_MAX_P;
+}
+
+// Hull of the set whose L is in slo/shi (p columns); whole CTA.
+__device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 *scr,
+                           int2 *hull, int *hull_count, int *s_warp, int *s_total, int *s_cnt)
+{
+    const Survivors sv = collect_survivors(p, slo, shi, smem + SM_L + SM_A,
+                                           reinterpret_cast<int2 *>(smem + SM_L), BPCAP, scr, s_warp,
+                                           s_cnt);
     int2 *B;
     int *F, *ix;
-    if (in_smem) {  // L is no longer needed: its region holds the peel scratch
+    if (sv.in_smem) {  // L is no longer needed: its region holds the peel scratch
         B = reinterpret_cast<int2 *>(smem);
         F = reinterpret_cast<int *>(B + BPCAP);
         ix = F + BPCAP;
-    } else {  // per-CTA global scratch: lists [0, 2P), D [2P, 4P), F, ix (P = BATCH_MAX_P)
-        B = scr;  // the survivor lists were copied to D already
-        F = reinterpret_cast<int *>(scr + 4 * BATCH_MAX_P);
-        ix = F + 2 * BATCH_MAX_P;
+    } else {
+        global_peel_scratch(scr, B, F, ix);
     }
-    peel_merge_stitch(D, B, F, ix, T0, T, hull, hull_count, s_warp, s_total);
+    peel_merge_stitch<FT, 0, true>(sv.D, B, F, ix, sv.T0, sv.T, hull, hull_count, s_warp, s_total);
 }
 
 // WRITE_L: instead of finishing a set, write its L (Algorithm 1's array,

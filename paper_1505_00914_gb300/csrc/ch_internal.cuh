@@ -29,6 +29,20 @@ __device__ __forceinline__ long long cross3(int2 o, int2 a, int2 b)
            (long long)(a.y - o.y) * (long long)(b.x - o.x);
 }
 
+// The same orientation in 32-bit arithmetic (NARROW = true), exact when
+// every coordinate difference is below 2^14 in magnitude, so that each
+// product is below 2^28: the batched and single-launch kernels take sets of
+// side p <= 16384, whose chain points differ by at most p - 1 in x and in y
+// (lower chains (x, y), upper chains mirrored to (x, -y), never mixed).
+template <bool NARROW>
+__device__ __forceinline__ long long orient(int2 o, int2 a, int2 b)
+{
+    if constexpr (NARROW)
+        return (long long)((a.x - o.x) * (b.y - o.y) - (a.y - o.y) * (b.x - o.x));
+    else
+        return cross3(o, a, b);
+}
+
 // Launch with programmatic dependent launch allowed: the grid may be
 // scheduled while the previous kernel of the stream finishes, which hides the
 // launch latency between the dependent kernels of the path.  Every kernel

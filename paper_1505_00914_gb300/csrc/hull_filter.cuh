@@ -76,7 +76,8 @@ __device__ __forceinline__ void build_min_trees(const int2 *P0, short *M0, int n
 // short-lived: a warp stops testing once all its points are dropped, and the
 // lowest level (blocks of two points, next to the +-2 neighbour tests) is
 // left out; the chain kernel's dense tiles are faster without the vote.
-template <bool SPARSE_EXIT = false>
+// NARROW: 32-bit orientation tests (see orient; chain points of p <= 16384).
+template <bool SPARSE_EXIT = false, bool NARROW = false>
 __device__ __forceinline__ bool run_keeps(const int2 *P, const short *M, int n, int i)
 {
     const bool alive = i < n;
@@ -84,8 +85,9 @@ __device__ __forceinline__ bool run_keeps(const int2 *P, const short *M, int n, 
     const bool h1 = alive && i >= 1 && i + 1 < n, l2 = i >= 2, r2 = i + 2 < n;
     const int2 nl1 = alive && i >= 1 ? P[i - 1] : q, nr1 = alive && i + 1 < n ? P[i + 1] : q;
     const int2 nl2 = alive && l2 ? P[i - 2] : q, nr2 = alive && r2 ? P[i + 2] : q;
-    bool drop = !alive || (h1 && (cross3(nl1, nr1, q) >= 0 || (r2 && cross3(nl1, nr2, q) >= 0) ||
-                                  (l2 && cross3(nl2, nr1, q) >= 0)));
+    bool drop = !alive || (h1 && (orient<NARROW>(nl1, nr1, q) >= 0 ||
+                                  (r2 && orient<NARROW>(nl1, nr2, q) >= 0) ||
+                                  (l2 && orient<NARROW>(nl2, nr1, q) >= 0)));
     constexpr int CH = 3;  // levels per batch; levels 1..RUN_LOG-1 have siblings
 #pragma unroll
     for (int k0 = SPARSE_EXIT ? 2 : 1; k0 < RUN_LOG; k0 += CH) {
@@ -106,7 +108,7 @@ __device__ __forceinline__ bool run_keeps(const int2 *P, const short *M, int n, 
         }
 #pragma unroll
         for (int u = 0; u < CH; ++u)
-            drop |= la[u] >= 0 && ra[u] >= 0 && cross3(A[u], B[u], q) >= 0;
+            drop |= la[u] >= 0 && ra[u] >= 0 && orient<NARROW>(A[u], B[u], q) >= 0;
     }
     return !drop;
 }

@@ -13,6 +13,17 @@ constexpr int SMALL = 32;     // pairs with na + nb <= SMALL merge on one thread
 constexpr int FT = 1024;      // threads of a CTA running the final steps
 constexpr int PEEL_MAX = 24;  // peeling rounds before the merge fallback
 
+// Barrier of a group of NT threads (whole warps): the whole CTA when BAR is
+// 0, else the named barrier BAR, which exactly those NT threads use.
+template <int BAR, int NT>
+__device__ __forceinline__ void group_sync()
+{
+    if constexpr (BAR == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
+}
+
 // Index of the tangent point from a (left of every point of B) to the lower
 // hull B: the vertex of least slope, the farthest one on ties.
 __device__ __forceinline__ int tangent(const int2 *B, int nb, int2 a)
@@ -81,11 +92,12 @@ __device__ int thread_merge(int2 *D, int a, int na, int b, int nb)
     return top;
 }
 
-// In-place exclusive scan of a[0..n) by the whole CTA; returns the total.
-template <int NT>
-__device__ int block_excl_scan(int *a, int n, int *s_warp, int *s_total)
+// In-place exclusive scan of a[0..n) by a group of NT threads (t = the
+// thread's index in the group, BAR its barrier); returns the total.
+template <int NT, int BAR = 0>
+__device__ int block_excl_scan(int *a, int n, int *s_warp, int *s_total, int t = threadIdx.x)
 {
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int lane = t & 31, w = t >> 5;
     const int per = (n + NT - 1) / NT;
     const int b = min(n, t * per), e = min(n, b + per);
     int sum = 0;
@@ -100,7 +112,7 @@ __device__ int block_excl_scan(int *a, int n, int *s_warp, int *s_total)
     }
     if (lane == 31)
         s_warp[w] = incl;
-    __syncthreads();
+    group_sync<BAR, NT>();
     if (w == 0) {
         const int v = lane < NT / 32 ? s_warp[lane] : 0;
         int inc = v;
@@ -115,7 +127,7 @@ __device__ int block_excl_scan(int *a, int n, int *s_warp, int *s_total)
         if (lane == 31)
             *s_total = inc;
     }
-    __syncthreads();
+    group_sync<BAR, NT>();
     int run = s_warp[w] + incl - sum;
     for (int i = b; i < e; ++i) {
         const int v = a[i];
@@ -123,7 +135,7 @@ __device__ int block_excl_scan(int *a, int n, int *s_warp, int *s_total)
         run += v;
     }
     const int total = *s_total;
-    __syncthreads();
+    group_sync<BAR, NT>();
     return total;
 }
 
@@ -137,14 +149,14 @@ struct Tree {
     int c0, c1;
 };
 
-template <int NT>
-__device__ void merge_tree(Tree &t)
+template <int NT, int BAR = 0>
+__device__ void merge_tree(Tree &t, int tid = threadIdx.x)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = tid & 31, warp = tid >> 5;
     while (t.c0 > 1 || t.c1 > 1) {
         const int d0 = (t.c0 + 1) >> 1, d1 = (t.c1 + 1) >> 1, nd = d0 + d1;
         // small pairs and carries: one thread each
-        for (int j = threadIdx.x; j < nd; j += NT) {
+        for (int j = tid; j < nd; j += NT) {
             const int chain = j >= d0;
             const int jj = j - (chain ? d0 : 0);
             const int cc = chain ? t.c1 : t.c0;
@@ -187,7 +199,7 @@ __device__ void merge_tree(Tree &t)
                 t.L2[j] = u + 1 + cnt;
             }
         }
-        __syncthreads();
+        group_sync<BAR, NT>();
         int *x = t.S;
         t.S = t.S2;
         t.S2 = x;
@@ -203,22 +215,23 @@ __device__ void merge_tree(Tree &t)
 // segment between two of its neighbours: any of the pairs at most two places
 // away, or the pairs three and four places away on both sides (those end a
 // long concave run in fewer rounds).
+template <bool NARROW = false>
 __device__ __forceinline__ bool peel_drops(const int2 *D, int cs, int ce, int i)
 {
     if (i - 1 < cs || i + 1 >= ce)
         return false;
     const int2 q = D[i], l1 = D[i - 1], r1 = D[i + 1];
-    if (cross3(l1, r1, q) >= 0)
+    if (orient<NARROW>(l1, r1, q) >= 0)
         return true;
     const bool l2 = i - 2 >= cs, r2 = i + 2 < ce;
     const int2 a2 = l2 ? D[i - 2] : l1, b2 = r2 ? D[i + 2] : r1;
-    if ((r2 && cross3(l1, b2, q) >= 0) || (l2 && cross3(a2, r1, q) >= 0) ||
-        (l2 && r2 && cross3(a2, b2, q) >= 0))
+    if ((r2 && orient<NARROW>(l1, b2, q) >= 0) || (l2 && orient<NARROW>(a2, r1, q) >= 0) ||
+        (l2 && r2 && orient<NARROW>(a2, b2, q) >= 0))
         return true;
     const bool l3 = i - 3 >= cs, r3 = i + 3 < ce, l4 = i - 4 >= cs, r4 = i + 4 < ce;
     const int2 a3 = l3 ? D[i - 3] : a2, b3 = r3 ? D[i + 3] : b2;
     const int2 a4 = l4 ? D[i - 4] : a3, b4 = r4 ? D[i + 4] : b3;
-    return (l3 && r3 && cross3(a3, b3, q) >= 0) || (l4 && r4 && cross3(a4, b4, q) >= 0);
+    return (l3 && r3 && orient<NARROW>(a3, b3, q) >= 0) || (l4 && r4 && orient<NARROW>(a4, b4, q) >= 0);
 }
 
 // Peel, merge fallback and stitch, run by a whole CTA of FT threads.  A holds
@@ -231,21 +244,26 @@ __device__ __forceinline__ bool peel_drops(const int2 *D, int cs, int ce, int i)
 // the rest goes through runs of HS points and the pairwise merge tree.  The
 // stitched hull (counter-clockwise from the lexicographic minimum) goes to
 // hull[0..*hull_count).
+// NT, BAR, tid: run by a group of NT threads (whole warps) with its own
+// barrier BAR instead of the whole CTA; tid is the thread's index in the
+// group and s_warp holds NT / 32 + 1 ints of the group's own.
+template <int NT = FT, int BAR = 0, bool NARROW = false>
 __device__ void peel_merge_stitch(int2 *A, int2 *B, int *F, int *ix, int T0, int T, int2 *hull,
-                                  int *hull_count, int *s_warp, int *s_total)
+                                  int *hull_count, int *s_warp, int *s_total, int tid = threadIdx.x)
 {
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
+    const int t = tid, lane = t & 31, w = t >> 5;
     bool done = false;
     for (int round = 0; round < PEEL_MAX && !done; ++round) {
-        if (T <= FT) {  // one point per thread: a ballot scan, three block barriers
+        if (T <= NT) {  // one point per thread: a ballot scan, three block barriers
             const bool c1 = t >= T0;
-            const bool keep = t < T && !peel_drops(A, c1 ? T0 : 0, c1 ? T : T0, t);
+            const bool keep = t < T && !peel_drops<NARROW>(A, c1 ? T0 : 0, c1 ? T : T0, t);
             const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
             if (lane == 0)
                 s_warp[w] = __popc(bal);
-            __syncthreads();
+            group_sync<BAR, NT>();
             if (w == 0) {
-                const int v = s_warp[lane];
+                const int v = lane < NT / 32 ? s_warp[lane] : 0;
                 int incl = v;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -253,11 +271,12 @@ __device__ void peel_merge_stitch(int2 *A, int2 *B, int *F, int *ix, int T0, int
                     if (lane >= o)
                         incl += x;
                 }
-                s_warp[lane] = incl - v;
+                if (lane < NT / 32)
+                    s_warp[lane] = incl - v;
                 if (lane == 31)
                     *s_total = incl;
             }
-            __syncthreads();
+            group_sync<BAR, NT>();
             const int kept = *s_total;
             if (kept == T) {
                 done = true;  // block-uniform
@@ -268,7 +287,7 @@ __device__ void peel_merge_stitch(int2 *A, int2 *B, int *F, int *ix, int T0, int
                 B[pos] = A[t];
             if (t == T0 && T0 < T)
                 F[0] = pos;  // points kept before the upper chain
-            __syncthreads();
+            group_sync<BAR, NT>();
             T0 = T0 < T ? F[0] : kept;
             T = kept;
             int2 *x = A;
@@ -276,23 +295,23 @@ __device__ void peel_merge_stitch(int2 *A, int2 *B, int *F, int *ix, int T0, int
             B = x;
             continue;
         }
-        for (int i = t; i < T; i += FT) {
+        for (int i = t; i < T; i += NT) {
             const bool c1 = i >= T0;
-            F[i] = peel_drops(A, c1 ? T0 : 0, c1 ? T : T0, i) ? 0 : 1;
+            F[i] = peel_drops<NARROW>(A, c1 ? T0 : 0, c1 ? T : T0, i) ? 0 : 1;
         }
-        __syncthreads();
-        const int kept = block_excl_scan<FT>(F, T, s_warp, s_total);
+        group_sync<BAR, NT>();
+        const int kept = block_excl_scan<NT, BAR>(F, T, s_warp, s_total, t);
         if (kept == T) {
             done = true;  // block-uniform
             break;
         }
-        for (int i = t; i < T; i += FT) {
+        for (int i = t; i < T; i += NT) {
             const int next = i + 1 < T ? F[i + 1] : kept;
             if (next != F[i])
                 B[F[i]] = A[i];
         }
         const int nT0 = T0 < T ? F[T0] : kept;
-        __syncthreads();
+        group_sync<BAR, NT>();
         int2 *x = A;
         A = B;
         B = x;
@@ -311,7 +330,7 @@ __device__ void peel_merge_stitch(int2 *A, int2 *B, int *F, int *ix, int T0, int
         // fallback: Andrew's scan over runs of HS points, then the merge tree
         const int T1 = T - T0;
         const int r0 = (T0 + HS - 1) / HS, r1 = (T1 + HS - 1) / HS, nr = r0 + r1;
-        for (int r = t; r < nr; r += FT) {
+        for (int r = t; r < nr; r += NT) {
             const bool c1 = r >= r0;
             const int st = c1 ? T0 + (r - r0) * HS : r * HS;
             const int cnt = min(HS, (c1 ? T : T0) - st);
@@ -319,7 +338,7 @@ __device__ void peel_merge_stitch(int2 *A, int2 *B, int *F, int *ix, int T0, int
             int2 a0 = make_int2(0, 0), a1 = make_int2(0, 0);
             for (int i = 0; i < cnt; ++i) {
                 const int2 q = A[st + i];
-                while (top >= 2 && cross3(a0, a1, q) <= 0) {
+                while (top >= 2 && orient<NARROW>(a0, a1, q) <= 0) {
                     --top;
                     a1 = a0;
                     if (top >= 2)
@@ -333,7 +352,7 @@ __device__ void peel_merge_stitch(int2 *A, int2 *B, int *F, int *ix, int T0, int
             ix[r] = st;
             ix[nr + r] = top;
         }
-        __syncthreads();
+        group_sync<BAR, NT>();
         Tree tr;
         tr.D = A;
         tr.S = ix;
@@ -342,7 +361,7 @@ __device__ void peel_merge_stitch(int2 *A, int2 *B, int *F, int *ix, int T0, int
         tr.L2 = ix + 3 * nr;
         tr.c0 = r0;
         tr.c1 = r1;
-        merge_tree<FT>(tr);
+        merge_tree<NT, BAR>(tr, t);
         hl = tr.c0 ? tr.L[0] : 0;
         hu = tr.c1 ? tr.L[tr.c0] : 0;
         LH = A + (tr.c0 ? tr.S[0] : 0);
@@ -361,15 +380,15 @@ __device__ void peel_merge_stitch(int2 *A, int2 *B, int *F, int *ix, int T0, int
             kf = 1;
     }
     const int nup = max(0, kl - kf + 1);
-    for (int k = t; k < hl; k += FT)
+    for (int k = t; k < hl; k += NT)
         hull[k] = LH[k];
-    for (int k = t; k < nup; k += FT) {
+    for (int k = t; k < nup; k += NT) {
         const int2 q = UH[kl - k];
         hull[hl + k] = make_int2(q.x, -q.y);
     }
     if (t == 0)
         *hull_count = hl + nup;
-    __syncthreads();
+    group_sync<BAR, NT>();
 }
 
 
