@@ -54,7 +54,7 @@ Other workloads (--workload):
             all three hulls agree.
   batched   10,000 sets, n log-uniform in [1e2, 1e6], p from {256, 1024,
             4096, 16384}, uniform/disc/Gaussian by seeded choice, in one
-            ragged buffer: ch_hull_batched (autotuned chunk size, replayed
+            ragged buffer: ch_hull_batched (autotuned chunk size and CTA shape, replayed
             from a captured CUDA graph) against one ch_convex_hull per set.
 """
 from __future__ import annotations
@@ -891,11 +891,11 @@ def run_batched(args):
     hull = torch.zeros((int(hoff[-1]), 2), dtype=torch.int32, device="cuda")
     cnt = torch.zeros(B, dtype=torch.int32, device="cuda")
     if args.no_aux:  # profiling runs: the usual choice, no tuning launches
-        best, tune_ms = 1024, {}
+        (best, fold), tune_ms = (1024, ch.CH_BATCH_FOLD_DEFAULT), {}
     else:
-        best, tune_ms = autotune.tune_batched(d_pts, off, ps, d_off, d_ps, hull, d_hoff, cnt)
+        (best, fold), tune_ms = autotune.tune_batched(d_pts, off, ps, d_off, d_ps, hull, d_hoff, cnt)
     ws = torch.empty(ch.ch_batched_workspace_size(off, ps, best), dtype=torch.uint8, device="cuda")
-    ch.ch_batched_prepare(off, ps, ws, best)
+    ch.ch_batched_prepare(off, ps, ws, best, fold_threads=fold)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         ch.ch_hull_batched(d_pts, d_off, d_ps, hull, d_hoff, cnt, ws)  # first call: set-up
@@ -987,7 +987,7 @@ def run_batched(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": workload_config(args.workload),
-        "batched": {"points": n_tot, "chunk_mult": best,
+        "batched": {"points": n_tot, "chunk_mult": best, "fold_threads": fold,
                     "launch": "one captured CUDA graph replay per step",
                     "per_set_plain_gpoints_s": world * n_tot / (ms_plain / 1e3) / 1e9,
                     "per_set_plain_ms": ms_plain, "speedup_vs_per_set": ms_plain / (ms / args.steps),

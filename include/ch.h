@@ -98,7 +98,7 @@ int ch_trace_set(void *const *events, int npairs);
  * when it is not asked for the chains (lower, upper and counts NULL):
  * *form = 0 (private shared-memory copies of L, p <= 29056), 1 (filtered
  * global L, p <= 116224), 2 (global L with a read-then-atomic test) or 3
- * (small problems: p <= 16384, at most 16384 points per thread block and
+ * (small problems: p <= 16384, at most 8192 points per thread block and
  * the blocks' partial copies of L at most 65536 words in all, the whole path
  * in one launch), and *kernels = the number of kernels one ch_convex_hull
  * call launches (with the second filter pass of the hull step from 128 runs
@@ -312,6 +312,22 @@ int ch_batched_workspace_size(int32_t B, const int64_t *host_offsets, const int3
  * a CUDA graph); prepare again after a change of sizes. */
 int ch_batched_prepare(int32_t B, const int64_t *host_offsets, const int32_t *host_ps,
                        int32_t chunk_mult, void *workspace, size_t ws_bytes, ch_stream_t stream);
+
+/* The CTA shape of ch_hull_batched's persistent kernel (1024 threads):
+ * fold_threads = 0 has every thread fold a set's points and then finish it
+ * (chains, exact pre-filter, peel/merge/stitch); 512, 768 or 896 splits the
+ * CTA: that many threads fold the next set's points while the other 512, 256
+ * or 128 threads peel, merge and stitch the previous set (the pre-filter,
+ * which reads the set's L in shared memory, is run by all of them).  The
+ * hulls are the same for every shape. */
+#define CH_BATCH_FOLD_DEFAULT 512
+
+/* ch_batched_prepare with the CTA shape (fold_threads: 0, 512, 768 or 896;
+ * anything else is CH_ERR_ARG).  ch_batched_prepare uses
+ * CH_BATCH_FOLD_DEFAULT; the autotuner times the others. */
+int ch_batched_prepare_shape(int32_t B, const int64_t *host_offsets, const int32_t *host_ps,
+                             int32_t chunk_mult, int32_t fold_threads, void *workspace,
+                             size_t ws_bytes, ch_stream_t stream);
 
 /* Hulls of the B sets of the prepared plan in one launch.  pts: the device
  * point array; offsets, ps: device copies of the sizes the plan was built

@@ -48,6 +48,7 @@ def _declare(lib):
         "ch_plan_info": (ctypes.c_int, [i64, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "ch_batched_workspace_size": (ctypes.c_int, [i32, P, P, i32, szp]),
         "ch_batched_prepare": (ctypes.c_int, [i32, P, P, i32, P, sz, P]),
+        "ch_batched_prepare_shape": (ctypes.c_int, [i32, P, P, i32, i32, P, sz, P]),
         "ch_hull_batched": (ctypes.c_int, [P, P, P, i32, P, P, P, P, sz, P]),
         "ch_reduce_batched": (ctypes.c_int, [P, P, P, i32, P, P, P, sz, P]),
         "ch_chain_batched": (ctypes.c_int, [P, P, P, i32, P, P, P, P]),
@@ -535,13 +536,27 @@ def ch_batched_workspace_size(offsets, ps, chunk_mult: int = 64) -> int:
     return int(out.value)
 
 
-def ch_batched_prepare(offsets, ps, workspace, chunk_mult: int = 64, stream=None):
-    """Plan the batch (host arrays offsets (B+1,), ps (B,)) into `workspace`."""
+CH_BATCH_FOLD_DEFAULT = 512  # the header's #define of the same name
+CH_BATCH_FOLD_SHAPES = (0, 512, 768, 896)
+
+
+def ch_batched_prepare(offsets, ps, workspace, chunk_mult: int = 64, stream=None,
+                       fold_threads: int | None = None):
+    """Plan the batch (host arrays offsets (B+1,), ps (B,)) into `workspace`;
+    fold_threads (None: the library's default) picks the CTA shape, see
+    ch_batched_prepare_shape in include/ch.h."""
     off, pp = _host_sizes(offsets, ps)
-    _check(lib().ch_batched_prepare(pp.shape[0], off.ctypes.data_as(ctypes.c_void_p),
-                                    pp.ctypes.data_as(ctypes.c_void_p), int(chunk_mult),
-                                    _ptr(workspace), workspace.numel(), _stream(stream)),
-           "ch_batched_prepare")
+    if fold_threads is None:
+        _check(lib().ch_batched_prepare(pp.shape[0], off.ctypes.data_as(ctypes.c_void_p),
+                                        pp.ctypes.data_as(ctypes.c_void_p), int(chunk_mult),
+                                        _ptr(workspace), workspace.numel(), _stream(stream)),
+               "ch_batched_prepare")
+    else:
+        _check(lib().ch_batched_prepare_shape(pp.shape[0], off.ctypes.data_as(ctypes.c_void_p),
+                                              pp.ctypes.data_as(ctypes.c_void_p), int(chunk_mult),
+                                              int(fold_threads), _ptr(workspace),
+                                              workspace.numel(), _stream(stream)),
+               "ch_batched_prepare_shape")
 
 
 def ch_hull_batched(pts, offsets, ps, hull_out, hull_offsets, hull_counts, workspace,

@@ -525,12 +525,15 @@ int ch_batched_workspace_size(int32_t B, const int64_t *host_offsets, const int3
     return batch_sizes(B, host_offsets, host_ps, chunk_mult, bytes, nullptr);
 }
 
-int ch_batched_prepare(int32_t B, const int64_t *host_offsets, const int32_t *host_ps,
-                       int32_t chunk_mult, void *workspace, size_t ws_bytes, ch_stream_t stream)
+int ch_batched_prepare_shape(int32_t B, const int64_t *host_offsets, const int32_t *host_ps,
+                             int32_t chunk_mult, int32_t fold_threads, void *workspace,
+                             size_t ws_bytes, ch_stream_t stream)
 {
     int rc = check_batch(B, host_offsets, host_ps, chunk_mult);
     if (rc != CH_OK)
         return rc;
+    if (!batch_fold_ok(fold_threads))
+        return CH_ERR_ARG;
     if (!workspace)
         return CH_ERR_WORKSPACE;
     BatchPlanInfo info;
@@ -538,9 +541,17 @@ int ch_batched_prepare(int32_t B, const int64_t *host_offsets, const int32_t *ho
                        reinterpret_cast<cudaStream_t>(stream), &info);
     if (rc != CH_OK)
         return rc;
+    info.fold = fold_threads;
     std::lock_guard<std::mutex> g(g_batch_mu);
     g_batch_plans[workspace] = info;
     return CH_OK;
+}
+
+int ch_batched_prepare(int32_t B, const int64_t *host_offsets, const int32_t *host_ps,
+                       int32_t chunk_mult, void *workspace, size_t ws_bytes, ch_stream_t stream)
+{
+    return ch_batched_prepare_shape(B, host_offsets, host_ps, chunk_mult, CH_BATCH_FOLD_DEFAULT,
+                                    workspace, ws_bytes, stream);
 }
 
 int ch_hull_batched(const int32_t *pts, const int64_t *offsets, const int32_t *ps, int32_t B,

@@ -217,7 +217,10 @@ constexpr int BATCH_MAX_P = 16384;  // largest p of a set in a batch
 struct BatchPlanInfo {
     int B, nitems, grid;
     long long part_words;
+    int fold;  // threads of a CTA that fold while the others finish (0: the whole CTA does both)
 };
+// The CTA splits the batched hull kernel is built for (threads that fold).
+inline bool batch_fold_ok(int fold) { return fold == 0 || fold == 512 || fold == 768 || fold == 896; }
 size_t batch_smem();
 // One set of n points and side p in one launch (k_small): the number of CTAs
 // it takes, or 0 when the set is too large for that path.

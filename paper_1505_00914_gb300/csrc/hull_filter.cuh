@@ -23,14 +23,28 @@ constexpr int RUN_LOG = 10;
 // tree_off(k); 2 * RUN shorts hold every level.
 __device__ __forceinline__ int tree_off(int k) { return 2 * RUN - ((2 * RUN) >> (k - 1)); }
 
-// Builds the min-y index trees of two runs, P0[0..n0) and P1[0..n1), level by
-// level; every thread of the CTA calls it.  Levels 5 and up have at most 32
-// nodes and read only nodes that warp 0 wrote, so warp 0 builds them alone
-// with warp barriers between levels.
-__device__ __forceinline__ void build_min_trees(const int2 *P0, short *M0, int n0, const int2 *P1,
-                                                short *M1, int n1)
+// Barrier of a group of NT threads (whole warps): the whole CTA when BAR is
+// 0, else the named barrier BAR, which exactly those NT threads use.
+template <int BAR, int NT>
+__device__ __forceinline__ void group_sync()
 {
-    const int i = threadIdx.x;
+    if constexpr (BAR == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
+}
+
+// Builds the min-y index trees of two runs, P0[0..n0) and P1[0..n1), level by
+// level; every thread of the CTA calls it (or, with NT and BAR, every thread
+// of a group of NT >= RUN / 2 threads with barrier BAR, tid its index in the
+// group).  Levels 5 and up have at most 32 nodes and read only nodes that
+// warp 0 wrote, so warp 0 builds them alone with warp barriers between levels.
+template <int NT = RUN, int BAR = 0>
+__device__ __forceinline__ void build_min_trees(const int2 *P0, short *M0, int n0, const int2 *P1,
+                                                short *M1, int n1, int tid = threadIdx.x)
+{
+    static_assert(NT >= RUN / 2, "one thread per node of the lowest level");
+    const int i = tid;
     auto level = [&](int k) {
         if (i < (RUN >> k)) {
             int a0, b0, a1, b1;
@@ -55,7 +69,7 @@ __device__ __forceinline__ void build_min_trees(const int2 *P0, short *M0, int n
     static_assert((RUN >> WARP_LEVEL) == 32, "levels from WARP_LEVEL on fit one warp");
     for (int k = 1; k < WARP_LEVEL; ++k) {
         level(k);
-        __syncthreads();
+        group_sync<BAR, NT>();
     }
     if (i < 32) {
         for (int k = WARP_LEVEL; k <= RUN_LOG; ++k) {
@@ -63,7 +77,7 @@ __device__ __forceinline__ void build_min_trees(const int2 *P0, short *M0, int n
             __syncwarp();
         }
     }
-    __syncthreads();
+    group_sync<BAR, NT>();
 }
 
 // True when point i of P[0..n) may be a strict lower-hull vertex.  The anchor

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "ch_internal.cuh"
+#include "hull_filter.cuh"
 
 namespace ch {
 namespace {
@@ -13,16 +14,6 @@ constexpr int SMALL = 32;     // pairs with na + nb <= SMALL merge on one thread
 constexpr int FT = 1024;      // threads of a CTA running the final steps
 constexpr int PEEL_MAX = 24;  // peeling rounds before the merge fallback
 
-// Barrier of a group of NT threads (whole warps): the whole CTA when BAR is
-// 0, else the named barrier BAR, which exactly those NT threads use.
-template <int BAR, int NT>
-__device__ __forceinline__ void group_sync()
-{
-    if constexpr (BAR == 0)
-        __syncthreads();
-    else
-        asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
-}
 
 // Index of the tangent point from a (left of every point of B) to the lower
 // hull B: the vertex of least slope, the farthest one on ties.

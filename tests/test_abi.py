@@ -146,7 +146,7 @@ def test_python_constants_match_the_header():
 
     names = ["CH_CHAIN_NOALLOC_MAX_P", "CH_OK", "CH_ERR_ARG", "CH_ERR_RANGE", "CH_ERR_CAPACITY",
              "CH_ERR_TIMEOUT", "CH_ERR_CUDA", "CH_ERR_WORKSPACE", "CH_MLP_IN", "CH_MLP_HID",
-             "CH_MLP_K", "CH_MLP_PARAMS"]
+             "CH_MLP_K", "CH_MLP_PARAMS", "CH_BATCH_FOLD_DEFAULT"]
     for n in names:
         if hasattr(ch, n):
             assert getattr(ch, n) == value(defs[n]), n

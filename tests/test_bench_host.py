@@ -85,7 +85,8 @@ def test_bench_reads_no_undefined_global():
 
 def test_autotune_cache_key_and_lookup(tmp_path, monkeypatch):
     """The tuning cache is keyed by the batch's shape, the candidate chunk
-    sizes and the kernel source; a cached batch is answered without a launch."""
+    sizes and CTA shapes and the kernel source; a cached batch is answered
+    without a launch."""
     from paper_1505_00914_gb300 import autotune
     monkeypatch.setenv("CH_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     off, ps = np.asarray([0, 10, 30]), np.asarray([16, 256], np.int32)
@@ -94,9 +95,11 @@ def test_autotune_cache_key_and_lookup(tmp_path, monkeypatch):
     assert k != autotune.batch_key(np.asarray([0, 11, 30]), ps)
     assert k != autotune.batch_key(off, np.asarray([16, 1024], np.int32))
     assert k != autotune.batch_key(off, ps, candidates=(8, 16))
-    autotune._store({k: {"chunk_mult": 256, "ms": {"8": 2.0, "256": 1.5}}})
+    assert k != autotune.batch_key(off, ps, shapes=(0, 768))
+    autotune._store({k: {"chunk_mult": 256, "fold_threads": 768,
+                         "ms": {"8/0": 2.0, "256/768": 1.5}}})
     best, times = autotune.tune_batched(None, off, ps, None, None, None, None, None)
-    assert best == 256 and times == {8: 2.0, 256: 1.5}
+    assert best == (256, 768) and times == {"8/0": 2.0, "256/768": 1.5}
 
 
 def test_clock_summary_from_nvidia_smi_rows():

@@ -18,7 +18,7 @@ def _gpu():
     assert ch.ch_sync_status() == ch.CH_OK
 
 
-def run_batch(pts, offsets, ps, chunk_mult=64):
+def run_batch(pts, offsets, ps, chunk_mult=64, fold=None):
     d_pts = torch.from_numpy(np.ascontiguousarray(pts, dtype=np.int32).reshape(-1, 2)).cuda()
     d_off = torch.from_numpy(np.asarray(offsets, np.int64)).cuda()
     d_ps = torch.from_numpy(np.asarray(ps, np.int32)).cuda()
@@ -28,7 +28,7 @@ def run_batch(pts, offsets, ps, chunk_mult=64):
     cnt = torch.full((len(ps),), -7, dtype=torch.int32, device="cuda")
     nws = ch.ch_batched_workspace_size(offsets, ps, chunk_mult)
     ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
-    ch.ch_batched_prepare(offsets, ps, ws, chunk_mult)
+    ch.ch_batched_prepare(offsets, ps, ws, chunk_mult, fold_threads=fold)
     ch.ch_hull_batched(d_pts, d_off, d_ps, hull, d_hoff, cnt, ws)
     torch.cuda.synchronize()
     return hull.cpu().numpy(), hoff, cnt.cpu().numpy()
@@ -54,8 +54,9 @@ def test_mixed_small_batch():
     offsets = np.zeros(B + 1, np.int64)
     np.cumsum(ns, out=offsets[1:])
     pts = np.concatenate(parts) if parts else np.zeros((0, 2), np.int32)
-    hull, hoff, cnt = run_batch(pts, offsets, ps)
-    check_sets(pts, offsets, ps, hull, hoff, cnt)
+    for fold in ch.CH_BATCH_FOLD_SHAPES:
+        hull, hoff, cnt = run_batch(pts, offsets, ps, fold=fold)
+        check_sets(pts, offsets, ps, hull, hoff, cnt)
 
 
 def test_multi_chunk_sets_merge():
@@ -69,8 +70,9 @@ def test_multi_chunk_sets_merge():
     np.cumsum(ns, out=offsets[1:])
     pts = np.concatenate(parts)
     for cm in (1, 3, 64):
-        hull, hoff, cnt = run_batch(pts, offsets, ps, chunk_mult=cm)
-        check_sets(pts, offsets, ps, hull, hoff, cnt)
+        for fold in ch.CH_BATCH_FOLD_SHAPES:
+            hull, hoff, cnt = run_batch(pts, offsets, ps, chunk_mult=cm, fold=fold)
+            check_sets(pts, offsets, ps, hull, hoff, cnt)
 
 
 def test_misaligned_set_starts_and_degenerate_sets():
@@ -82,8 +84,9 @@ def test_misaligned_set_starts_and_degenerate_sets():
     offsets = np.zeros(len(sets) + 1, np.int64)
     np.cumsum([s.shape[0] for s in sets], out=offsets[1:])
     pts = np.concatenate(sets)
-    hull, hoff, cnt = run_batch(pts, offsets, ps)
-    check_sets(pts, offsets, ps, hull, hoff, cnt)
+    for fold in ch.CH_BATCH_FOLD_SHAPES:
+        hull, hoff, cnt = run_batch(pts, offsets, ps, fold=fold)
+        check_sets(pts, offsets, ps, hull, hoff, cnt)
 
 
 def test_batched_range_error_and_arguments():
@@ -147,8 +150,9 @@ def test_culling_polygon_shapes():
     np.cumsum([s.shape[0] for s in sets], out=offsets[1:])
     pts = np.concatenate(sets)
     for cm in (1, 64):
-        hull, hoff, cnt = run_batch(pts, offsets, ps, chunk_mult=cm)
-        check_sets(pts, offsets, ps, hull, hoff, cnt)
+        for fold in ch.CH_BATCH_FOLD_SHAPES:
+            hull, hoff, cnt = run_batch(pts, offsets, ps, chunk_mult=cm, fold=fold)
+            check_sets(pts, offsets, ps, hull, hoff, cnt)
 
 
 def _device_batch(pts, offsets, ps):
@@ -162,7 +166,7 @@ def _device_batch(pts, offsets, ps):
     return d_pts, d_off, d_ps, hoff, d_hoff, hull, cnt
 
 
-def run_batch_graph(dev_batch, offsets, ps, chunk_mult, replays=2):
+def run_batch_graph(dev_batch, offsets, ps, chunk_mult, replays=2, fold=None):
     """The benchmark's launch: prepare the plan, a first call on a side stream
     (set-up), capture one ch_hull_batched in a CUDA graph on that stream, then
     replay the graph; the outputs are overwritten with garbage before every
@@ -171,7 +175,7 @@ def run_batch_graph(dev_batch, offsets, ps, chunk_mult, replays=2):
     d_pts, d_off, d_ps, hoff, d_hoff, hull, cnt = dev_batch
     ws = torch.empty(ch.ch_batched_workspace_size(offsets, ps, chunk_mult), dtype=torch.uint8,
                      device="cuda")
-    ch.ch_batched_prepare(offsets, ps, ws, chunk_mult)
+    ch.ch_batched_prepare(offsets, ps, ws, chunk_mult, fold_threads=fold)
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(stream):
@@ -215,33 +219,36 @@ def _check_against(hulls, hoff, hull, cnt, sets, where):
 
 def test_batched_graph_replay_as_benchmarked():
     """The launch the benchmark times: the 10,000-set batch, the chunk
-    multiplier chosen by the autotuner on this batch (and 4096, the choice of
-    the recorded runs), one ch_hull_batched captured in a CUDA graph and
+    multiplier and CTA shape chosen by the autotuner on this batch (and 4096
+    with the default shape), one ch_hull_batched captured in a CUDA graph and
     replayed twice; 200 sampled sets and the largest against the oracle."""
     pts, offsets, ps, _ = synth.batched(10_000, seed=4)
     db = _device_batch(pts, offsets, ps)
     d_pts, d_off, d_ps, hoff, d_hoff, hull, cnt = db
-    best, times = autotune.tune_batched(d_pts, offsets, ps, d_off, d_ps, hull, d_hoff, cnt,
-                                        use_cache=False)
-    assert best in autotune.CANDIDATES and set(times) == set(autotune.CANDIDATES)
+    (best, fold), times = autotune.tune_batched(d_pts, offsets, ps, d_off, d_ps, hull, d_hoff,
+                                                cnt, use_cache=False)
+    assert best in autotune.CANDIDATES and fold in autotune.SHAPES
+    assert len(times) == len(autotune.CANDIDATES) * len(autotune.SHAPES)
     rng = np.random.default_rng(0)
     sample = sorted(set(rng.choice(len(ps), size=200, replace=False).tolist())
                     | {int(np.argmax(np.diff(offsets)))})
     hulls = _OracleHulls(pts, offsets, ps)
-    for cm in sorted({best, 4096}):
-        for r, (h, c) in enumerate(run_batch_graph(db, offsets, ps, cm)):
+    for cm, fd in sorted({(best, fold), (4096, ch.CH_BATCH_FOLD_DEFAULT)}):
+        for r, (h, c) in enumerate(run_batch_graph(db, offsets, ps, cm, fold=fd)):
             assert np.all(c >= 1)
-            _check_against(hulls, hoff, h, c, sample, f"chunk_mult {cm} replay {r}")
+            _check_against(hulls, hoff, h, c, sample, f"chunk_mult {cm} fold {fd} replay {r}")
 
 
 def test_batched_graph_replay_every_candidate():
-    """Every chunk multiplier the autotuner may choose, each as a CUDA-graph
-    replay (twice) on a 1,000-set batch of the benchmark's recipe: every set
-    against the oracle."""
+    """Every chunk multiplier and CTA shape the autotuner may choose, each as
+    a CUDA-graph replay (twice) on a 1,000-set batch of the benchmark's
+    recipe: every set against the oracle."""
     pts, offsets, ps, _ = synth.batched(1_000, seed=11)
     db = _device_batch(pts, offsets, ps)
     hoff = db[3]
     hulls = _OracleHulls(pts, offsets, ps)
     for cm in autotune.CANDIDATES:
-        for r, (h, c) in enumerate(run_batch_graph(db, offsets, ps, cm)):
-            _check_against(hulls, hoff, h, c, range(len(ps)), f"chunk_mult {cm} replay {r}")
+        for fd in autotune.SHAPES:
+            for r, (h, c) in enumerate(run_batch_graph(db, offsets, ps, cm, fold=fd)):
+                _check_against(hulls, hoff, h, c, range(len(ps)),
+                               f"chunk_mult {cm} fold {fd} replay {r}")

@@ -1,5 +1,5 @@
 """The single-launch path of ch_convex_hull for small problems (p <= 16384,
-up to 16384 points per CTA, the partial rows of all CTAs small enough for
+up to 8192 points per CTA, the partial rows of all CTAs small enough for
 one CTA to merge): one kernel folds, merges and finishes the set.  Every
 hull and L against the oracle (Algorithm 1, then the hull of its chains),
 including empty, degenerate and misaligned inputs, range errors, repeated
@@ -43,14 +43,15 @@ def check(P, p, d=None):
 
 def test_plan_reports_one_launch():
     assert small(100_000, 1024)  # the small configuration: p = 1024, n = 10^5
-    assert small(0, 1) and small(16384, 16384) and small(65536, 16384)
-    assert not small(65537, 16384)  # five CTAs' rows of 16384 words: too many to merge
+    assert small(0, 1) and small(32_768, 16384) and small(524_288, 1024)
+    assert not small(32_769, 16384)  # five CTAs' rows of 16384 words: too many to merge
+    assert not small(524_289, 1024)
     assert not small(100_000, 16385)
     assert not small(1 << 26, 65536)
 
 
 @pytest.mark.parametrize("p", [1, 2, 5, 31, 33, 256, 1000, 1024, 1025, 4096, 16384])
-@pytest.mark.parametrize("n", [0, 1, 2, 7, 1000, 16383, 16384, 16385, 100_000])
+@pytest.mark.parametrize("n", [0, 1, 2, 7, 1000, 8191, 8192, 8193, 32_768, 100_000, 524_288])
 def test_small_path_matches_oracle(p, n):
     if not small(n, p):
         pytest.skip("not a single-launch case")
