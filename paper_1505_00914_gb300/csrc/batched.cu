@@ -180,8 +180,8 @@ __device__ Survivors collect_survivors(int p, const int *slo, const int *shi, un
         }
         __syncthreads();
         build_min_trees(P0, M0, cnt, P1, M1, cnt);
-        const bool k0 = run_keeps<true, true>(P0, M0, cnt, threadIdx.x);
-        const bool k1 = run_keeps<true, true>(P1, M1, cnt, threadIdx.x);
+        bool k0, k1;
+        run_keeps_pair<true>(P0, M0, P1, M1, cnt, threadIdx.x, k0, k1);
         const int2 nk = compact_runs<false>(P0, k0, glo + T0, P1, k1, gup + T1, s_warp);
         T0 += nk.x;
         T1 += nk.y;

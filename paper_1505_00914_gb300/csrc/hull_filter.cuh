@@ -72,9 +72,39 @@ __device__ __forceinline__ void build_min_trees(const int2 *P0, short *M0, int n
         group_sync<BAR, NT>();
     }
     if (i < 32) {
-        for (int k = WARP_LEVEL; k <= RUN_LOG; ++k) {
-            level(k);
-            __syncwarp();
+        // lane i holds node i of the current level as (index of its lowest
+        // point, that point's y; INT_MAX when the node is empty) for both
+        // runs; the next level combines lanes 2j and 2j + 1 by shuffles
+        constexpr int EMPTY_Y = 0x7FFFFFFF;
+        auto node = [&](const int2 *P, const short *M, int n, int &m, int &y) {
+            const int a = M[tree_off(WARP_LEVEL - 1) + 2 * i];
+            const int b = M[tree_off(WARP_LEVEL - 1) + 2 * i + 1];
+            const bool va = a >= 0 && a < n, vb = b >= 0 && b < n;
+            const int ya = va ? P[a].y : EMPTY_Y, yb = vb ? P[b].y : EMPTY_Y;
+            m = va ? ((vb && yb < ya) ? b : a) : (vb ? b : -1);
+            y = yb < ya ? yb : ya;
+        };
+        int m0, y0, m1, y1;
+        node(P0, M0, n0, m0, y0);
+        node(P1, M1, n1, m1, y1);
+        M0[tree_off(WARP_LEVEL) + i] = (short)m0;
+        M1[tree_off(WARP_LEVEL) + i] = (short)m1;
+#pragma unroll
+        for (int k = WARP_LEVEL + 1; k <= RUN_LOG; ++k) {
+            const int sa = (2 * i) & 31, sb = (2 * i + 1) & 31;
+            const int ma0 = __shfl_sync(0xFFFFFFFFu, m0, sa), ya0 = __shfl_sync(0xFFFFFFFFu, y0, sa);
+            const int mb0 = __shfl_sync(0xFFFFFFFFu, m0, sb), yb0 = __shfl_sync(0xFFFFFFFFu, y0, sb);
+            const int ma1 = __shfl_sync(0xFFFFFFFFu, m1, sa), ya1 = __shfl_sync(0xFFFFFFFFu, y1, sa);
+            const int mb1 = __shfl_sync(0xFFFFFFFFu, m1, sb), yb1 = __shfl_sync(0xFFFFFFFFu, y1, sb);
+            // the left child wins ties; an empty child (y = INT_MAX) never wins
+            m0 = yb0 < ya0 ? mb0 : ma0;
+            y0 = yb0 < ya0 ? yb0 : ya0;
+            m1 = yb1 < ya1 ? mb1 : ma1;
+            y1 = yb1 < ya1 ? yb1 : ya1;
+            if (i < (RUN >> k)) {
+                M0[tree_off(k) + i] = (short)m0;
+                M1[tree_off(k) + i] = (short)m1;
+            }
         }
     }
     group_sync<BAR, NT>();
@@ -125,6 +155,61 @@ __device__ __forceinline__ bool run_keeps(const int2 *P, const short *M, int n, 
             drop |= la[u] >= 0 && ra[u] >= 0 && orient<NARROW>(A[u], B[u], q) >= 0;
     }
     return !drop;
+}
+
+// run_keeps<true, NARROW> for point i of two runs at once (P0/M0 and P1/M1
+// of the same length n, the two chains of one tile): the same tests, their
+// shared-memory loads interleaved so that the two chains' latencies overlap,
+// and a warp stops once every point of both is dropped.
+template <bool NARROW>
+__device__ __forceinline__ void run_keeps_pair(const int2 *P0, const short *M0, const int2 *P1,
+                                               const short *M1, int n, int i, bool &keep0,
+                                               bool &keep1)
+{
+    const bool alive = i < n;
+    const bool h1 = alive && i >= 1 && i + 1 < n, l2 = i >= 2, r2 = i + 2 < n;
+    const int2 q0 = alive ? P0[i] : make_int2(0, 0), q1 = alive ? P1[i] : make_int2(0, 0);
+    const int2 a1 = alive && i >= 1 ? P0[i - 1] : q0, b1 = alive && i + 1 < n ? P0[i + 1] : q0;
+    const int2 c1 = alive && i >= 1 ? P1[i - 1] : q1, d1 = alive && i + 1 < n ? P1[i + 1] : q1;
+    const int2 a2 = alive && l2 ? P0[i - 2] : q0, b2 = alive && r2 ? P0[i + 2] : q0;
+    const int2 c2 = alive && l2 ? P1[i - 2] : q1, d2 = alive && r2 ? P1[i + 2] : q1;
+    bool drop0 = !alive || (h1 && (orient<NARROW>(a1, b1, q0) >= 0 ||
+                                   (r2 && orient<NARROW>(a1, b2, q0) >= 0) ||
+                                   (l2 && orient<NARROW>(a2, b1, q0) >= 0)));
+    bool drop1 = !alive || (h1 && (orient<NARROW>(c1, d1, q1) >= 0 ||
+                                   (r2 && orient<NARROW>(c1, d2, q1) >= 0) ||
+                                   (l2 && orient<NARROW>(c2, d1, q1) >= 0)));
+    constexpr int CH = 3;  // levels per batch; levels 2..RUN_LOG-1 have siblings
+#pragma unroll
+    for (int k0 = 2; k0 < RUN_LOG; k0 += CH) {
+        if (__all_sync(0xFFFFFFFFu, drop0 && drop1))
+            break;
+        int la0[CH], ra0[CH], la1[CH], ra1[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int k = k0 + u, node = i >> k;
+            const bool hl = k < RUN_LOG && node >= 1, hr = k < RUN_LOG && (node + 1) < (RUN >> k);
+            la0[u] = hl ? M0[tree_off(k) + node - 1] : -1;
+            ra0[u] = hr ? M0[tree_off(k) + node + 1] : -1;
+            la1[u] = hl ? M1[tree_off(k) + node - 1] : -1;
+            ra1[u] = hr ? M1[tree_off(k) + node + 1] : -1;
+        }
+        int2 A0[CH], B0[CH], A1[CH], B1[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            A0[u] = la0[u] >= 0 ? P0[la0[u]] : q0;
+            B0[u] = ra0[u] >= 0 ? P0[ra0[u]] : q0;
+            A1[u] = la1[u] >= 0 ? P1[la1[u]] : q1;
+            B1[u] = ra1[u] >= 0 ? P1[ra1[u]] : q1;
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            drop0 |= la0[u] >= 0 && ra0[u] >= 0 && orient<NARROW>(A0[u], B0[u], q0) >= 0;
+            drop1 |= la1[u] >= 0 && ra1[u] >= 0 && orient<NARROW>(A1[u], B1[u], q1) >= 0;
+        }
+    }
+    keep0 = !drop0;
+    keep1 = !drop1;
 }
 
 // Writes the kept points of P[0..n), in order, to out; returns their number.
