@@ -154,37 +154,6 @@ __device__ __forceinline__ void stream_pairs(const int4 *__restrict__ p4, int64_
     }
 }
 
-// stream_pairs, but fold(v, m) takes a thread's whole group of RU vectors
-// at once, the first m of which are in the slice (m >= 1).
-template <int RT, typename Fold>
-__device__ __forceinline__ void stream_groups(const int4 *__restrict__ p4, int64_t s0, int64_t e0,
-                                              Fold &&fold)
-{
-    int4 v[RU];
-#pragma unroll
-    for (int u = 0; u < RU; ++u) {
-        const int64_t j = s0 + threadIdx.x + (int64_t)u * RT;
-        v[u] = j < e0 ? __ldcs(p4 + j) : make_int4(0, 0, 0, 0);
-    }
-    for (int64_t i = s0 + threadIdx.x; i < e0; i += (int64_t)RT * RU) {
-        int4 w[RU];
-#pragma unroll
-        for (int u = 0; u < RU; ++u) {
-            const int64_t j = i + (int64_t)(RU + u) * RT;
-            w[u] = j < e0 ? __ldcs(p4 + j) : make_int4(0, 0, 0, 0);
-        }
-        const int64_t left = (e0 - i + RT - 1) / RT;
-        fold(v, left < RU ? (int)left : RU);
-#pragma unroll
-        for (int u = 0; u < RU; ++u)
-            v[u] = w[u];
-    }
-}
-
-#ifndef CH_PRIVATE_GROUPED
-#define CH_PRIVATE_GROUPED 1
-#endif
-
 // ---------------------------------------------------------------- private
 template <int RT, int FM>
 __global__ void __launch_bounds__(RT)
@@ -222,56 +191,7 @@ __global__ void __launch_bounds__(RT)
     const int64_t per = (pv.nvec + gridDim.x - 1) / gridDim.x;
     const int64_t s0 = (int64_t)blockIdx.x * per;
     const int64_t e0 = min(pv.nvec, s0 + per);
-#if CH_PRIVATE_GROUPED
-    // all the shared reads of a thread's RU vectors are issued before any
-    // compare or atomic, so their latencies overlap; a read that an atomic
-    // of the same group has since made stale only costs an atomic that does
-    // not change the entry (entries only tighten), never a missed update
-    constexpr int VC = 4 / PPV<FM>;  // vectors per chunk of four points
-    stream_groups<RT>(pv.p4, s0, e0, [&](const int4 (&v)[RU], int m) {
-#pragma unroll
-        for (int u0 = 0; u0 < RU; u0 += VC) {
-            uint32_t c[4];
-            int r[4];
-            bool ok[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int u = u0 + k / PPV<FM>, q = k % PPV<FM>;
-                int x, y;
-                if constexpr (FM == 3) {
-                    const uint32_t wv = (uint32_t)(q == 0 ? v[u].x : q == 1 ? v[u].y
-                                                   : q == 2 ? v[u].z : v[u].w);
-                    x = (int)(wv & 0xFFFFu) + 1;
-                    y = (int)(wv >> 16) + 1;
-                } else {
-                    x = q == 0 ? v[u].x : v[u].z;
-                    y = q == 0 ? v[u].y : v[u].w;
-                }
-                uint32_t rr;
-                frame_map<FM>(f, x, y, c[k], rr);
-                const bool in = c[k] < (uint32_t)nc && rr < (uint32_t)f.nr;
-                bad |= u < m && !in;
-                ok[k] = u < m && in;
-                r[k] = (int)rr + 1;
-            }
-            int lo[4], hi[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                lo[k] = ok[k] ? slo[c[k]] : 0;
-                hi[k] = ok[k] ? shi[c[k]] : 0;
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (ok[k] && r[k] < lo[k])
-                    atomicMin(slo + c[k], r[k]);
-                if (ok[k] && r[k] > hi[k])
-                    atomicMax(shi + c[k], r[k]);
-            }
-        }
-    });
-#else
     stream_pairs<RT>(pv.p4, s0, e0, [&](const int4 &v) { each_point<FM>(v, fold); });
-#endif
     __syncthreads();
     uint32_t *out = part + (size_t)blockIdx.x * nc;
     for (int i = threadIdx.x; i < nc; i += RT)  // rows <= 65536 in this form
