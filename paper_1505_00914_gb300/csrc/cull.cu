@@ -41,7 +41,7 @@ constexpr int HB = 32;                   // histogram CTAs (rows of counts)
 constexpr int HU = (SJ + HB - 1) / HB;   // runs per histogram CTA
 constexpr int KC = 64;                   // inputs per CTA of a hidden layer
 constexpr int KS1 = NI / KC, KS2 = NH / KC;
-constexpr int EXB = 128, EXT = 256;      // extremes CTAs x threads
+constexpr int EXB = 32, EXT = 256;       // extremes CTAs x threads (k_cull_init folds EXB candidates per direction)
 constexpr int EXU = 8;                   // sample points in flight per thread
 constexpr long long NONE = 0x7FFFFFFFFFFFFFFFll;
 static_assert(SR == NI, "one histogram cell per thread");
