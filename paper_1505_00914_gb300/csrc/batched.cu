@@ -108,7 +108,13 @@ __device__ void fold_range(const int32_t *__restrict__ base, int64_t n, int p, i
 
 // Tiles with at most this many valid columns skip the pre-filter: below it
 // the peeling rounds remove their non-vertices for less than the trees cost.
-constexpr int SPARSE_TILE = 512;
+// Swept on the 10,000-set batch with the split CTA (ms per replay): 64 2.625,
+// 128 2.588, 192 2.574, 256 2.553, 384 2.568, 512 2.587, 768 2.704, 1024
+// (no tile filtered) 3.996.
+#ifndef CH_SPARSE_TILE
+#define CH_SPARSE_TILE 256
+#endif
+constexpr int SPARSE_TILE = CH_SPARSE_TILE;
 
 // What the tile pre-filter leaves of a set: the survivors at D, the lower
 // chain in D[0..T0) and the mirrored upper chain in D[T0..T).

@@ -41,7 +41,10 @@
 namespace ch {
 namespace {
 
-constexpr int RU = 4;            // 16-byte loads in flight per thread per iteration
+#ifndef CH_RU
+#define CH_RU 4
+#endif
+constexpr int RU = CH_RU;        // 16-byte loads in flight per thread per iteration
 
 // The point array is read as 16-byte vectors from the first 16-byte
 // boundary: two int32 (x, y) points per vector, or four packed 16-bit points
