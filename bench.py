@@ -5,7 +5,9 @@ Default workload (the configuration the headline metric is quoted on):
 p = 65536, n = 2^26 int32 points per instance, three seeded distributions
 (uniform square, inscribed disc, Gaussian sigma = p/8) run separately.  One
 step = one ch_convex_hull call per distribution (3 * 2^26 points), each
-instance on its own CUDA stream and workspace (independent problems).
+instance on its own CUDA stream and workspace (independent problems);
+consecutive steps are pipelined: each instance's stream runs its calls in
+order and the streams are joined only at the ends of a timed region.
 Inputs (537 MB each) are resident in HBM and larger than L2, so no flush is
 needed.
 
@@ -329,7 +331,11 @@ def workload_config(workload):
             "point_format": ("packed uint16 pairs (x - 1, y - 1), 4 bytes per point"
                              if bpp == 4 else "int32 pairs, 8 bytes per point"),
             "instances_per_step": len(dists),
-            "concurrency": "each instance on its own CUDA stream and workspace",
+            "concurrency": ("each instance on its own CUDA stream and workspace"
+                            + ("; consecutive steps pipelined (an instance's calls in order on "
+                               "its stream, the streams joined at the ends of each timed region)"
+                               if n * bpp >= L2_FLUSH_BELOW else
+                               "; the streams joined after every step (each step follows a flush)")),
             "l2": (f"inputs {bpp}n bytes per instance, larger than L2; no flush"
                    if n * bpp >= L2_FLUSH_BELOW else
                    "inputs smaller than L2: a 256 MB write precedes every step and its time "
@@ -461,12 +467,23 @@ def run_ours(args):
     # the main stream, timed alone and subtracted)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if n * bpp < L2_FLUSH_BELOW else None
 
+    # without a flush between steps, consecutive steps are pipelined: an
+    # instance's stream runs that instance's calls in order (one workspace
+    # each), and the streams are joined only at the ends of a timed region,
+    # so the last instance's chain and final-hull kernels of one step overlap
+    # the next step's first instance
+    pipelined = flush is None
+
     def step(concurrent=True):
         if flush is not None:
             flush.zero_()
         if not concurrent:  # one after another on the main stream
             for d, h, c, w in zip(dev_in, hulls, hcs, wss):
                 hull_fn(d, p, hull=h, hull_count=c, workspace=w, stream=stream)
+            return
+        if pipelined:
+            for d, h, c, w, st in zip(dev_in, hulls, hcs, wss, streams):
+                hull_fn(d, p, hull=h, hull_count=c, workspace=w, stream=st)
             return
         fork = torch.cuda.Event()
         fork.record(stream)
@@ -501,7 +518,8 @@ def run_ours(args):
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
-    ms, regions = _timed_regions(torch, dist, world, step, args.steps, stream, args.regions, fl)
+    ms, regions = _timed_regions(torch, dist, world, step, args.steps, stream, args.regions, fl,
+                                 side=streams if pipelined else ())
     for _ in range(2):
         step(False)
     ch.ch_trace_set(evs)
@@ -661,26 +679,35 @@ def _status(ch, *streams):
     return rc
 
 
-def _timed_regions(torch, dist, world, fn, steps, stream, regions, offset=0.0):
+def _timed_regions(torch, dist, world, fn, steps, stream, regions, offset=0.0, side=()):
     """`regions` timed regions of exactly `steps` calls of fn each, back to
     back (each bracketed by a barrier and a synchronize on both sides, max
     over ranks); returns (median region ms minus offset, [every region's ms
     minus offset]).  More than one region keeps the GPU under load long
     enough for the clock sampler to see it several times."""
-    ts = [_timed(torch, dist, world, fn, steps, stream) - offset for _ in range(max(1, regions))]
+    ts = [_timed(torch, dist, world, fn, steps, stream, side) - offset
+          for _ in range(max(1, regions))]
     return statistics.median(ts), ts
 
 
-def _timed(torch, dist, world, fn, steps, stream):
+def _timed(torch, dist, world, fn, steps, stream, side=()):
     """Device time in ms of `steps` calls of fn, barrier + synchronize on
-    both sides, max over ranks."""
+    both sides, max over ranks.  side: streams fn also launches on without
+    joining them itself (pipelined steps): they start after the region's
+    start event and the end event waits for all of them."""
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
+    for st in side:
+        st.wait_event(a)
     for _ in range(steps):
         fn()
+    for st in side:
+        j = torch.cuda.Event()
+        j.record(st)
+        stream.wait_event(j)
     b.record(stream)
     torch.cuda.synchronize()
     if world > 1:
