@@ -296,7 +296,9 @@ def workload_config(workload):
         p, n, dists = LEARNED
         return {"workload": "learned", "p": p, "n_per_instance": n, "distributions": list(dists),
                 "instances_per_step": len(dists),
-                "concurrency": "each instance on its own CUDA stream and workspace, in every arm",
+                "concurrency": ("each instance on its own CUDA stream and workspace, in every arm; "
+                                "consecutive steps pipelined (streams joined at the ends of each "
+                                "timed region)"),
                 "l2": "inputs 8n bytes per instance, larger than L2; no flush"}
     if workload == "box":
         return {"workload": "box", "n_per_instance": BOX_N,
@@ -737,14 +739,17 @@ def run_learned(args):
     Linit = {a: [torch.empty((p, 2), dtype=torch.int32, device="cuda") for _ in inputs]
              for a in ("learned", "centres")}
 
-    def step(arm, concurrent=True):
+    # as in the plain workload, consecutive steps are pipelined on the
+    # instances' streams (joined at the ends of a timed region), in every arm
+    def step(arm, concurrent=True, pipelined=False):
         sts = streams if concurrent else [stream] * len(inputs)
-        if concurrent:
+        fork_join = concurrent and not pipelined
+        if fork_join:
             fork = torch.cuda.Event()
             fork.record(stream)
         for i, d in enumerate(dev_in):
             h, c, st = hulls[arm][i], hcs[arm][i], sts[i]
-            if concurrent:
+            if fork_join:
                 st.wait_event(fork)
             if arm == "plain":
                 ch.ch_convex_hull(d, p, hull=h, hull_count=c, workspace=wss[i], stream=st)
@@ -752,7 +757,7 @@ def run_learned(args):
                 ch.ch_hull_learned(d, p, params=params if arm == "learned" else None,
                                    Linit=Linit[arm][i], hull=h, hull_count=c, workspace=wss[i],
                                    stream=st)
-        if concurrent:
+        if fork_join:
             for st in streams:
                 join = torch.cuda.Event()
                 join.record(st)
@@ -823,7 +828,8 @@ def run_learned(args):
     time.sleep(0.3)
     ms = {}
     for arm in ("learned", "plain", "centres"):
-        ms[arm] = _timed(torch, dist, world, lambda arm=arm: step(arm), args.steps, stream)
+        ms[arm] = _timed(torch, dist, world, lambda arm=arm: step(arm, pipelined=True), args.steps,
+                         stream, side=streams)
     for _ in range(2):
         step("learned", False)
     ch.ch_trace_set(evs)  # the learned arm again, one instance after another, reductions timed
