@@ -315,14 +315,14 @@ int ch_batched_prepare(int32_t B, const int64_t *host_offsets, const int32_t *ho
 
 /* The CTA shape of ch_hull_batched's persistent kernel (1024 threads):
  * fold_threads = 0 has every thread fold a set's points and then finish it
- * (chains, exact pre-filter, peel/merge/stitch); 512, 768 or 896 splits the
- * CTA: that many threads fold the next set's points while the other 512, 256
- * or 128 threads peel, merge and stitch the previous set (the pre-filter,
- * which reads the set's L in shared memory, is run by all of them).  The
- * hulls are the same for every shape. */
+ * (chains, exact pre-filter, peel/merge/stitch); 384, 512, 640, 768 or 896
+ * splits the CTA: that many threads fold the next set's points while the
+ * other 1024 - fold_threads peel, merge and stitch the previous set (the
+ * pre-filter, which reads the set's L in shared memory, is run by all of
+ * them).  The hulls are the same for every shape. */
 #define CH_BATCH_FOLD_DEFAULT 512
 
-/* ch_batched_prepare with the CTA shape (fold_threads: 0, 512, 768 or 896;
+/* ch_batched_prepare with the CTA shape (fold_threads: 0, 384, 512, 640, 768 or 896;
  * anything else is CH_ERR_ARG).  ch_batched_prepare uses
  * CH_BATCH_FOLD_DEFAULT; the autotuner times the others. */
 int ch_batched_prepare_shape(int32_t B, const int64_t *host_offsets, const int32_t *host_ps,

@@ -537,7 +537,7 @@ def ch_batched_workspace_size(offsets, ps, chunk_mult: int = 64) -> int:
 
 
 CH_BATCH_FOLD_DEFAULT = 512  # the header's #define of the same name
-CH_BATCH_FOLD_SHAPES = (0, 512, 768, 896)
+CH_BATCH_FOLD_SHAPES = (0, 384, 512, 640, 768, 896)
 
 
 def ch_batched_prepare(offsets, ps, workspace, chunk_mult: int = 64, stream=None,

@@ -739,7 +739,9 @@ int batch_launch(const int32_t *pts, int2 *hull_out, const int64_t *hull_offsets
         const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
         if (cudaFuncSetAttribute(k_batched<false>, a, (int)BATCH_SMEM) != cudaSuccess ||
             cudaFuncSetAttribute(k_batched<true>, a, (int)BATCH_SMEM) != cudaSuccess ||
+            cudaFuncSetAttribute(k_batched_ws<384>, a, (int)WS_SMEM) != cudaSuccess ||
             cudaFuncSetAttribute(k_batched_ws<512>, a, (int)WS_SMEM) != cudaSuccess ||
+            cudaFuncSetAttribute(k_batched_ws<640>, a, (int)WS_SMEM) != cudaSuccess ||
             cudaFuncSetAttribute(k_batched_ws<768>, a, (int)WS_SMEM) != cudaSuccess ||
             cudaFuncSetAttribute(k_batched_ws<896>, a, (int)WS_SMEM) != cudaSuccess)
             return CH_ERR_CUDA;
@@ -752,7 +754,9 @@ int batch_launch(const int32_t *pts, int2 *hull_out, const int64_t *hull_offsets
     if (!L_out && info.fold > 0) {
         if (!batch_fold_ok(info.fold))
             return CH_ERR_ARG;
-        auto ws_kern = info.fold == 512 ? k_batched_ws<512>
+        auto ws_kern = info.fold == 384   ? k_batched_ws<384>
+                       : info.fold == 512 ? k_batched_ws<512>
+                       : info.fold == 640 ? k_batched_ws<640>
                        : info.fold == 768 ? k_batched_ws<768>
                                           : k_batched_ws<896>;
         ws_kern<<<info.grid, BT, WS_SMEM, s>>>(

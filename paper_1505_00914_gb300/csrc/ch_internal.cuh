@@ -220,7 +220,10 @@ struct BatchPlanInfo {
     int fold;  // threads of a CTA that fold while the others finish (0: the whole CTA does both)
 };
 // The CTA splits the batched hull kernel is built for (threads that fold).
-inline bool batch_fold_ok(int fold) { return fold == 0 || fold == 512 || fold == 768 || fold == 896; }
+inline bool batch_fold_ok(int fold)
+{
+    return fold == 0 || fold == 384 || fold == 512 || fold == 640 || fold == 768 || fold == 896;
+}
 size_t batch_smem();
 // One set of n points and side p in one launch (k_small): the number of CTAs
 // it takes, or 0 when the set is too large for that path.
