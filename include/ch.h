@@ -25,8 +25,10 @@
  *     point array gives the fastest loads.
  *   - Nothing allocates device memory inside a call: each call that needs
  *     scratch takes a caller-owned device workspace whose size is returned by
- *     the matching *_workspace_size query.  A workspace may be reused by any
- *     later call on the same stream; two calls in flight at once need two.
+ *     the matching *_workspace_size query.  A workspace starts on a 256-byte
+ *     boundary (as cudaMalloc returns memory); a misaligned one is refused
+ *     with CH_ERR_ARG.  A workspace may be reused by any later call on the
+ *     same stream; two calls in flight at once need two.
  *   - Calls are asynchronous and stream-ordered on `stream` (NULL = legacy
  *     default stream).  The return value reports argument and launch errors
  *     only.  Errors that depend on the data (a point outside [1,p]^2, a

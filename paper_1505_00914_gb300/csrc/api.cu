@@ -34,6 +34,9 @@ std::map<cudaStream_t, int> g_slot_of[MAX_DEV];
 int g_sms[MAX_DEV] = {};
 
 inline bool aligned8(const void *p) { return ((uintptr_t)p & 7) == 0; }
+// Workspaces start on a 256-byte boundary (as cudaMalloc returns them): the
+// kernels put 16-byte vectors and 8-byte words at offsets inside them.
+inline bool ws_aligned(const void *w) { return ((uintptr_t)w & 255) == 0; }
 
 // ch_trace_set ring of event pairs around the reduction kernel.
 std::mutex g_trace_mu;
@@ -300,6 +303,8 @@ int ch_reduce(const int32_t *pts, int64_t n, int32_t p, int32_t *L, void *worksp
     if (rc != CH_OK)
         return rc;
     const size_t need = reduce_partials_bytes(pl, p);
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < need || (need > 0 && !workspace))
         return CH_ERR_WORKSPACE;
     unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
@@ -332,6 +337,8 @@ int ch_chain(const int32_t *L, int32_t p, int32_t *lower, int32_t *upper, int32_
         return CH_ERR_ARG;
     size_t need = 0;
     ch_chain_workspace_size(p, &need);
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < need || !workspace)
         return CH_ERR_WORKSPACE;
     unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
@@ -355,6 +362,8 @@ int ch_hull(const int32_t *lower, const int32_t *upper, const int32_t *counts, i
 {
     if (p < 1 || p > CH_MAX_P || !lower || !upper || !counts || !hull || !hull_count ||
         !aligned8(lower) || !aligned8(upper) || !aligned8(hull))
+        return CH_ERR_ARG;
+    if (!ws_aligned(workspace))
         return CH_ERR_ARG;
     if (ws_bytes < hull_ws_bytes(p) || !workspace)
         return CH_ERR_WORKSPACE;
@@ -396,6 +405,8 @@ int convex_hull_square(const int32_t *pts, int64_t n, int32_t p, const Frame &fr
     if (rc != CH_OK)
         return rc;
     const bool int32_pts = frame_mode(frame) == 0;
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < (int32_pts ? plain_ws_bytes(w, n, p) : w.end) || !workspace)
         return CH_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -483,6 +494,8 @@ int ch_reduce_u16(const uint32_t *pts, int64_t n, int32_t p, int32_t *L, void *w
     if (rc != CH_OK)
         return rc;
     const size_t need = reduce_partials_bytes(pl, p);
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < need || (need > 0 && !workspace))
         return CH_ERR_WORKSPACE;
     unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
@@ -533,6 +546,8 @@ int ch_batched_prepare_shape(int32_t B, const int64_t *host_offsets, const int32
     if (rc != CH_OK)
         return rc;
     if (!batch_fold_ok(fold_threads))
+        return CH_ERR_ARG;
+    if (!ws_aligned(workspace))
         return CH_ERR_ARG;
     if (!workspace)
         return CH_ERR_WORKSPACE;
@@ -669,6 +684,8 @@ int ch_mlp_backward(const float *params, const float *X, const float *H1, const 
 {
     if (M < 1 || !params || !X || !H1 || !H2 || !dY || !grads)
         return CH_ERR_ARG;
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < 2 * (size_t)M * CH_MLP_HID * sizeof(float) || !workspace)
         return CH_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -743,6 +760,8 @@ int ch_cull_propose(const int32_t *pts, int64_t n, int32_t p, const float *param
     if (check_np(n, p) != CH_OK || (n > 0 && !pts) || !Linit || !aligned8(pts) ||
         !aligned8(Linit) || !aligned8(poly))
         return CH_ERR_ARG;
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < cull_ws_bytes(p) || !workspace)
         return CH_ERR_WORKSPACE;
     return cuda_rc(cull_launch(pts, n, p, params, workspace, Linit, nullptr, nullptr, false, 0,
@@ -791,6 +810,8 @@ int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *param
     int rc = learned_layout(n, p, &w);
     if (rc != CH_OK)
         return rc;
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < w.end || !workspace)
         return CH_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -863,6 +884,8 @@ int ch_bbox(const int32_t *pts, int64_t n, int32_t *box, void *workspace, size_t
 {
     if (n < 0 || (n > 0 && !pts) || !box || !aligned8(pts))
         return CH_ERR_ARG;
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < (size_t)bbox_parts() * 16 || !workspace)
         return CH_ERR_WORKSPACE;
     return cuda_rc(bbox_launch(pts, n, box, workspace, reinterpret_cast<cudaStream_t>(stream)));
@@ -912,6 +935,8 @@ int ch_convex_hull_box(const int32_t *pts, int64_t n, const int32_t *host_box, i
     int rc = box_layout(n, f, &w);
     if (rc != CH_OK)
         return rc;
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < w.end || !workspace)
         return CH_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -976,6 +1001,8 @@ int ch_convex_hull_host(const int32_t *host_pts, int64_t n, int32_t p, int32_t *
     int rc = ch_convex_hull_host_workspace_size(n, p, &need);
     if (rc != CH_OK)
         return rc;
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < need || !workspace)
         return CH_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -1022,6 +1049,8 @@ int ch_polyline(const int32_t *L, int32_t p, int32_t *poly, int32_t *count, void
 {
     if (p < 1 || p > CH_MAX_P || !L || !poly || !count || !aligned8(L) || !aligned8(poly))
         return CH_ERR_ARG;
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < polyline_state_bytes(p) || !workspace)
         return CH_ERR_WORKSPACE;
     unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
@@ -1046,6 +1075,8 @@ int ch_hull_melkman(const int32_t *poly, const int32_t *count, int32_t p, int32_
         !aligned8(hull))
         return CH_ERR_ARG;
     const size_t need = melkman_ws_bytes(p);
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < need || (need && !workspace))
         return CH_ERR_WORKSPACE;
     unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
@@ -1100,6 +1131,8 @@ int ch_convex_hull_melkman(const int32_t *pts, int64_t n, int32_t p, int32_t *L,
     int rc = melkman_layout(n, p, &w);
     if (rc != CH_OK)
         return rc;
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < w.end || !workspace)
         return CH_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -1157,6 +1190,8 @@ int ch_convex_hull_sparse(const int32_t *pts, int64_t n, int32_t p, int32_t *low
         !aligned8(lower) || !aligned8(upper) || !aligned8(hull))
         return CH_ERR_ARG;
     const SparseLayout L = sparse_layout(n, p);
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < L.end || !workspace)
         return CH_ERR_WORKSPACE;
     unsigned *st = device_status_ptr(reinterpret_cast<cudaStream_t>(stream));
@@ -1230,6 +1265,8 @@ int ch_convex_hull_rxy(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int
     int rc = rxy_layout(n, p, &w);
     if (rc != CH_OK)
         return rc;
+    if (!ws_aligned(workspace))
+        return CH_ERR_ARG;
     if (ws_bytes < w.end || !workspace)
         return CH_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -165,3 +165,21 @@ def test_chain_binding_checks_array_sizes():
         ch.ch_chain_noalloc(L, 4, lo, lo, cnt)  # host tensors
     with pytest.raises(ValueError):
         ch._check_chain_args(L, 4, lo, lo, cnt, None)
+
+
+def test_misaligned_workspace_is_refused_before_any_launch(lib_path):
+    """A workspace that does not start on a 256-byte boundary is an argument
+    error, returned before any CUDA call (the pointers are never touched, so
+    no GPU is needed)."""
+    import ctypes
+    lib = ctypes.CDLL(lib_path)
+    P = ctypes.c_void_p
+    dev = P(1 << 20)              # 8-byte-aligned stand-ins for device arrays
+    bad = P((1 << 21) + 16)       # 16-byte but not 256-byte aligned
+    lib.ch_chain.argtypes = [P, ctypes.c_int32, P, P, P, P, P, ctypes.c_size_t, P]
+    lib.ch_hull.argtypes = [P, P, P, ctypes.c_int32, P, P, P, ctypes.c_size_t, P]
+    lib.ch_polyline.argtypes = [P, ctypes.c_int32, P, P, P, ctypes.c_size_t, P]
+    big = 1 << 30
+    assert lib.ch_chain(dev, 4096, dev, dev, dev, None, bad, big, None) == -1
+    assert lib.ch_hull(dev, dev, dev, 4096, dev, dev, bad, big, None) == -1
+    assert lib.ch_polyline(dev, 4096, dev, dev, bad, big, None) == -1

@@ -187,6 +187,15 @@ def test_argument_errors():
     with pytest.raises(ch.ChError) as e:
         ch.ch_convex_hull(P, 4096, workspace=small)
     assert e.value.code == ch.CH_ERR_WORKSPACE
+    # a workspace that does not start on a 256-byte boundary
+    for fn, size in ((ch.ch_convex_hull, ch.ch_convex_hull_workspace_size(10, 4096)),
+                     (ch.ch_reduce, ch.ch_reduce_workspace_size(10, 70000))):
+        buf = torch.empty(size + 512, dtype=torch.uint8, device="cuda")
+        for off in (8, 16, 128):
+            with pytest.raises(ch.ChError) as e:
+                fn(P, 4096 if fn is ch.ch_convex_hull else 70000, workspace=buf[off:])
+            assert e.value.code == ch.CH_ERR_ARG
+        fn(P, 4096 if fn is ch.ch_convex_hull else 70000, workspace=buf[256:])
 
 
 def test_host_entry_point_matches():
