@@ -425,12 +425,14 @@ int convex_hull_square(const int32_t *pts, int64_t n, int32_t p, const Frame &fr
     char *b = reinterpret_cast<char *>(workspace);
     if (!L && w.plan.mode != 0)
         L = reinterpret_cast<int32_t *>(b + w.L);  // the filtered forms write L directly
-    if (!lower)
-        lower = reinterpret_cast<int32_t *>(b + w.lower);
-    if (!upper)
-        upper = reinterpret_cast<int32_t *>(b + w.upper);
-    if (!counts)
-        counts = reinterpret_cast<int32_t *>(b + w.counts);
+    if (lower || upper || counts) {  // else the chain step writes only the hull's candidates
+        if (!lower)
+            lower = reinterpret_cast<int32_t *>(b + w.lower);
+        if (!upper)
+            upper = reinterpret_cast<int32_t *>(b + w.upper);
+        if (!counts)
+            counts = reinterpret_cast<int32_t *>(b + w.counts);
+    }
     void *part = b + w.part;
     cudaEvent_t ev0, ev1;
     next_trace(&ev0, &ev1);
@@ -455,7 +457,7 @@ int convex_hull_square(const int32_t *pts, int64_t n, int32_t p, const Frame &fr
                      st, s);
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
-    return cuda_rc(hull_final_launch(hl, hw, hull, hull_count, s));
+    return cuda_rc(hull_final_launch(hl, hw, hull, hull_count, s, p <= 16384));
 }
 }  // namespace
 }  // namespace ch
@@ -863,7 +865,7 @@ int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *param
                      st, s, Linit);
     if (e != cudaSuccess)
         return CH_ERR_CUDA;
-    e = hull_final_launch(hl, hw, hull, hull_count, s);
+    e = hull_final_launch(hl, hw, hull, hull_count, s, p <= 16384);
     if (e == cudaSuccess && stats)
         e = cull_count_launch(pts, n, p, Linit, reinterpret_cast<unsigned long long *>(&stats->culled),
                               s);
@@ -946,9 +948,6 @@ int ch_convex_hull_box(const int32_t *pts, int64_t n, const int32_t *host_box, i
     char *b = reinterpret_cast<char *>(workspace);
     const PathWs &pw = w.path;
     int32_t *L = reinterpret_cast<int32_t *>(b + pw.L);
-    int32_t *lower = reinterpret_cast<int32_t *>(b + pw.lower);
-    int32_t *upper = reinterpret_cast<int32_t *>(b + pw.upper);
-    int32_t *counts = reinterpret_cast<int32_t *>(b + pw.counts);
     void *part = b + pw.part;
     unsigned long long *zero = reinterpret_cast<unsigned long long *>(b + pw.state);
     const int nzero = (int)(chain_state_bytes(f.nc) / 8);
@@ -962,12 +961,14 @@ int ch_convex_hull_box(const int32_t *pts, int64_t n, const int32_t *host_box, i
         return CH_ERR_CUDA;
     const HullLayout hl = hull_layout(f.nc);
     char *hw = b + pw.hull;
-    e = chain_launch(L, f.nc, lower, upper, counts, nullptr, zero, true,
+    // only the hull's candidates: no chain outputs
+    e = chain_launch(L, f.nc, nullptr, nullptr, nullptr, nullptr, zero, true,
                      reinterpret_cast<int2 *>(hw + hl.cand), reinterpret_cast<int *>(hw + hl.ccnt),
                      st, s, nullptr, f.nr);
     if (e == cudaSuccess)
         e = hull_final_launch(hl, hw, reinterpret_cast<int32_t *>(b + w.hull),
-                              reinterpret_cast<int32_t *>(b + w.count), s);
+                              reinterpret_cast<int32_t *>(b + w.count), s,
+                              f.nc <= 16384 && f.nr <= 16384);
     if (e == cudaSuccess)
         e = unframe_launch(reinterpret_cast<int32_t *>(b + w.hull),
                            reinterpret_cast<int32_t *>(b + w.count), f, hull, hull_count, s);
@@ -1293,13 +1294,11 @@ int ch_convex_hull_rxy(const int32_t *pts, int64_t n, int32_t p, int32_t *L, int
     int32_t *hull_t = reinterpret_cast<int32_t *>(b + w.hull_t);
     int32_t *count_t = reinterpret_cast<int32_t *>(b + w.count_t);
     if (e == cudaSuccess)
-        e = chain_launch(R, p, reinterpret_cast<int32_t *>(b + pw.lower),
-                         reinterpret_cast<int32_t *>(b + pw.upper),
-                         reinterpret_cast<int32_t *>(b + pw.counts), nullptr, b + pw.state, false,
+        e = chain_launch(R, p, nullptr, nullptr, nullptr, nullptr, b + pw.state, false,
                          reinterpret_cast<int2 *>(hw + hl.cand), reinterpret_cast<int *>(hw + hl.ccnt),
                          st, s);
     if (e == cudaSuccess)
-        e = hull_final_launch(hl, hw, hull_t, count_t, s);
+        e = hull_final_launch(hl, hw, hull_t, count_t, s, p <= 16384);
     if (e == cudaSuccess)
         e = unframe_launch(hull_t, count_t, Frame{1, 1, p, p, 1, 0}, hull, hull_count, s);
     return cuda_rc(e);

@@ -188,6 +188,9 @@ size_t chain_state_bytes(int p);
 // each 1024-column tile and writes its survivors in the hull layout (so that
 // hull_final_launch can follow directly).  state: chain_state_bytes(p),
 // zeroed here unless state_zeroed.
+// With cand, lower, upper, counts and mask may all be nullptr: the step then
+// writes only the candidates (no look-back).  NARROW orientation tests are
+// taken when p and nr are at most 16384.
 // Linit != nullptr: chains of a culled reduction (see k_chain); counts[0] and
 // counts[1] then differ.  nr: rows of the frame (empty columns hold
 // (nr + 1, -1)); 0 means p.
@@ -208,9 +211,11 @@ size_t hull_ws_bytes(int p);
 cudaError_t hull_launch(const int32_t *lower, const int32_t *upper, const int32_t *counts, int p,
                         int32_t *hull, int32_t *hull_count, void *ws, unsigned *status,
                         cudaStream_t s);
-// Final CTA only, from survivors already in the hull workspace.
+// Final CTA only, from survivors already in the hull workspace.  narrow:
+// the survivors come from a frame whose columns and rows are at most 16384
+// (32-bit orientation tests are exact there).
 cudaError_t hull_final_launch(const HullLayout &h, void *ws, int32_t *hull, int32_t *hull_count,
-                              cudaStream_t s);
+                              cudaStream_t s, bool narrow = false);
 
 // ---- batched (batched.cu) ----
 constexpr int BATCH_MAX_P = 16384;  // largest p of a set in a batch

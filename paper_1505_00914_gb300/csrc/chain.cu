@@ -42,7 +42,12 @@ constexpr int CNT_SHIFT = 31;
 constexpr int SPARSE_TILE = 64;  // tiles with at most this many points per chain skip the pre-filter
 constexpr long long CNT_LOW = (1ll << CNT_SHIFT) - 1;
 
-template <bool FILTER, bool CULL>
+// CHAINS = false (with FILTER): only the pre-filter's survivors are wanted
+// (the hull path when the caller asks for no chain outputs), so the tile
+// skips the look-back and the chain writes.  NARROW: 32-bit orientation tests
+// in the pre-filter (sides and rows of at most 16384), and without culling
+// both chains' keep tests interleaved (run_keeps_pair).
+template <bool FILTER, bool CULL, bool CHAINS = true, bool NARROW = false>
 __global__ void __launch_bounds__(TILE)
     k_chain(const int2 *__restrict__ L, const int2 *__restrict__ Linit, int p, int nr, int2 *lower,
             int2 *upper, int *counts, uint32_t *mask, unsigned long long *state, int ntiles,
@@ -124,8 +129,13 @@ __global__ void __launch_bounds__(TILE)
                 fs.P[1][r1] = make_int2(c + 1, -e.y);
             __syncthreads();
             build_min_trees(fs.P[0], fs.M[0], cnt0, fs.P[1], fs.M[1], cnt1);
-            const bool k0 = run_keeps(fs.P[0], fs.M[0], cnt0, threadIdx.x);
-            const bool k1 = run_keeps(fs.P[1], fs.M[1], cnt1, threadIdx.x);
+            bool k0, k1;
+            if constexpr (NARROW && !CULL) {
+                run_keeps_pair<true>(fs.P[0], fs.M[0], fs.P[1], fs.M[1], cnt0, threadIdx.x, k0, k1);
+            } else {
+                k0 = run_keeps<false, NARROW>(fs.P[0], fs.M[0], cnt0, threadIdx.x);
+                k1 = run_keeps<false, NARROW>(fs.P[1], fs.M[1], cnt1, threadIdx.x);
+            }
             __shared__ int s_cw[WPB + 1];
             const int2 nk = compact_runs<false>(fs.P[0], k0, cand + (size_t)tile * TILE, fs.P[1], k1,
                                          cand + ((size_t)ntiles + tile) * TILE, s_cw);
@@ -135,6 +145,8 @@ __global__ void __launch_bounds__(TILE)
             }
         }
     }
+    if constexpr (FILTER && !CHAINS)
+        return;
     if (w == 0) {
         const long long agg = CULL ? ((long long)cnt0 << CNT_SHIFT) | cnt1 : cnt0;
         const long long pre = warp_look_back(state + 1, tile, agg, lane, status);
@@ -177,12 +189,15 @@ cudaError_t chain_launch(const int32_t *L, int p, int32_t *lower, int32_t *upper
     auto *st = reinterpret_cast<unsigned long long *>(state);
     const int2 *L2 = reinterpret_cast<const int2 *>(L), *Li = reinterpret_cast<const int2 *>(Linit);
     int2 *lo = reinterpret_cast<int2 *>(lower), *up = reinterpret_cast<int2 *>(upper);
+    const bool narrow = p <= 16384 && nr <= 16384;
+    const bool chains = lower || upper || counts || mask;
     if (cand && Linit)
-        launch(k_chain<true, true>, nt, TILE, 0, s, L2, Li, p, nr, lo, up, counts, mask, st, nt, cand, ccnt,
-                                                status);
+        launch(narrow ? k_chain<true, true, true, true> : k_chain<true, true>, nt, TILE, 0, s, L2, Li, p,
+               nr, lo, up, counts, mask, st, nt, cand, ccnt, status);
     else if (cand)
-        launch(k_chain<true, false>, nt, TILE, 0, s, L2, nullptr, p, nr, lo, up, counts, mask, st, nt, cand,
-                                                 ccnt, status);
+        launch(chains ? (narrow ? k_chain<true, false, true, true> : k_chain<true, false>)
+                      : (narrow ? k_chain<true, false, false, true> : k_chain<true, false, false>),
+               nt, TILE, 0, s, L2, nullptr, p, nr, lo, up, counts, mask, st, nt, cand, ccnt, status);
     else if (Linit)
         launch(k_chain<false, true>, nt, TILE, 0, s, L2, Li, p, nr, lo, up, counts, mask, st, nt, nullptr,
                                                  nullptr, status);

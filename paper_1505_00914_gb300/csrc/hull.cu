@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(1024)
 
 // The final CTA: gathers the survivors of every run (chain 0 first) into A,
 // then peels, merges and stitches them (hull_merge.cuh).
-template <bool SM>
+template <bool SM, bool NARROW>
 __device__ __forceinline__ void final_body(const int2 *__restrict__ cand, const int *__restrict__ ccnt,
                                            const int *offs, int nblk, int T0, int T, int2 *gA,
                                            int2 *gB, int *gF, int *gix, int2 *hull, int *hull_count,
@@ -158,9 +158,12 @@ __device__ __forceinline__ void final_body(const int2 *__restrict__ cand, const 
     }
     __syncthreads();
 
-    peel_merge_stitch(A, B, F, ix, T0, T, hull, hull_count, s_warp, s_total);
+    peel_merge_stitch<FT, 0, NARROW>(A, B, F, ix, T0, T, hull, hull_count, s_warp, s_total);
 }
 
+// NARROW: 32-bit orientation tests in the peeling (the survivors of chains of
+// a frame of side and rows at most 16384).
+template <bool NARROW>
 __global__ void __launch_bounds__(FT, 1)
     k_hull_final(const int2 *__restrict__ cand, const int *__restrict__ ccnt, int nblk, int2 *gA,
                  int2 *gB, int *gF, int *gix, int2 *hull, int *hull_count)
@@ -181,10 +184,10 @@ __global__ void __launch_bounds__(FT, 1)
     __syncthreads();
     const int T0 = s_t0;
     if (total <= PCAP)
-        final_body<true>(cand, ccnt, offs, nblk, T0, total, gA, gB, gF, gix + nb + 1, hull,
+        final_body<true, NARROW>(cand, ccnt, offs, nblk, T0, total, gA, gB, gF, gix + nb + 1, hull,
                          hull_count, s_warp, &s_total);
     else
-        final_body<false>(cand, ccnt, offs, nblk, T0, total, gA, gB, gF, gix + nb + 1, hull,
+        final_body<false, NARROW>(cand, ccnt, offs, nblk, T0, total, gA, gB, gF, gix + nb + 1, hull,
                           hull_count, s_warp, &s_total);
 }
 
@@ -223,8 +226,11 @@ cudaError_t set_attrs()
     if (dev < 0 || dev >= 64)
         return cudaErrorInvalidDevice;
     if (!attrs_set[dev]) {
-        cudaError_t a = cudaFuncSetAttribute(k_hull_final, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)FINAL_SMEM);
+        cudaError_t a = cudaFuncSetAttribute(k_hull_final<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FINAL_SMEM);
+        if (a == cudaSuccess)
+            a = cudaFuncSetAttribute(k_hull_final<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)FINAL_SMEM);
         if (a != cudaSuccess)
             return a;
         attrs_set[dev] = true;
@@ -237,7 +243,7 @@ cudaError_t set_attrs()
 size_t hull_ws_bytes(int p) { return hull_layout(p).end; }
 
 cudaError_t hull_final_launch(const HullLayout &h, void *ws, int32_t *hull, int32_t *hull_count,
-                              cudaStream_t s)
+                              cudaStream_t s, bool narrow)
 {
     cudaError_t e = set_attrs();
     if (e != cudaSuccess)
@@ -266,7 +272,7 @@ cudaError_t hull_final_launch(const HullLayout &h, void *ws, int32_t *hull, int3
         cand = h.gB;  // gathered by the final CTA before it reuses gB
         ccnt = h.ccnt2;
     }
-    launch(k_hull_final, 1, FT, FINAL_SMEM, s,
+    launch(narrow ? k_hull_final<true> : k_hull_final<false>, 1, FT, FINAL_SMEM, s,
         reinterpret_cast<const int2 *>(b + cand), reinterpret_cast<const int *>(b + ccnt), h.nblk,
         reinterpret_cast<int2 *>(b + h.gA), reinterpret_cast<int2 *>(b + h.gB),
         reinterpret_cast<int *>(b + h.gF), reinterpret_cast<int *>(b + h.gix),

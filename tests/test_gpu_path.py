@@ -242,6 +242,38 @@ def test_plain_at_scale_full_size(dist):
     np.testing.assert_array_equal(host(h)[: int(host(hc)[0])], H)
 
 
+@pytest.mark.parametrize("p", [1, 2, 33, 1023, 1024, 1025, 4096, 9999, 16384, 16385])
+def test_fused_path_with_and_without_chain_outputs(p):
+    """ch_convex_hull with chain outputs (the chain step ranks and writes both
+    chains) and without (it writes only the pre-filter's candidates), on
+    sides around the tile size and the 16384 limit of the 32-bit orientation
+    tests: a uniform set, a disc and a circle (a hull vertex in most columns),
+    each compared with the oracle."""
+    rng = np.random.default_rng(p)
+    t = np.linspace(0, 2 * np.pi, 50_000, endpoint=False)
+    r = (p - 1) / 2
+    circle = np.stack([np.rint(1 + r + r * np.cos(t)), np.rint(1 + r + r * np.sin(t))], 1)
+    sets = [rng.integers(1, p + 1, size=(300_001, 2)), synth.points("disc", 200_000, p, seed=p),
+            circle]
+    for P in sets:
+        P = np.ascontiguousarray(np.clip(P, 1, p), dtype=np.int32)
+        Lo = oracle.reduce(P, p)
+        H = oracle.hull_chain(Lo)
+        lo_o, up_o = oracle.chain(Lo)
+        d = dev(P)
+        h0, hc0 = ch.ch_convex_hull(d, p)
+        np.testing.assert_array_equal(host(h0)[: int(host(hc0)[0])], H)
+        lo = torch.empty((p, 2), dtype=torch.int32, device="cuda")
+        up = torch.empty((p, 2), dtype=torch.int32, device="cuda")
+        cnt = torch.empty(2, dtype=torch.int32, device="cuda")
+        h1, hc1 = ch.ch_convex_hull(d, p, lower=lo, upper=up, counts=cnt)
+        np.testing.assert_array_equal(host(h1)[: int(host(hc1)[0])], H)
+        s = int(host(cnt)[0])
+        assert s == int(host(cnt)[1]) == lo_o.shape[0]
+        np.testing.assert_array_equal(host(lo)[:s], lo_o)
+        np.testing.assert_array_equal(host(up)[:s], up_o)
+
+
 def test_projected_shells_full_size():
     """p=4096, n=10^7 projected shells and cylinders."""
     p = 4096
