@@ -49,7 +49,8 @@ def test_bbox_of_nothing():
 
 
 @pytest.mark.parametrize("sx,sy", [(1000, 1000), (5000, 300), (300, 5000), (1, 700), (700, 1),
-                                   (1, 1), (29056, 70000), (70000, 29056), (70000, 300000),
+                                   (1, 1), (16384, 16384), (16384, 16385), (16385, 16384),
+                                   (12000, 40000), (29056, 70000), (70000, 29056), (70000, 300000),
                                    (300000, 70000), (130000, 200000), (200000, 130000)])
 @pytest.mark.parametrize("dist", ["uniform", "disc", "gaussian", "shells"])
 def test_any_box_matches_the_oracle(sx, sy, dist):
