@@ -155,14 +155,17 @@ int ch_hull(const int32_t *lower, const int32_t *upper, const int32_t *counts,
             void *workspace, size_t ws_bytes, ch_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
-/* The three steps in one call (the reduction's per-block partial arrays   */
-/* are merged inside the chain step instead of through a separate pass).   */
+/* The three steps in one call, back to back on the stream (each kernel   */
+/* launched with programmatic dependent launch), with the chain step and   */
+/* the hull's pre-filter fused into one kernel.                            */
 /* ---------------------------------------------------------------------- */
 
 int ch_convex_hull_workspace_size(int64_t n, int32_t p, size_t *bytes);
 
 /* Same outputs as ch_reduce + ch_chain + ch_hull; L, lower, upper, counts
- * may each be NULL, in which case the workspace holds them.  A small problem
+ * may each be NULL, in which case the workspace holds them.  When lower,
+ * upper and counts are all NULL the chains are not ranked or written at all:
+ * the chain step writes only the candidates of the hull.  A small problem
  * (ch_plan_info form 3) called with lower, upper and counts all NULL runs
  * as one kernel: its thread blocks fold slices of the points into private
  * copies of L, and the block that finishes last (a ticket word kept per
