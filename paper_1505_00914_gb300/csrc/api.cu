@@ -826,12 +826,14 @@ int ch_hull_learned(const int32_t *pts, int64_t n, int32_t p, const float *param
         L = reinterpret_cast<int32_t *>(b + pw.L);
     if (!Linit)
         Linit = reinterpret_cast<int32_t *>(b + w.Linit);
-    if (!lower)
-        lower = reinterpret_cast<int32_t *>(b + pw.lower);
-    if (!upper)
-        upper = reinterpret_cast<int32_t *>(b + pw.upper);
-    if (!counts)
-        counts = reinterpret_cast<int32_t *>(b + pw.counts);
+    if (lower || upper || counts) {  // else the chain step writes only the hull's candidates
+        if (!lower)
+            lower = reinterpret_cast<int32_t *>(b + pw.lower);
+        if (!upper)
+            upper = reinterpret_cast<int32_t *>(b + pw.upper);
+        if (!counts)
+            counts = reinterpret_cast<int32_t *>(b + pw.counts);
+    }
     void *part = b + pw.part;
     unsigned long long *zero = reinterpret_cast<unsigned long long *>(b + pw.state);
     const int nzero = (int)(chain_state_bytes(p) / 8);

@@ -192,8 +192,9 @@ cudaError_t chain_launch(const int32_t *L, int p, int32_t *lower, int32_t *upper
     const bool narrow = p <= 16384 && nr <= 16384;
     const bool chains = lower || upper || counts || mask;
     if (cand && Linit)
-        launch(narrow ? k_chain<true, true, true, true> : k_chain<true, true>, nt, TILE, 0, s, L2, Li, p,
-               nr, lo, up, counts, mask, st, nt, cand, ccnt, status);
+        launch(chains ? (narrow ? k_chain<true, true, true, true> : k_chain<true, true>)
+                      : (narrow ? k_chain<true, true, false, true> : k_chain<true, true, false>),
+               nt, TILE, 0, s, L2, Li, p, nr, lo, up, counts, mask, st, nt, cand, ccnt, status);
     else if (cand)
         launch(chains ? (narrow ? k_chain<true, false, true, true> : k_chain<true, false>)
                       : (narrow ? k_chain<true, false, false, true> : k_chain<true, false, false>),
