@@ -129,9 +129,10 @@ __device__ __forceinline__ void fold_edges(const int32_t *pts, int64_t n, const 
 // (register double buffering), so the loads never wait for the folding.
 // fold(v) takes one vector of points.  KEEP: load through L2 with the
 // normal policy (the data is read again soon) instead of evict-first.
-template <int RT, bool KEEP = false, typename Fold>
-__device__ __forceinline__ void stream_pairs(const int4 *__restrict__ p4, int64_t s0, int64_t e0,
-                                             Fold &&fold)
+// The same over 64-bit indices.
+template <int RT, bool KEEP, typename Fold>
+__device__ __forceinline__ void stream_pairs_wide(const int4 *__restrict__ p4, int64_t s0,
+                                                  int64_t e0, Fold &fold)
 {
     auto ld = [&](int64_t j) { return KEEP ? __ldcg(p4 + j) : __ldcs(p4 + j); };
     int4 v[RU];
@@ -155,6 +156,50 @@ __device__ __forceinline__ void stream_pairs(const int4 *__restrict__ p4, int64_
         for (int u = 0; u < RU; ++u)
             v[u] = w[u];
     }
+}
+
+#ifndef CH_STREAM32
+#define CH_STREAM32 1  // index a slice with 32-bit offsets from its first vector
+#endif
+template <int RT, bool KEEP = false, typename Fold>
+__device__ __forceinline__ void stream_pairs(const int4 *__restrict__ p4, int64_t s0, int64_t e0,
+                                             Fold &&fold)
+{
+#if CH_STREAM32
+    // a slice below 2^31 - 2 RU RT vectors (any that fits in memory at one
+    // CTA per SM) is indexed by 32-bit offsets from its start, which keeps the
+    // loop's index tests and address sums single-word
+    if (e0 - s0 > (int64_t)(0x7FFFFFFF - 2 * RU * RT)) {
+        stream_pairs_wide<RT, KEEP>(p4, s0, e0, fold);
+        return;
+    }
+    const int4 *__restrict__ q = p4 + s0;
+    const int len = (int)(e0 - s0);
+    auto ld = [&](int j) { return KEEP ? __ldcg(q + j) : __ldcs(q + j); };
+    int4 v[RU];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+        const int j = (int)threadIdx.x + u * RT;
+        v[u] = j < len ? ld(j) : make_int4(0, 0, 0, 0);
+    }
+    for (int i = (int)threadIdx.x; i < len; i += RT * RU) {
+        int4 w[RU];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int j = i + (RU + u) * RT;
+            w[u] = j < len ? ld(j) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < RU; ++u)
+            if (i + u * RT < len)
+                fold(v[u]);
+#pragma unroll
+        for (int u = 0; u < RU; ++u)
+            v[u] = w[u];
+    }
+#else
+    stream_pairs_wide<RT, KEEP>(p4, s0, e0, fold);
+#endif
 }
 
 // ---------------------------------------------------------------- private
