@@ -106,15 +106,29 @@ def _peaks():
 KERNEL_OF_FORM = ("k_reduce_private", "k_reduce_filtered", "k_reduce_global", "k_small")
 
 
-def _kernel_sha(src_path, name):
-    """Digest of one kernel's source text: from the line that names it in a
-    definition to the end of its body (the first line that is a lone "}")."""
-    lines = open(src_path).read().split("\n")
-    start = next(i for i, l in enumerate(lines) if l.strip().startswith(name + "("))
+# device functions every reduction kernel streams its points through: a change
+# to them changes the kernels' traffic as much as a change to their own text
+STREAM_HELPERS = ("stream_pairs_wide", "stream_pairs")
+
+
+def _def_text(lines, name):
+    """Source text of one definition: from the line that names it (a kernel's
+    name starts its line, a device function's follows `void`) back over its
+    template lines, to the end of its body (the first lone "}")."""
+    start = next(i for i, l in enumerate(lines)
+                 if l.strip().startswith(name + "(") or (" void " + name + "(") in l)
     while start > 0 and lines[start - 1].strip() and not lines[start - 1].startswith("//"):
         start -= 1
     end = next(i for i in range(start, len(lines)) if lines[i] == "}")
-    return hashlib.sha256("\n".join(lines[start:end + 1]).encode()).hexdigest()[:16]
+    return "\n".join(lines[start:end + 1])
+
+
+def _kernel_sha(src_path, name):
+    """Digest of one kernel's source text and of the streaming helpers it
+    calls."""
+    lines = open(src_path).read().split("\n")
+    text = "\n".join(_def_text(lines, k) for k in (name,) + STREAM_HELPERS)
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
 def _traffic(kernel, n, p, u16=False):
