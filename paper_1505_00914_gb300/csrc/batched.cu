@@ -323,14 +323,23 @@ __global__ void __launch_bounds__(BT, 1)
 // tile pre-filter in the finish threads as well, on the set's valid columns
 // extracted from L by the whole CTA, measured slower: 3.18 against 2.62 ms
 // on the 10,000-set batch at a 512/512 split.)
+// The survivor capacity BPW sets how much of the SM's 256 KB of combined
+// L1 and shared memory is left to L1, which holds the fold threads' loads in
+// flight: 4096 survivors (212 KB of shared memory, 28 KB of L1) against 2048
+// (170 KB, 60 KB of L1): 2.55 against 2.27 ms per replay of the 10,000-set
+// batch (1536: no further gain); a set with more survivors peels them in
+// global scratch.
 constexpr int WS_BAR_FOLD = 1, WS_BAR_FINISH = 2;  // named barriers (0 is the whole CTA)
-constexpr int BPW = 4096;  // survivors (both chains) peeled in shared memory
-constexpr size_t WS_D = SM_L;                          // survivors
-constexpr size_t WS_B = WS_D + BPW * sizeof(int2);     // peel buffer B (tile buffers between sets)
+#ifndef CH_BPW
+#define CH_BPW 2048
+#endif
+constexpr int BPW = CH_BPW;  // survivors (both chains) peeled in shared memory
+constexpr size_t WS_D = SM_L;                          // survivors (with B: the tile buffers at a hand-over)
+constexpr size_t WS_B = WS_D + BPW * sizeof(int2);     // peel buffer B
 constexpr size_t WS_F = WS_B + BPW * sizeof(int2);     // peel flags F
 constexpr size_t WS_IX = WS_F + BPW * sizeof(int);     // merge-tree index arrays
 constexpr size_t WS_SMEM = WS_IX + 4 * (BPW / HS + 2) * sizeof(int);
-static_assert(SM_RUNS <= WS_IX - WS_B, "the tile buffers fit the peel buffers B and F");
+static_assert(SM_RUNS <= WS_F - WS_D, "the tile buffers fit the survivor and peel buffers D and B");
 static_assert(WS_SMEM <= 227 * 1024, "one CTA's shared memory");
 
 template <int FW>
@@ -405,7 +414,7 @@ __global__ void __launch_bounds__(BT, 1)
                     s_done = 0;
                 }
                 group_sync<0, BT>();  // hand-over: the finish threads are done with the last set
-                collect_survivors(p, slo, shi, smem + WS_B, Ds, BPW, scr, s_warp, &s_cnt);
+                collect_survivors(p, slo, shi, smem + WS_D, Ds, BPW, scr, s_warp, &s_cnt);
             }
         }
         if (t == 0)
@@ -420,7 +429,7 @@ __global__ void __launch_bounds__(BT, 1)
             const int set = s_set;  // read before the tile phase: s_set changes only after it
             const int p = sets[set].p;
             const Survivors sv =
-                collect_survivors(p, slo, slo + p, smem + WS_B, Ds, BPW, scr, s_warp, &s_cnt);
+                collect_survivors(p, slo, slo + p, smem + WS_D, Ds, BPW, scr, s_warp, &s_cnt);
             int2 *B;
             int *F, *ix;
             if (sv.in_smem) {
