@@ -214,23 +214,51 @@ __device__ __forceinline__ void global_peel_scratch(int2 *scr, int2 *&B, int *&F
 }
 
 // Hull of the set whose L is in slo/shi (p columns); whole CTA.
-__device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 *scr,
-                           int2 *hull, int *hull_count, int *s_warp, int *s_total, int *s_cnt)
+// Layout of the shared memory a set is finished in: L at `smem` (which holds
+// the peel scratch once the tiles are done: cap int2 + cap int + the merge
+// tree's index arrays), the tile buffers at `runs`, up to `cap` survivors at
+// Ds; more survivors peel in the CTA's global scratch.
+__device__ void finish_set_at(int p, int *slo, int *shi, unsigned char *smem, unsigned char *runs,
+                              int2 *Ds, int cap, int2 *scr, int2 *hull, int *hull_count,
+                              int *s_warp, int *s_total, int *s_cnt)
 {
-    const Survivors sv = collect_survivors(p, slo, shi, smem + SM_L + SM_A,
-                                           reinterpret_cast<int2 *>(smem + SM_L), BPCAP, scr, s_warp,
-                                           s_cnt);
+    const Survivors sv = collect_survivors(p, slo, shi, runs, Ds, cap, scr, s_warp, s_cnt);
     int2 *B;
     int *F, *ix;
     if (sv.in_smem) {  // L is no longer needed: its region holds the peel scratch
         B = reinterpret_cast<int2 *>(smem);
-        F = reinterpret_cast<int *>(B + BPCAP);
-        ix = F + BPCAP;
+        F = reinterpret_cast<int *>(B + cap);
+        ix = F + cap;
     } else {
         global_peel_scratch(scr, B, F, ix);
     }
     peel_merge_stitch<FT, 0, true>(sv.D, B, F, ix, sv.T0, sv.T, hull, hull_count, s_warp, s_total);
 }
+
+// The batched kernels' layout: [L: SM_L][survivors: BPCAP int2][tile buffers].
+__device__ void finish_set(int p, int *slo, int *shi, unsigned char *smem, int2 *scr,
+                           int2 *hull, int *hull_count, int *s_warp, int *s_total, int *s_cnt)
+{
+    finish_set_at(p, slo, shi, smem, smem + SM_L + SM_A, reinterpret_cast<int2 *>(smem + SM_L),
+                  BPCAP, scr, hull, hull_count, s_warp, s_total, s_cnt);
+}
+
+// k_small's layout, sized for its p: [L or peel scratch][survivors: SCAP
+// int2][tile buffers].  Less shared memory leaves more of the SM to L1,
+// which holds the folding threads' loads in flight.
+constexpr int SCAP = 2048;
+__host__ __device__ constexpr size_t small_lreg(int p)
+{
+    return ((8 * (size_t)p > (size_t)SCAP * 12 + 4 * (SCAP / HS + 2) * 4
+                 ? 8 * (size_t)p
+                 : (size_t)SCAP * 12 + 4 * (SCAP / HS + 2) * 4) +
+            15) & ~size_t(15);
+}
+__host__ __device__ constexpr size_t small_smem(int p)
+{
+    return small_lreg(p) + (size_t)SCAP * sizeof(int2) + SM_RUNS;
+}
+static_assert(small_smem(BATCH_MAX_P) <= BATCH_SMEM, "k_small never needs more than the batched kernels");
 
 // WRITE_L: instead of finishing a set, write its L (Algorithm 1's array,
 // (p+1, -1) for an empty column) to L_out[L_offsets[set] ...].
@@ -575,8 +603,10 @@ __global__ void __launch_bounds__(BT, 1)
     if (L_out)
         for (int i = threadIdx.x; i < p; i += BT)
             L_out[i] = make_int2(slo[i], shi[i]);
-    finish_set(p, slo, shi, smem, reinterpret_cast<int2 *>(scratch), hull, hull_count, s_warp,
-               &s_total, &s_cnt);
+    const size_t lreg = small_lreg(p);
+    finish_set_at(p, slo, shi, smem, smem + lreg + (size_t)SCAP * sizeof(int2),
+                  reinterpret_cast<int2 *>(smem + lreg), SCAP, reinterpret_cast<int2 *>(scratch),
+                  hull, hull_count, s_warp, &s_total, &s_cnt);
 }
 
 constexpr int SMALL_PPC = 8192;                // points per CTA of k_small
@@ -677,7 +707,7 @@ cudaError_t small_launch(const int32_t *pts, int64_t n, int p, int G, void *ws, 
     unsigned char *scratch = reinterpret_cast<unsigned char *>(b + w.take(SCR_BYTES));
     if (ev0)
         cudaEventRecord(ev0, s);
-    launch(k_small, G, BT, BATCH_SMEM, s, pts, n, p, part, ticket, scratch,
+    launch(k_small, G, BT, small_smem(p), s, pts, n, p, part, ticket, scratch,
            reinterpret_cast<int2 *>(L_out), reinterpret_cast<int2 *>(hull), hull_count, status);
     if (ev1)
         cudaEventRecord(ev1, s);
