@@ -98,7 +98,7 @@ int ch_trace_set(void *const *events, int npairs);
 
 /* How ch_convex_hull will run n points of side p on the current device
  * when it is not asked for the chains (lower, upper and counts NULL):
- * *form = 0 (private shared-memory copies of L, p <= 29056), 1 (filtered
+ * *form = 0 (private shared-memory copies of L, p <= 20480), 1 (filtered
  * global L, p <= 116224), 2 (global L with a read-then-atomic test) or 3
  * (small problems: p <= 16384, at most 8192 points per thread block and
  * the blocks' partial copies of L at most 65536 words in all, the whole path

@@ -7,7 +7,7 @@
 // GB300 (compare-and-swap and cluster-remote atomics are an order of
 // magnitude slower), which fixes the two forms used here:
 //
-// Private form (8p bytes fit one CTA's shared memory, p <= 29056):
+// Private form (8p bytes of shared memory, p <= 20480):
 //   every CTA (one per SM) keeps int32 lo[p], hi[p] in shared memory, folds
 //   its slice of the points with unconditional shared atomics and writes its
 //   copy as one row of a partial array, packed as ((lo-1) << 16) | (hi-1)
@@ -625,6 +625,17 @@ int private_bps(int dev, size_t smem)
     return bps;
 }
 
+// Shared memory the private form may use.  Above it the filtered form is
+// faster: a private copy of 8p bytes leaves the SM too little L1 for the
+// loads in flight (a whole call on 2^26 points: p = 16384 private 115.9 us
+// against filtered 120.5; p = 24576 126.5 against 123.8; p = 29056 155.6
+// against 122.8).
+#ifndef CH_PRIVATE_SMEM_MAX
+#define CH_PRIVATE_SMEM_MAX 163840u  // p <= 20480
+#endif
+#ifndef CH_FILTER_SMEM_MAX
+#define CH_FILTER_SMEM_MAX (1u << 30)  // the filtered form up to the opt-in limit (the global form is slower)
+#endif
 #ifndef CH_WARM_CLUSTER_MAX
 #define CH_WARM_CLUSTER_MAX 8  // largest cluster of the filter warm-up (portable limit)
 #endif
@@ -692,7 +703,7 @@ int reduce_plan(int64_t n, int nc, int nr, ReducePlan *pl)
     const int64_t npairs = n / 2;
     pl->cluster = 1;
     pl->threads = 1024;
-    if ((size_t)nc * 8 <= optin && nr <= 65536) {
+    if ((size_t)nc * 8 <= std::min<size_t>(optin, CH_PRIVATE_SMEM_MAX) && nr <= 65536) {
         pl->mode = 0;  // private copies (rows packed in 16 bits for the merge)
         pl->smem = (size_t)nc * 8;
         // at least ~16K points per CTA so a private copy pays for its merge
@@ -703,7 +714,7 @@ int reduce_plan(int64_t n, int nc, int nr, ReducePlan *pl)
         pl->grid = (int)std::min<int64_t>(want, (int64_t)std::max(1, std::min(bps, 1)) * sms);
         pl->copies = pl->grid;
     } else {
-        pl->mode = (size_t)nc * 2 <= optin ? 1 : 2;  // filtered / read-then-atomic
+        pl->mode = (size_t)nc * 2 <= std::min<size_t>(optin, CH_FILTER_SMEM_MAX) ? 1 : 2;  // filtered / read-then-atomic
         pl->smem = pl->mode == 1 ? (((size_t)nc * 2 + 15) & ~size_t(15)) : 0;
         pl->grid = sms;
         pl->copies = 0;

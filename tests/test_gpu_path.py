@@ -78,8 +78,8 @@ def test_block_bit_index_on_gpu():
     assert int(M[keys["block"]]) == 1 << keys["bit"]
 
 
-@pytest.mark.parametrize("p", [1, 2, 5, 31, 32, 33, 1000, 1024, 1025, 4096, 4097, 16384, 29056,
-                               29057, 65535, 65536, 116224, 116225])
+@pytest.mark.parametrize("p", [1, 2, 5, 31, 32, 33, 1000, 1024, 1025, 4096, 4097, 16384, 20480,
+                               20481, 29056, 29057, 65535, 65536, 116224, 116225])
 def test_tile_boundaries_and_layouts(p):
     rng = np.random.default_rng(p)
     for n in (0, 1, 2, 3, 1001, 50_000):

@@ -44,7 +44,8 @@ def check(P, p, offset=0):
     np.testing.assert_array_equal(host(h)[: int(host(hc)[0])], oracle.hull_chain(Lo))
 
 
-@pytest.mark.parametrize("p", [1, 2, 31, 1024, 1025, 4096, 29056, 29057, 65535, 65536])
+@pytest.mark.parametrize("p", [1, 2, 31, 1024, 1025, 4096, 20480, 20481, 29056, 29057, 65535,
+                               65536])
 @pytest.mark.parametrize("offset", [0, 1, 2, 3])
 def test_every_alignment_and_tail(p, offset):
     rng = np.random.default_rng(p * 4 + offset)
