@@ -25,7 +25,8 @@ namespace ch {
 namespace {
 
 constexpr int BT = 1024;       // threads per CTA (= RUN, one column per thread in a tile)
-constexpr int BPCAP = 8192;    // survivors (both chains) finished in shared memory
+constexpr int BPCAP = 2048;    // survivors (both chains) finished in shared memory (more: global
+                               // scratch; a smaller region leaves more L1 for loads in flight)
 
 struct BItem {
     long long start, end;  // global point range [start, end)
@@ -806,7 +807,8 @@ int batch_launch(const int32_t *pts, int2 *hull_out, const int64_t *hull_offsets
         return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ERR_CUDA;
     }
     auto kern = L_out ? k_batched<true> : k_batched<false>;
-    kern<<<info.grid, BT, BATCH_SMEM, s>>>(
+    // writing L needs only L's region of the layout (the rest would take L1)
+    kern<<<info.grid, BT, L_out ? SM_L : BATCH_SMEM, s>>>(
         pts, reinterpret_cast<const BItem *>(b + l.items), info.nitems,
         reinterpret_cast<const BSet *>(b + l.sets), head, head + 1,
         reinterpret_cast<uint32_t *>(b + l.part), hull_out, hull_offsets, hull_counts, L_out,
