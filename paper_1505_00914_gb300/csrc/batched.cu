@@ -79,24 +79,30 @@ __device__ void fold_range(const int32_t *__restrict__ base, int64_t n, int p, i
     }
     const int4 *p4 = reinterpret_cast<const int4 *>(base + 2 * head);
     // U loads in flight per thread; the next U are issued before the current
-    // ones are folded (register double buffering)
-    constexpr int U = 4;
+    // ones are folded (register double buffering).  A work item holds at most
+    // 2^22 points (and a small problem's slice fewer), so the vector indices
+    // are 32-bit, which keeps the loop's tests and address sums single-word.
+#ifndef CH_FOLD_U
+#define CH_FOLD_U 4
+#endif
+    constexpr int U = CH_FOLD_U;
+    const int m = (int)npairs;
     int4 v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        const int64_t j = tid + (int64_t)u * NT;
-        v[u] = j < npairs ? __ldcs(p4 + j) : make_int4(0, 0, 0, 0);
+        const int j = tid + u * NT;
+        v[u] = j < m ? __ldcs(p4 + j) : make_int4(0, 0, 0, 0);
     }
-    for (int64_t i = tid; i < npairs; i += (int64_t)NT * U) {
+    for (int i = tid; i < m; i += NT * U) {
         int4 nx[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t j = i + (int64_t)(U + u) * NT;
-            nx[u] = j < npairs ? __ldcs(p4 + j) : make_int4(0, 0, 0, 0);
+            const int j = i + (U + u) * NT;
+            nx[u] = j < m ? __ldcs(p4 + j) : make_int4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (i + (int64_t)u * NT < npairs) {
+            if (i + u * NT < m) {
                 fold(slo, shi, up, v[u].x, v[u].y, bad);
                 fold(slo, shi, up, v[u].z, v[u].w, bad);
             }
