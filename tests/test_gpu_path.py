@@ -175,6 +175,17 @@ def test_out_of_range_points_set_status():
     assert ch.ch_sync_status() == ch.CH_OK  # the status word clears on read
 
 
+def test_reduction_forms_switch_at_their_limits():
+    """The private form up to 160 KB of shared memory (p = 20480), the
+    filtered form up to the opt-in limit (p = 116224), the global form
+    beyond (form numbers of ch_plan_info)."""
+    n = 1 << 22
+    assert ch.ch_plan_info(n, 20480)[0] == 0
+    assert ch.ch_plan_info(n, 20481)[0] == 1
+    assert ch.ch_plan_info(n, 116224)[0] == 1
+    assert ch.ch_plan_info(n, 116225)[0] == 2
+
+
 def test_argument_errors():
     P = dev(np.ones((10, 2), np.int32))
     with pytest.raises(ch.ChError) as e:
