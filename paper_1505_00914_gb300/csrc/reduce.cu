@@ -489,22 +489,45 @@ __global__ void __launch_bounds__(RT)
     auto fold = [&](int x, int y) {
         uint32_t c, rr;
         frame_map<FM>(fr, x, y, c, rr);
-        if (c >= (uint32_t)fr.nc || rr >= (uint32_t)fr.nr) {
-            bad = true;
-            return;
-        }
-        const int r = (int)rr + 1;
-        const uint32_t f = F[c], b = rr >> shift;
-        const uint32_t qlo = f >> 8, qhi = f & 0xFFu;
-        if (b <= qlo) {
-            atomicMin(&L[c].x, r);
-            if (b < qlo)
-                fb[2 * c + 1] = (unsigned char)b;
-        }
-        if (b >= qhi) {
-            atomicMax(&L[c].y, r);
-            if (b > qhi)
-                fb[2 * c] = (unsigned char)b;
+        if constexpr (FM == 3) {
+            // packed 16-bit points, four per load, leave the fold issue-bound:
+            // no early exit for a point outside the frame (it reads column 0's
+            // filter and passes no test), which drops a branch per point
+            // (bench: 729 -> 781 Gpoints/s; with int32 pairs it gains nothing)
+            const bool ok = c < (uint32_t)fr.nc && rr < (uint32_t)fr.nr;
+            bad |= !ok;
+            c = ok ? c : 0u;
+            const int r = (int)rr + 1;
+            const uint32_t f = F[c], b = rr >> shift;
+            const uint32_t qlo = f >> 8, qhi = f & 0xFFu;
+            if (ok && b <= qlo) {
+                atomicMin(&L[c].x, r);
+                if (b < qlo)
+                    fb[2 * c + 1] = (unsigned char)b;
+            }
+            if (ok && b >= qhi) {
+                atomicMax(&L[c].y, r);
+                if (b > qhi)
+                    fb[2 * c] = (unsigned char)b;
+            }
+        } else {
+            if (c >= (uint32_t)fr.nc || rr >= (uint32_t)fr.nr) {
+                bad = true;
+                return;
+            }
+            const int r = (int)rr + 1;
+            const uint32_t f = F[c], b = rr >> shift;
+            const uint32_t qlo = f >> 8, qhi = f & 0xFFu;
+            if (b <= qlo) {
+                atomicMin(&L[c].x, r);
+                if (b < qlo)
+                    fb[2 * c + 1] = (unsigned char)b;
+            }
+            if (b >= qhi) {
+                atomicMax(&L[c].y, r);
+                if (b > qhi)
+                    fb[2 * c] = (unsigned char)b;
+            }
         }
     };
     const VecView pv = vec_view<FM>(pts, n);
